@@ -1,0 +1,275 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+exhaustive enumeration, closed forms, the paper's lemmas, library eigenvalues and
+finite differences.  Each test names the passage it checks."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle.brute import enumerate_min
+from paper_2408_04875_gb300 import instances as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "bruteforce_n16_n20.json")
+
+
+def _small(n=12, seed=0, density=0.4):
+    Q, b = I.random_ubqp(n, density, seed, b_range=(-50, 50))
+    return Q, b
+
+
+# ---- Eq. (bqp): objective --------------------------------------------------------
+
+def test_objective_matches_maxcut_edge_count():
+    """Max-Cut mapping of Sec. 5.3: f(y) must equal minus the number-weighted cut,
+    counted edge by edge."""
+    W, b = I.maxcut_ubqp(14, 0.5, 3)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        y = rng.integers(0, 2, 14).astype(np.uint8)
+        cut = sum(W[i, j] for i in range(14) for j in range(i + 1, 14) if y[i] != y[j])
+        assert O.objective(W, b, y) == -cut
+
+
+def test_objective_equals_penalized_on_binary_points():
+    """Sec. 2.2 / problem (p): h(x,p) = f(x) for every p when x is binary."""
+    Q, b = _small()
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        x = rng.integers(0, 2, Q.shape[0]).astype(np.uint8)
+        p = rng.uniform(-50, 50, Q.shape[0])
+        assert O.penalized(Q, b, p, x.astype(float), want_grad=False) == pytest.approx(
+            O.objective(Q, b, x), abs=1e-9)
+
+
+def test_reformulation_leaves_binary_objective_unchanged():
+    """Sec. 3.5: Q + Diag(gamma), b - gamma give the same f on {0,1}^n."""
+    Q, b = _small(10, 2)
+    Qp, bp, gam = O.reformulate(Q, b, None)
+    assert np.all(gam > 2 * np.abs(Q).sum(1) + np.abs(b))
+    f1, x1 = enumerate_min(Q, b)
+    f2, x2 = enumerate_min(Qp, bp)
+    assert f1 == f2 and np.array_equal(x1, x2)
+
+
+# ---- h and its gradient ----------------------------------------------------------
+
+def test_gradient_matches_central_differences():
+    """A quadratic has zero third derivative, so the central difference with step
+    1e-3 is exact up to rounding."""
+    Q, b = I.dense_ubqp(40, 1)
+    rng = np.random.default_rng(2)
+    p = rng.uniform(0, 100, 40)
+    x = rng.random(40)
+    h0, g = O.penalized(Q, b, p, x)
+    fd = np.empty(40)
+    for i in range(40):
+        e = np.zeros(40); e[i] = 1e-3
+        fd[i] = (O.penalized(Q, b, p, x + e, False) - O.penalized(Q, b, p, x - e, False)) / 2e-3
+    assert np.max(np.abs(fd - g)) <= 1e-7 * np.max(np.abs(g))
+
+
+def test_lemma_4_1_monotone_in_p():
+    """Lemma 4.1: h(x, p1) <= h(x, p2) on the box whenever p1 <= p2."""
+    Q, b = _small()
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        x = rng.random(Q.shape[0])
+        p1 = rng.uniform(-100, 100, Q.shape[0])
+        p2 = p1 + rng.uniform(0, 100, Q.shape[0])
+        assert O.penalized(Q, b, p1, x, False) <= O.penalized(Q, b, p2, x, False) + 1e-9
+
+
+# ---- Eq. (cret) and rho ----------------------------------------------------------
+
+def test_kkt_residual_index_sets():
+    """Sec. 3.3: interior coordinates count |g|, x=0 counts max(-g,0), x=1 counts max(g,0)."""
+    x = np.array([0.0, 0.0, 1.0, 1.0, 0.5])
+    assert O.kkt_residual(x, np.array([3.0, 0, 0, 0, 0])) == 0.0
+    assert O.kkt_residual(x, np.array([-3.0, 0, 0, 0, 0])) == 3.0
+    assert O.kkt_residual(x, np.array([0, 0, -4.0, 0, 0])) == 0.0
+    assert O.kkt_residual(x, np.array([0, 0, 4.0, 0, 0])) == 4.0
+    assert O.kkt_residual(x, np.array([0, 0, 0, 0, -2.5])) == 2.5
+
+
+def test_rho_hand_example():
+    Q = np.array([[2.0, -7.0], [-7.0, 1.0]])
+    assert O.rho(Q, np.array([0.0, 0.0]), np.array([0.0, 0.0])) == 14.0
+    assert O.rho(Q, np.array([30.0, 0.0]), np.array([0.0, 0.0])) == 30.0
+    assert O.rho(Q, np.array([0.0, 0.0]), np.array([-20.0, 0.0])) == 44.0   # |2(2+20)|
+    assert O.rho(np.zeros((1, 1)), np.zeros(1), np.zeros(1)) == 1.0
+
+
+# ---- Eq. (gamma): x^0 --------------------------------------------------------------
+
+def test_initial_point_solves_first_order_condition_and_is_interior():
+    """Sec. 3.5: 2(Q + Diag gamma) x = gamma - b, and gamma as chosen keeps 0 < x < 1."""
+    for seed in range(3):
+        Q, b = I.random_ubqp(60, 0.3, seed, b_range=(-50, 50))
+        mu = I.perturbation(Q, seed)
+        Qp, bp, gam = O.reformulate(Q, b, mu)
+        x0 = O.initial_point(Qp, bp)
+        assert np.max(np.abs(2 * Qp @ x0 + bp)) <= 1e-10 * np.max(gam)
+        assert np.all(x0 > 0) and np.all(x0 < 1)
+        # x0 - e/2 = -(1/2) Q'^-1 ((Q+mu) e + b) and, Q' being strictly diagonally
+        # dominant, ||Q'^-1||_inf <= 1 / min_i (Q'_ii - sum_{j!=i} |Q'_ij|)
+        Qm = Q + mu
+        off = np.abs(Qp).sum(1) - np.abs(np.diag(Qp))
+        bound = 0.5 * np.max(np.abs(Qm.sum(1) + b)) / np.min(np.diag(Qp) - off)
+        assert np.max(np.abs(x0 - 0.5)) <= bound * (1 + 1e-12)
+
+
+# ---- lambda_min ------------------------------------------------------------------
+
+@pytest.mark.parametrize("m", [1, 2, 3, 7, 40, 130])
+def test_lambda_min_matches_library_eigvalsh(m):
+    rng = np.random.default_rng(m)
+    A = rng.standard_normal((m, m))
+    A = A + A.T + np.diag(rng.uniform(-3, 3, m))
+    assert O.lambda_min(A) == pytest.approx(np.linalg.eigvalsh(A)[0], rel=1e-12, abs=1e-12)
+
+
+def test_lambda_min_closed_forms():
+    a, c, d = 3.0, -1.5, 0.5
+    lam = (a + d) / 2 - np.sqrt(((a - d) / 2) ** 2 + c * c)
+    assert O.lambda_min(np.array([[a, c], [c, d]])) == pytest.approx(lam, rel=1e-14)
+    assert O.lambda_min(np.diag([4.0, -2.0, 9.0])) == pytest.approx(-2.0, rel=1e-14)
+
+
+def test_penalty_step_first_outer_step_positive():
+    """At s = 0, p = 0 and Q' is strictly diagonally dominant: lambda > 0 (Sec. 3.4)."""
+    Q, b = I.random_ubqp(50, 0.1, 0)
+    mu = I.perturbation(Q, 0)
+    Qp, bp, _ = O.reformulate(Q, b, mu)
+    x0 = O.initial_point(Qp, bp)
+    a, m, lam, fb = O.penalty_step(Qp, bp, np.zeros(50), x0)
+    z = x0 - x0 ** 2
+    ref = np.linalg.eigvalsh(Qp / np.sqrt(np.outer(z, z)))[0]
+    assert m == 50 and not fb and lam > 0
+    assert lam == pytest.approx(ref, rel=1e-10) and a == pytest.approx(0.9 * ref, rel=1e-10)
+
+
+# ---- Alg. 2 / Alg. 1 ---------------------------------------------------------------
+
+def test_pabb_separable_case_reaches_closed_form():
+    """Q_off = 0: h is separable and strictly convex on the box when Q_ii - p_i > 0;
+    its minimiser is clip(-bbar_i / (2 Qbar_ii), 0, 1)."""
+    rng = np.random.default_rng(5)
+    n = 30
+    d = rng.uniform(1, 10, n)
+    Qp = np.diag(d)
+    bp = rng.uniform(-30, 30, n)
+    p = rng.uniform(0, 0.5, n)
+    r = O.inner(Qp, bp, p, np.full(n, 0.5), O.opts(tol_inner=1e-12))
+    xs = np.clip(-(bp + p) / (2 * (d - p)), 0, 1)
+    assert r["exit"] in (0, 2)
+    assert np.max(np.abs(r["x"] - xs)) <= 1e-9
+
+
+def test_iterates_stay_in_box_and_steps_positive():
+    Q, b = I.random_ubqp(50, 0.1, 1)
+    Qp, bp, _ = O.reformulate(Q, b, I.perturbation(Q, 1))
+    x0 = O.initial_point(Qp, bp)
+    p = np.full(50, 0.5) * np.diag(Qp)
+    r = O.inner(Qp, bp, p, x0, trace_len=200)
+    tx = r["trace_x"][: min(200, r["steps"] + 1)]
+    assert np.all(tx >= 0.0) and np.all(tx <= 1.0)
+    ta = r["trace_alpha"][: min(200, r["steps"])]
+    assert np.all(ta > 0)
+
+
+def test_bb_steps_follow_alternation():
+    """Eq. (bb1): odd k uses s^T s / s^T y, even k uses s^T y / y^T y of the last pair."""
+    Q, b = I.random_ubqp(40, 0.3, 4)
+    Qp, bp, _ = O.reformulate(Q, b, None)
+    x0 = O.initial_point(Qp, bp)
+    p = 0.3 * np.diag(Qp)
+    r = O.inner(Qp, bp, p, x0, trace_len=30)
+    X, A = r["trace_x"], r["trace_alpha"]
+    Qb = Qp - np.diag(p)
+    for k in range(1, min(25, r["steps"])):
+        s = X[k] - X[k - 1]
+        y = 2 * Qb @ s
+        if s @ y <= 0:
+            continue
+        want = (s @ s) / (s @ y) if k % 2 == 1 else (s @ y) / (y @ y)
+        assert A[k] == pytest.approx(want, rel=1e-9)
+
+
+def test_lemma_4_2_large_penalty_gives_binary_points():
+    """Lemma 4.2 / Thm 4.3: with p > diag(Q) every local minimiser is binary, so the
+    subproblem solver started anywhere stops at a binary point."""
+    Q, b = I.random_ubqp(16, 0.3, 7)
+    Qp, bp, _ = O.reformulate(Q, b, None)
+    p = np.diag(Qp) + 1.0
+    rng = np.random.default_rng(7)
+    for _ in range(10):
+        r = O.inner(Qp, bp, p, rng.random(16))
+        assert np.all((r["x"] == 0.0) | (r["x"] == 1.0))
+
+
+def test_theorem_4_3_box_minimum_not_below_binary_optimum():
+    """Lemma 4.1 with Thm 4.3: min over the box of h(., p) <= min f, with equality once
+    p > diag(Q); sampled box points never go below f* then."""
+    Q, b = I.random_ubqp(14, 0.4, 8, b_range=(-20, 20))
+    fstar, _ = enumerate_min(Q, b)
+    p = np.diag(Q) + 1.0
+    X = np.random.default_rng(8).random((20000, 14))
+    H = np.einsum("ij,jk,ik->i", X, Q, X) + X @ b + ((X - X * X) * p).sum(1)
+    assert H.min() >= fstar - 1e-9
+
+
+def test_ppa_descent_lemma_4_4():
+    """Lemma 4.4: h(x^{k+1}) <= h(x^k) - d^T (H_p - Q + P*) d along Alg. 1, and
+    H_p + P is positive semidefinite (Sec. 3.1)."""
+    Q, b = I.random_ubqp(40, 0.3, 9)
+    Qp, bp, _ = O.reformulate(Q, b, I.perturbation(Q, 9))
+    x0 = O.initial_point(Qp, bp)
+    p = 0.7 * np.diag(Qp)
+    o = O.opts(method=1)
+    r = O.inner(Qp, bp, p, x0, o, trace_len=60)
+    r_abs = np.abs(Qp).sum(1)
+    hp = np.maximum(r_abs - p, 1e-8 * max(1.0, r_abs.max()))
+    M = np.diag(hp) - Qp + np.diag(p)
+    assert np.linalg.eigvalsh(M)[0] >= -1e-9 * np.abs(M).max()
+    X = r["trace_x"][: min(60, r["steps"] + 1)]
+    for k in range(len(X) - 1):
+        d = X[k + 1] - X[k]
+        h0 = O.penalized(Qp, bp, p, X[k], False)
+        h1 = O.penalized(Qp, bp, p, X[k + 1], False)
+        assert h1 <= h0 - d @ M @ d + 1e-8 * abs(h0)
+
+
+# ---- Alg. 3 ------------------------------------------------------------------------
+
+def test_solve_never_below_enumerated_optimum_and_mostly_reaches_it():
+    """Global quality: the rounded objective is never below the exhaustive optimum
+    (tests/golden), is exactly f(x_best), and the mean gap stays small (Table 2
+    reports 0.06% at n = 20 on the paper's own instances)."""
+    cases = json.load(open(GOLD))["cases"]
+    gaps = []
+    for c in cases:
+        Q, b = I.random_ubqp(c["n"], 0.1, c["seed"])
+        xb, f, st = O.solve(Q, b, I.perturbation(Q, c["seed"]))
+        assert f >= c["f_star"]
+        assert f == O.objective(Q, b, xb)
+        gaps.append(abs(f - c["f_star"]) / abs(c["f_star"]))
+    assert np.mean(gaps) < 0.01
+    assert sum(g == 0 for g in gaps) >= 15
+
+
+def test_solve_terminates_at_binary_point():
+    Q, b = I.c1_instance()
+    xb, f, st = O.solve(Q, b, I.perturbation(Q, 0))
+    assert st["status"] == 0 and st["final_binarity"] <= 1e-5
+    assert st["outer"] < 1000
+    assert np.all(np.asarray(st["inner_hist"]) <= 10000)
+
+
+def test_solve_random_start_path():
+    Q, b = I.random_ubqp(18, 0.2, 11)
+    xs = I.random_starts(18, 1, 11)[0]
+    fstar, _ = enumerate_min(Q, b)
+    xb, f, st = O.solve(Q, b, I.perturbation(Q, 11), x_start=xs)
+    assert f >= fstar and st["status"] == 0
