@@ -1,0 +1,270 @@
+"""Benchmark of the vectorized PSDP solver (arXiv 2408.04875) on one node.
+
+A step is one pass of the whole method (initialization, penalty updates with their
+lambda_min solves, the PABB inner loops, rounding and exact evaluation) over one batch
+of synthetic instances: the plain-PSDP sweep, n in {250, 500, 1000, 2500} x 10 seeded
+instances (density 0.1, integers uniform in [-100, 100], b = 0), FP32 path, one start
+per instance.  With N ranks (torchrun) every rank solves its own 40 instances (seeds
+offset by 10 * rank): weak scaling, no collective on the data path.
+
+Metric: inner projected-gradient iterations x n per second over all lanes (each
+gradient evaluation of Alg. 2 on a lane of size n counts n).  Inputs are resident in HBM
+when the timed region starts; the FP32 matrices of one batch (302 MB) exceed the 129 MB
+L2, so no flush is needed between steps.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "inner PG iters/s (batch×n) and time-to-oracle-objective vs plain FP32 path"
+UNIT = "lane-var-updates/s"
+SIZES = (250, 500, 1000, 2500)
+SEEDS_PER_SIZE = 10
+WORKLOAD = ("plain PSDP sweep: n in {250,500,1000,2500} x 10 seeded instances, density 0.1, "
+            "integers in [-100,100], b=0, FP32, 1 start")
+
+
+def _env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def _instances(rank: int, sizes=SIZES, seeds=SEEDS_PER_SIZE):
+    from paper_2408_04875_gb300 import instances as I
+    Qs, mus = [], []
+    for n in sizes:
+        for k in range(seeds):
+            seed = SEEDS_PER_SIZE * rank + k
+            Q, _ = I.c2_instance(n, seed)
+            Qs.append(Q)
+            mus.append(I.perturbation(Q, seed))
+    return Qs, mus
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks, power, throttle reasons)."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(budget_s: float = 12.0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the same
+    workload: the n = 250 instances of the sweep, solved one after another until the
+    time budget is used."""
+    import oracle as O
+    from paper_2408_04875_gb300 import instances as I
+    O.build()
+    done, work, t0 = 0, 0, time.perf_counter()
+    for seed in range(SEEDS_PER_SIZE):
+        Q, _ = I.c2_instance(250, seed)
+        _, _, st = O.solve(Q, None, I.perturbation(Q, seed))
+        work += st["grad_evals"] * 250
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": work / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of the 10 n=250 instances of the sweep, full solves, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    steps = []
+    for i in range(args.warmup + args.steps):
+        b = cpu_baseline(budget_s=10.0)
+        if i >= args.warmup:
+            steps.append(b)
+    value = statistics.mean(s["value"] for s in steps)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "impl": "reference", "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference_sample": steps[-1]["sample"]},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": steps[-1]["sample"], "value": value,
+                             "unit": UNIT},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2408_04875_gb300 as ub
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    Qs, mus = _instances(rank, args.sizes, args.seeds)
+    Qd = [torch.from_numpy(Q).cuda() for Q in Qs]
+    Md = [torch.from_numpy(m).cuda() for m in mus]
+    torch.cuda.synchronize()
+    kw = dict(profile_kernels=0 if args.no_profile else 1)
+    if args.max_outer is not None:
+        kw["max_outer"] = args.max_outer
+    for _ in range(args.warmup):
+        ub.solve_batched(Qd, None, Md, **kw)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    stats = []
+    objs = None
+    for _ in range(args.steps):
+        _, objs, st = ub.solve_batched(Qd, None, Md, **kw)
+        stats.append(st)
+    e1.record()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    work = sum(s["var_updates"] for s in stats)
+    work_t = torch.tensor([float(work)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(work_t)
+    value = float(work_t.item()) / (ms_max * 1e-3)
+
+    # end to end through the public API with host buffers (H2D of Q and mu, D2H of x, f)
+    st_e2e, e2e_s = None, None
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        _, _, st_e2e = ub.solve_batched(Qs, None, mus, **{k: v for k, v in kw.items() if k != "profile_kernels"})
+        e2e_s = time.perf_counter() - t0
+    h2d = sum(Q.nbytes + m.nbytes for Q, m in zip(Qs, mus))
+    d2h = sum(Q.shape[0] for Q in Qs) + 8 * len(Qs)
+
+    # roofline of the dominant kernel (phase-A GEMV), CUDA events around every launch
+    pa_ms = sum(s["phase_a_ms"] for s in stats)
+    pa_n = sum(s["phase_a_launches"] for s in stats)
+    pa_bytes = sum(s["phase_a_bytes"] for s in stats)
+    peak, peak_kind = _peaks()
+    achieved = pa_bytes / (pa_ms * 1e-3) / 1e9 if pa_ms > 0 else None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "instances_per_gpu": len(Qs), "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (302 MB of FP32 Q per batch); no flush",
+                       "time_to_solution_ms": ms_max / args.steps,
+                       "inner_iters_per_step": stats[-1]["inner_iters"], "outer_steps_per_step": stats[-1]["outer_steps"],
+                       "ticks_per_step": stats[-1]["ticks"], "best_objectives_first3": [float(v) for v in objs[:3]]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "phase_a_gemv_kernel", "launches": pa_n,
+                         "avg_launch_us": pa_ms * 1e3 / max(pa_n, 1),
+                         "algorithmic_bytes_per_launch": pa_bytes / max(pa_n, 1), "peak_kind": peak_kind},
+            "e2e": None if st_e2e is None else {"value": st_e2e["var_updates"] / e2e_s, "unit": UNIT,
+                                                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+            "clocks": clocks,
+        }
+        if args.sizes != SIZES or args.seeds != SEEDS_PER_SIZE or args.max_outer is not None:
+            line["config"]["workload"] = (f"profiling case: n in {list(args.sizes)} x {args.seeds} seeds, "
+                                          f"max_outer={args.max_outer}")
+        line["cpu_baseline"] = None if args.no_cpu_baseline else cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    # profiling knobs (defaults are the benchmark workload)
+    ap.add_argument("--sizes", type=lambda v: tuple(int(x) for x in v.split(",")), default=SIZES)
+    ap.add_argument("--seeds", type=int, default=SEEDS_PER_SIZE)
+    ap.add_argument("--max-outer", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * ubqp.h - C ABI of the GB300 (sm_103a) implementation of the vectorized
+ * positive-semidefinite-penalty (PSDP) method for unconstrained binary quadratic
+ * programs, arXiv 2408.04875 (Huo & Gu):
+ *
+ *     min  f(x) = x^T Q x + b^T x     over x in {0,1}^n,  Q symmetric   (Eq. (bqp))
+ *
+ * The library runs Alg. 3 of the paper on one GPU: initialization (Sec. 3.5:
+ * reformulation with gamma, random symmetric perturbation, x^0 from Eq. (gamma)),
+ * the penalty update p += alpha z with alpha from Lemma 3.1 / Eq. (eq:alpha1), the
+ * subproblem solver (Alg. 2, projected alternating Barzilai-Borwein, or Alg. 1,
+ * proximal point) with the KKT stopping test of Eq. (cret), then rounding and exact
+ * evaluation of every candidate, keeping the best.
+ *
+ * Conventions shared by all entry points
+ *   - Matrices are dense, row-major, n x n, FP64 unless stated otherwise.
+ *   - Pointers may be host or device memory unless stated otherwise; the library
+ *     detects which with cudaPointerGetAttributes.  It never keeps a caller pointer
+ *     after returning and never frees caller memory.
+ *   - Every call returns a ubqp_status.  Negative values are errors (outputs are
+ *     then unspecified); positive values are warnings (outputs valid).  Detail for the
+ *     last failing call of the calling thread is available from ubqp_last_error().
+ *     The library never aborts, traps or prints.
+ *   - All GPU work runs on opts->stream (NULL = the legacy default stream) of the
+ *     current device; the entry points synchronize that stream before returning.
+ *   - Every device-side wait is bounded; a wait that runs out returns UBQP_ETIMEOUT
+ *     and leaves the device usable.
+ */
+#ifndef UBQP_H
+#define UBQP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    UBQP_OK = 0,
+    UBQP_EINVAL = -1,      /* bad argument (size, NULL pointer, option out of range) */
+    UBQP_ENOTSYM = -2,     /* Q is not symmetric                                     */
+    UBQP_ENONFINITE = -3,  /* Q or b holds NaN or Inf                                */
+    UBQP_ECUDA = -4,       /* a CUDA runtime or driver call failed                   */
+    UBQP_ENOMEM = -5,      /* device allocation failed                               */
+    UBQP_ETIMEOUT = -6,    /* a bounded device wait ran out                          */
+    UBQP_ENOTSUP = -7,     /* request not supported on this device / configuration  */
+    UBQP_EMAXITER = 1      /* warning: some instance hit max_outer; results valid    */
+} ubqp_status;
+
+enum { UBQP_PABB = 0, UBQP_PPA = 1 };                 /* subproblem solver        */
+enum { UBQP_FP32 = 0, UBQP_BF16X2_TC = 1, UBQP_BF16_TC = 2 };  /* matvec precision */
+enum { UBQP_DTYPE_F32 = 0, UBQP_DTYPE_F64 = 1 };
+
+#define UBQP_HIST_BINS 101   /* inner-iteration histogram: bins of 100 steps, last = 10000+ */
+
+/* Counters of one solve (sums over every lane = instance x start). */
+typedef struct {
+    int64_t inner_iters;     /* gradient evaluations of the subproblem solver         */
+    int64_t inner_steps;     /* projected steps (Alg. 1/2 iterations)                 */
+    int64_t var_updates;     /* sum over lanes of inner_iters * n                     */
+    int64_t outer_steps;     /* subproblems solved (penalty updates)                  */
+    int64_t lobpcg_iters;    /* eigen-solver iterations for lambda_min                */
+    int64_t jacobi_iters;    /* sweeps spent on x^0                                   */
+    int64_t floor_steps;     /* penalty steps that used the resolution floor          */
+    int64_t ticks;           /* device ticks (one matvec pass over all active lanes)  */
+    int64_t lanes;           /* instance x start pairs                                */
+    int64_t lanes_capped;    /* lanes that stopped at max_outer                        */
+    double ms_device;        /* device time of the iteration loop (CUDA events)        */
+    double ms_total;         /* whole call, host wall clock                           */
+    double phase_a_ms;       /* summed duration of the matvec (phase A) launches,      */
+                             /* CUDA events around each launch (profile_kernels only)  */
+    int64_t phase_a_launches;/* phase-A launches timed                                 */
+    int64_t phase_a_bytes;   /* algorithmic bytes of those launches: stored matrix     */
+                             /* entries of every active lane once, plus its vectors    */
+    int64_t kernel_launches; /* launches of this library's kernels during the call      */
+    int64_t inner_hist[UBQP_HIST_BINS]; /* projected steps per subproblem (Fig. 5)   */
+} ubqp_stats;
+
+/* Options; ubqp_opts_default() fills the paper's settings and this library's readings
+ * of the points the paper leaves open. */
+typedef struct {
+    int method;              /* UBQP_PABB (Alg. 2, default) or UBQP_PPA (Alg. 1)     */
+    int max_outer;           /* 1000 penalty updates (Sec. 5)                          */
+    int max_inner;           /* 10000 subproblem iterations (Sec. 5)                   */
+    double tol_inner;        /* delta of Eq. (cret): 1e-5                              */
+    double tol_outer;        /* Alg. 3 while-test on max_i min(x_i, 1-x_i): 1e-5       */
+    double eta;              /* Eq. (eq:alpha1), 0 < eta < 1: 0.9                      */
+    double gamma_margin;     /* gamma_i = 2 sum_j |Q_ij| + |b_i| + margin: 1.0         */
+    double alpha_min;        /* clamp of the BB step: 1e-10                             */
+    double alpha_max;        /*                        1e10                             */
+    double tau_z;            /* coordinates with x - x^2 > tau_z enter lambda_min: 1e-12 */
+    double eps_hp_rel;       /* PPA epsilon relative to max row sum: 1e-8              */
+    double lambda_floor_rel; /* resolution floor F = this * tol_inner * rho: 4.0        */
+    double sigma_rel;        /* perturbation std-dev / max|Q_ij| (i != j): 1e-3; 0 = off */
+    uint64_t seed;           /* seeds the library's own draws (perturbation, starts)  */
+    int restarts;            /* starts per instance: 1 = x^0 of Eq. (gamma) only;      */
+                             /* R > 1 adds R-1 starts uniform in [0,1]^n              */
+    int precision;           /* UBQP_FP32 (default), UBQP_BF16X2_TC, UBQP_BF16_TC      */
+    int lobpcg_max_iter;     /* cap of the lambda_min eigen-solver: 64                 */
+    double lobpcg_tol;       /* relative change of the Ritz value to stop: 1e-4        */
+    int jacobi_max_iter;     /* sweeps for x^0: 60                                      */
+    int max_ticks_per_sync;  /* ticks launched between host checks: 64                 */
+    int profile_kernels;     /* 1: time every phase-A launch with CUDA events: 0       */
+    void* stream;            /* cudaStream_t, NULL = default stream                    */
+    const double* const* mu; /* optional perturbations, one n x n matrix per instance   */
+                             /* (symmetric); NULL = drawn from seed when sigma_rel > 0 */
+    const double* const* x_starts; /* optional extra starts, one (R-1) x n block per   */
+                             /* instance; NULL = drawn from seed                        */
+    ubqp_stats* stats;       /* optional output (host memory)                          */
+} ubqp_opts;
+
+/* Fills *o with the defaults listed above. */
+void ubqp_opts_default(ubqp_opts* o);
+
+/* Human-readable name of a status code (static storage). */
+const char* ubqp_status_string(int status);
+
+/* Detail on the last error of the calling thread (static thread-local storage). */
+const char* ubqp_last_error(void);
+
+/*
+ * ubqp_solve - Alg. 3 for one instance.
+ *   Q      n x n symmetric (checked: |Q_ij - Q_ji| <= 1e-12 max|Q|), host or device.
+ *   b      n, host or device; NULL means b = 0.
+ *   n      1 <= n <= 65536.
+ *   o      options; NULL means defaults.
+ *   x_out  n bytes (0/1), host or device: the best rounded point found.
+ *   obj_out 1 double, host or device: f(x_out) of the ORIGINAL Q, b, evaluated in FP64
+ *          (exact for integer data with |f| < 2^53).
+ * Returns UBQP_OK, UBQP_EMAXITER (warning), or a negative error.
+ * The same as ubqp_solve_batched with num = 1.
+ */
+int ubqp_solve(const double* Q, const double* b, int64_t n, const ubqp_opts* o,
+               uint8_t* x_out, double* obj_out);
+
+/*
+ * ubqp_solve_batched - Alg. 3 for num independent instances of uneven size, each with
+ * o->restarts starts, all advanced together on the device (one lane per instance x
+ * start; lanes of one instance share its Q).
+ *   num    >= 1 instances;  n[i], Q[i], b[i] (b may be NULL or hold NULL entries) as
+ *          in ubqp_solve.
+ *   x_out[i] n[i] bytes, obj_out num doubles: per instance, the best rounded point over
+ *          all of its starts and outer steps and its exact objective.
+ * With o->precision = UBQP_BF16X2_TC / UBQP_BF16_TC the matvecs of all starts of an
+ * instance run as one BF16 tensor-core contraction (Q off-diagonal in BF16, the iterate
+ * split into two BF16 terms for X2, FP32 accumulation); the perturbation then touches
+ * only the diagonal (kept in FP32), since BF16 cannot carry it off the diagonal.
+ */
+int ubqp_solve_batched(int32_t num, const int64_t* n, const double* const* Q,
+                       const double* const* b, const ubqp_opts* o, uint8_t* const* x_out,
+                       double* obj_out);
+
+/*
+ * ubqp_penalized_eval - the penalized objective of Sec. 4.1, problem (p), and its
+ * gradient (Sec. 3.1, used as g^k in Alg. 2), for `batch` points sharing Q, b, p:
+ *     h_r = x_r^T Q x_r + b^T x_r + sum_i p_i (x_ri - x_ri^2)
+ *     g_r = 2 (Q - Diag p) x_r + b + p
+ * All pointers are DEVICE memory of element type dtype (UBQP_DTYPE_F32 / _F64):
+ *   Q n x n row-major, b and p n (either may be NULL = 0), x batch x n row-major,
+ *   h_out batch (may be NULL), g_out batch x n (may be NULL).
+ * stream: cudaStream_t (NULL = default).  Runs the same gradient kernel the inner loop
+ * uses.  Scratch is allocated and freed inside the call.
+ */
+int ubqp_penalized_eval(const void* Q, const void* b, const void* p, const void* x, int64_t n,
+                        int64_t batch, int dtype, void* h_out, void* g_out, void* stream);
+
+/*
+ * ubqp_inner_run - test entry: Alg. 2 (or Alg. 1 when o->method = UBQP_PPA) on the
+ * subproblem (p1) with a GIVEN reformulated matrix Qp = Q' (n x n, diagonal included),
+ * bp = b', penalty p and start x0 (all FP64, host or device), on the FP32 GPU path.
+ *   trace_len  iterates to record; trace_x (trace_len x n) receives x_k and trace_alpha
+ *              (trace_len) the step used at iteration k (host or device; may be NULL).
+ *   x_out (n), steps_out, exit_out (0 KKT test met, 1 iteration cap, 2 zero step).
+ */
+int ubqp_inner_run(const double* Qp, const double* bp, const double* p, const double* x0,
+                   int64_t n, const ubqp_opts* o, int32_t trace_len, double* trace_x,
+                   double* trace_alpha, double* x_out, int32_t* steps_out, int32_t* exit_out);
+
+/*
+ * ubqp_penalty_probe - test entry: one penalty step of Sec. 3.4 on the GPU for a given
+ * state (Qp, bp, p, x as in ubqp_inner_run): lambda_min of Z^-1/2 Qbar_II Z^-1/2 by the
+ * device eigen-solver, the step alpha (Eq. (eq:alpha1) with the resolution floor, no
+ * previous floor steps), |I| and the eigen-solver iterations.  Outputs are host memory.
+ */
+int ubqp_penalty_probe(const double* Qp, const double* bp, const double* p, const double* x,
+                       int64_t n, const ubqp_opts* o, double* lambda_out, double* alpha_out,
+                       int32_t* n_active_out, int32_t* iters_out);
+
+/*
+ * ubqp_initial_point - test entry: the device initialization of Sec. 3.5 for one instance
+ * (perturbation mu, host/device n x n or NULL; reformulation; x^0 of Eq. (gamma) by
+ * Jacobi sweeps on the FP32 path).  x0_out (n) and gamma_out (n, may be NULL), host or
+ * device, FP64.
+ */
+int ubqp_initial_point(const double* Q, const double* b, const double* mu, int64_t n,
+                       const ubqp_opts* o, double* x0_out, double* gamma_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UBQP_H */

@@ -1,0 +1,1025 @@
+// Host driver and C ABI of the vectorized PSDP solver (see include/ubqp.h).
+//
+// One call = one Solver: stage the inputs on the device, validate them, reformulate
+// every instance (Sec. 3.5), lay out one lane per (instance, start), then advance all
+// lanes in ticks (phase A matvec + phase B update) until every lane is done.  Ticks are
+// enqueued in batches captured once into a CUDA graph; the host only reads one counter
+// per batch.  Finally the best lane of every instance is selected on the device and its
+// rounded point and exact objective are returned.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/ubqp.h"
+#include "ubqp_engine.cuh"
+
+namespace ubqp {
+
+static thread_local char g_last_error[512] = "";
+
+static void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+
+#define UBQP_CK(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return e_ == cudaErrorMemoryAllocation ? UBQP_ENOMEM : UBQP_ECUDA;               \
+        }                                                                                    \
+    } while (0)
+
+static bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// one device allocation carved into 256-byte aligned pieces
+class Arena {
+  public:
+    size_t reserve(size_t bytes)
+    {
+        size_t off = size_;
+        size_ += round_up(bytes ? bytes : 1, 256);
+        return off;
+    }
+    int commit()
+    {
+        if (size_ == 0) return UBQP_OK;
+        cudaError_t e = cudaMalloc(&base_, size_);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("cudaMalloc of %zu bytes failed: %s", size_, cudaGetErrorString(e));
+            base_ = nullptr;
+            return e == cudaErrorMemoryAllocation ? UBQP_ENOMEM : UBQP_ECUDA;
+        }
+        return UBQP_OK;
+    }
+    template <class T>
+    T* at(size_t off) const
+    {
+        return reinterpret_cast<T*>(static_cast<char*>(base_) + off);
+    }
+    size_t size() const { return size_; }
+    ~Arena()
+    {
+        if (base_) cudaFree(base_);
+    }
+
+  private:
+    void* base_ = nullptr;
+    size_t size_ = 0;
+};
+
+static Params make_params(const ubqp_opts& o, int64_t* hist)
+{
+    Params P;
+    P.max_outer = o.max_outer;
+    P.max_inner = o.max_inner;
+    P.lob_max = o.lobpcg_max_iter;
+    P.jac_max = o.jacobi_max_iter;
+    P.tol_inner = (float)o.tol_inner;
+    P.tol_outer = (float)o.tol_outer;
+    P.eta = (float)o.eta;
+    P.alpha_min = (float)o.alpha_min;
+    P.alpha_max = (float)o.alpha_max;
+    P.tau_z = (float)o.tau_z;
+    P.eps_hp_rel = (float)o.eps_hp_rel;
+    P.lambda_floor_rel = (float)o.lambda_floor_rel;
+    P.lob_tol = (float)o.lobpcg_tol;
+    P.jac_tol = 2e-7f;
+    P.hist = hist;
+    P.bytes = nullptr;
+    return P;
+}
+
+static int check_opts(const ubqp_opts& o)
+{
+    if (o.method != UBQP_PABB && o.method != UBQP_PPA) { set_error("method must be UBQP_PABB or UBQP_PPA"); return UBQP_EINVAL; }
+    if (o.max_outer < 0 || o.max_inner < 0) { set_error("max_outer/max_inner must be >= 0"); return UBQP_EINVAL; }
+    if (!(o.eta > 0.0 && o.eta < 1.0)) { set_error("eta must lie in (0, 1) (Eq. (eq:alpha1))"); return UBQP_EINVAL; }
+    if (!(o.tol_inner > 0.0) || !(o.tol_outer >= 0.0)) { set_error("tolerances must be positive"); return UBQP_EINVAL; }
+    if (!(o.alpha_min > 0.0) || !(o.alpha_max >= o.alpha_min)) { set_error("bad BB step clamp"); return UBQP_EINVAL; }
+    if (o.restarts < 1 || o.restarts > 4096) { set_error("restarts must be in [1, 4096]"); return UBQP_EINVAL; }
+    if (o.precision != UBQP_FP32 && o.precision != UBQP_BF16X2_TC && o.precision != UBQP_BF16_TC) {
+        set_error("unknown precision");
+        return UBQP_EINVAL;
+    }
+    if (o.lobpcg_max_iter < 1 || o.jacobi_max_iter < 1) { set_error("iteration caps must be >= 1"); return UBQP_EINVAL; }
+    if (o.max_ticks_per_sync < 1 || o.max_ticks_per_sync > 4096) { set_error("max_ticks_per_sync out of range"); return UBQP_EINVAL; }
+    if (!(o.sigma_rel >= 0.0) || !(o.gamma_margin > 0.0)) { set_error("sigma_rel >= 0 and gamma_margin > 0 required"); return UBQP_EINVAL; }
+    return UBQP_OK;
+}
+
+// ---------------------------------------------------------------------------------
+struct InstIn {
+    int64_t n;
+    const double* Q;
+    const double* b;
+    const double* mu;
+    const double* starts;   // (R-1) x n extra starts or null
+    bool reformulated;      // Q, b are already Q', b' (test entries): no gamma, no mu
+};
+
+struct LaneIn {
+    int inst, restart, phase, start_kind;
+    const double* x0;       // host or device, n doubles, or null
+    const double* p0;
+    int stop_after, trace_len;
+};
+
+struct InstDev {
+    int64_t n;
+    int ld;
+    const double *Q, *b, *mu, *starts;
+    size_t o_Q, o_b, o_mu, o_starts;  // staging offsets (when host data)
+    bool Q_host, b_host, mu_host, starts_host;
+    size_t o_Qoff, o_Qbf, o_Qeval, o_d, o_bp, o_oabs, o_rabs, o_tsum, o_borig, o_qdb, o_gamma;
+    size_t o_Uhi, o_Ulo;
+    int lane0, nl;
+};
+
+class Solver {
+  public:
+    Solver(const ubqp_opts& o) : o_(o) {}
+    ~Solver()
+    {
+        if (gexec_) cudaGraphExecDestroy(gexec_);
+        if (graph_) cudaGraphDestroy(graph_);
+        if (h_active_) cudaFreeHost(h_active_);
+        if (ev0_) cudaEventDestroy(ev0_);
+        if (ev1_) cudaEventDestroy(ev1_);
+        for (auto e : evA_) cudaEventDestroy(e);
+        if (stream_) {
+            cudaStreamSynchronize(stream_);
+            cudaStreamDestroy(stream_);
+        }
+    }
+
+    int setup(const std::vector<InstIn>& insts, const std::vector<LaneIn>& lanes, bool tc)
+    {
+        tc_ = tc;
+        int rc = check_opts(o_);
+        if (rc) return rc;
+        UBQP_CK(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+        cudaStream_t user = (cudaStream_t)o_.stream;
+        {
+            cudaEvent_t e;
+            UBQP_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            cudaEventRecord(e, user);
+            cudaStreamWaitEvent(stream_, e, 0);
+            cudaEventDestroy(e);
+        }
+        UBQP_CK(cudaEventCreate(&ev0_));
+        UBQP_CK(cudaEventCreate(&ev1_));
+        int dev = 0;
+        UBQP_CK(cudaGetDevice(&dev));
+        UBQP_CK(cudaDeviceGetAttribute(&num_sms_, cudaDevAttrMultiProcessorCount, dev));
+
+        // ---- layout
+        inst_.resize(insts.size());
+        int max_ld = 32;
+        for (size_t t = 0; t < insts.size(); ++t) {
+            const InstIn& in = insts[t];
+            InstDev& I = inst_[t];
+            I.n = in.n;
+            I.ld = (int)round_up((size_t)in.n, tc ? 128 : 32);
+            max_ld = std::max(max_ld, I.ld);
+            const size_t n = (size_t)in.n, ld = (size_t)I.ld;
+            I.Q_host = !is_device_ptr(in.Q);
+            I.b_host = in.b && !is_device_ptr(in.b);
+            I.mu_host = in.mu && !is_device_ptr(in.mu);
+            I.starts_host = in.starts && !is_device_ptr(in.starts);
+            I.o_Q = I.Q_host ? ar_.reserve(n * n * 8) : 0;
+            I.o_b = I.b_host ? ar_.reserve(n * 8) : 0;
+            I.o_mu = I.mu_host ? ar_.reserve(n * n * 8) : 0;
+            I.o_starts = 0;
+            I.o_Qoff = tc ? 0 : ar_.reserve(n * ld * 4);
+            I.o_Qbf = tc ? ar_.reserve(ld * ld * 2) : 0;
+            I.o_Qeval = tc ? 0 : ar_.reserve(n * ld * 8);
+            I.o_d = ar_.reserve(ld * 4);
+            I.o_bp = ar_.reserve(ld * 4);
+            I.o_oabs = ar_.reserve(ld * 4);
+            I.o_rabs = ar_.reserve(ld * 4);
+            I.o_tsum = ar_.reserve(ld * 4);
+            I.o_borig = ar_.reserve(ld * 8);
+            I.o_qdb = ar_.reserve(ld * 8);
+            I.o_gamma = ar_.reserve(ld * 8);
+            I.lane0 = -1;
+            I.nl = 0;
+        }
+        max_ld_ = max_ld;
+        o_scal_ = ar_.reserve(insts.size() * 4 * sizeof(float));
+        o_valid_ = ar_.reserve(insts.size() * 4 * sizeof(float));
+        o_inexact_ = ar_.reserve(insts.size() * sizeof(int));
+        o_hist_ = ar_.reserve(UBQP_HIST_BINS * sizeof(int64_t));
+        o_active_ = ar_.reserve(sizeof(int32_t));
+        o_bytes_ = ar_.reserve(sizeof(unsigned long long));
+
+        // lanes: rows per phase-A item for the GEMV path
+        int64_t total_rows = 0;
+        for (const LaneIn& l : lanes) total_rows += insts[l.inst].n;
+        int target_items = 8 * num_sms_;
+        int rb = 8;
+        while (rb < 256 && total_rows / rb > target_items) rb *= 2;
+        rows_per_item_ = rb;
+
+        lanes_.assign(lanes.size(), LaneDev());
+        lane_init_.resize(lanes.size());
+        o_vec_.resize(lanes.size());
+        o_bx_.resize(lanes.size());
+        o_part_.resize(lanes.size());
+        o_trace_x_.assign(lanes.size(), 0);
+        o_trace_a_.assign(lanes.size(), 0);
+        o_x0_.assign(lanes.size(), SIZE_MAX);
+        o_p0_.assign(lanes.size(), SIZE_MAX);
+        int64_t nitems = 0;
+        for (size_t l = 0; l < lanes.size(); ++l) {
+            const LaneIn& in = lanes[l];
+            InstDev& I = inst_[in.inst];
+            if (I.lane0 < 0) I.lane0 = (int)l;
+            I.nl += 1;
+            LaneDev& L = lanes_[l];
+            L.n = (int)I.n;
+            L.ld = I.ld;
+            L.mode = tc ? MODE_TC : MODE_GEMV;
+            L.nblk = tc ? (int)(I.ld / 128) : (int)((I.n + rb - 1) / rb);
+            L.method = o_.method;
+            L.stop_after = in.stop_after;
+            L.restart = in.restart;
+            L.trace_len = in.trace_len;
+            if (!tc) nitems += L.nblk;
+            o_vec_[l] = ar_.reserve((size_t)NVEC * I.ld * 4);
+            o_bx_[l] = ar_.reserve((size_t)I.ld);
+            o_part_[l] = ar_.reserve((size_t)L.nblk * sizeof(Partial));
+            if (in.trace_len > 0) {
+                o_trace_x_[l] = ar_.reserve((size_t)in.trace_len * I.n * 4);
+                o_trace_a_[l] = ar_.reserve((size_t)in.trace_len * 4);
+            }
+            if (in.x0) o_x0_[l] = is_device_ptr(in.x0) ? SIZE_MAX - 1 : ar_.reserve((size_t)I.n * 8);
+            if (in.p0) o_p0_[l] = is_device_ptr(in.p0) ? SIZE_MAX - 1 : ar_.reserve((size_t)I.n * 8);
+        }
+        if (tc) {
+            for (InstDev& I : inst_) {
+                int rpad = (int)round_up((size_t)I.nl, 16);
+                I.o_Uhi = ar_.reserve((size_t)rpad * I.ld * 2);
+                I.o_Ulo = o_.precision == UBQP_BF16X2_TC ? ar_.reserve((size_t)rpad * I.ld * 2) : 0;
+            }
+        }
+        o_states_ = ar_.reserve(lanes.size() * sizeof(LaneState));
+        o_lanes_ = ar_.reserve(lanes.size() * sizeof(LaneDev));
+        o_linit_ = ar_.reserve(lanes.size() * sizeof(LaneInit));
+        o_items_ = ar_.reserve((size_t)std::max<int64_t>(nitems, 1) * sizeof(int2));
+        o_final_lane0_ = ar_.reserve(insts.size() * 4);
+        o_final_nl_ = ar_.reserve(insts.size() * 4);
+        o_final_obj_ = ar_.reserve(insts.size() * 8);
+        o_final_best_ = ar_.reserve(insts.size() * 4);
+        o_final_xptr_ = ar_.reserve(insts.size() * sizeof(void*));
+        o_final_xbuf_ = 0;
+        size_t xbuf = 0;
+        for (InstDev& I : inst_) xbuf += round_up((size_t)I.n, 256);
+        o_final_xbuf_ = ar_.reserve(xbuf);
+        nitems_ = (int)nitems;
+        rc = ar_.commit();
+        if (rc) return rc;
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_hist_), 0, UBQP_HIST_BINS * sizeof(int64_t), stream_));
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_bytes_), 0, sizeof(unsigned long long), stream_));
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_valid_), 0, insts.size() * 4 * sizeof(float), stream_));
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_scal_), 0, insts.size() * 4 * sizeof(float), stream_));
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_inexact_), 0, insts.size() * sizeof(int), stream_));
+
+        // ---- stage inputs
+        for (size_t t = 0; t < insts.size(); ++t) {
+            const InstIn& in = insts[t];
+            InstDev& I = inst_[t];
+            const size_t n = (size_t)in.n;
+            I.Q = in.Q;
+            I.b = in.b;
+            I.mu = in.mu;
+            I.starts = in.starts;
+            if (I.Q_host) {
+                UBQP_CK(cudaMemcpyAsync(ar_.at<double>(I.o_Q), in.Q, n * n * 8, cudaMemcpyHostToDevice, stream_));
+                I.Q = ar_.at<double>(I.o_Q);
+            }
+            if (I.b_host) {
+                UBQP_CK(cudaMemcpyAsync(ar_.at<double>(I.o_b), in.b, n * 8, cudaMemcpyHostToDevice, stream_));
+                I.b = ar_.at<double>(I.o_b);
+            }
+            if (I.mu_host) {
+                UBQP_CK(cudaMemcpyAsync(ar_.at<double>(I.o_mu), in.mu, n * n * 8, cudaMemcpyHostToDevice, stream_));
+                I.mu = ar_.at<double>(I.o_mu);
+            }
+        }
+        // ---- validate (Q symmetric, finite)
+        for (size_t t = 0; t < insts.size(); ++t) {
+            UBQP_CK(launch_validate(inst_[t].Q, inst_[t].b, (int)inst_[t].n, ar_.at<float>(o_valid_) + 4 * t, stream_));
+            launches_ += 1;
+        }
+        std::vector<float> val(insts.size() * 4);
+        UBQP_CK(cudaMemcpyAsync(val.data(), ar_.at<float>(o_valid_), val.size() * 4, cudaMemcpyDeviceToHost, stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        for (size_t t = 0; t < insts.size(); ++t) {
+            if (val[4 * t + 2] != 0.f) { set_error("instance %zu: Q or b holds NaN/Inf", t); return UBQP_ENONFINITE; }
+            if (val[4 * t + 0] > 1e-12f * std::max(val[4 * t + 3], 1e-30f)) {
+                set_error("instance %zu: Q is not symmetric (max |Q_ij - Q_ji| = %g)", t, val[4 * t + 0]);
+                return UBQP_ENOTSYM;
+            }
+        }
+        // ---- reformulate (Sec. 3.5)
+        for (size_t t = 0; t < insts.size(); ++t) {
+            const InstIn& in = insts[t];
+            InstDev& I = inst_[t];
+            RefArgs a;
+            memset(&a, 0, sizeof(a));
+            a.n = (int)I.n;
+            a.ld = I.ld;
+            a.inst = (int)t;
+            a.diag_only_mu = tc ? 1 : 0;
+            a.Q = I.Q;
+            a.b = I.b;
+            a.mu = in.reformulated ? nullptr : I.mu;
+            double offmax = val[4 * t + 1];
+            a.sigma = (in.reformulated || I.mu) ? 0.0 : o_.sigma_rel * (offmax > 0 ? offmax : 1.0);
+            a.margin = in.reformulated ? 0.0 : o_.gamma_margin;
+            a.seed = o_.seed;
+            a.Qoff = tc ? nullptr : ar_.at<float>(I.o_Qoff);
+            a.Qbf = tc ? ar_.at<__nv_bfloat16>(I.o_Qbf) : nullptr;
+            a.Qeval = tc ? nullptr : ar_.at<double>(I.o_Qeval);
+            a.d = ar_.at<float>(I.o_d);
+            a.bprime = ar_.at<float>(I.o_bp);
+            a.oabs = ar_.at<float>(I.o_oabs);
+            a.rabs = ar_.at<float>(I.o_rabs);
+            a.tsum = ar_.at<float>(I.o_tsum);
+            a.borig = ar_.at<double>(I.o_borig);
+            a.qdb = ar_.at<double>(I.o_qdb);
+            a.gamma = ar_.at<double>(I.o_gamma);
+            a.scal = ar_.at<float>(o_scal_) + 4 * t;
+            a.inexact = ar_.at<int>(o_inexact_) + t;
+            a.no_gamma = in.reformulated ? 1 : 0;  // Q', b' given: no shift
+            UBQP_CK(launch_reformulate(a, stream_));
+            launches_ += (I.ld > I.n) ? 2 : 1;
+            if (tc && I.nl > 0 && a.Qbf) {
+                // zero the padded rows of the BF16 matrix (rows n..ld-1)
+                if ((size_t)I.ld > (size_t)I.n)
+                    UBQP_CK(cudaMemsetAsync(a.Qbf + (size_t)I.n * I.ld, 0, (size_t)(I.ld - I.n) * I.ld * 2, stream_));
+            }
+        }
+        std::vector<float> scal(insts.size() * 4);
+        UBQP_CK(cudaMemcpyAsync(scal.data(), ar_.at<float>(o_scal_), scal.size() * 4, cudaMemcpyDeviceToHost, stream_));
+        std::vector<int> inexact(insts.size());
+        UBQP_CK(cudaMemcpyAsync(inexact.data(), ar_.at<int>(o_inexact_), inexact.size() * sizeof(int),
+                                cudaMemcpyDeviceToHost, stream_));
+        // ---- stage lane-specific inputs
+        for (size_t l = 0; l < lanes.size(); ++l) {
+            const LaneIn& in = lanes[l];
+            const size_t n = (size_t)inst_[in.inst].n;
+            const double* x0 = in.x0;
+            const double* p0 = in.p0;
+            if (in.x0 && o_x0_[l] != SIZE_MAX - 1) {
+                UBQP_CK(cudaMemcpyAsync(ar_.at<double>(o_x0_[l]), in.x0, n * 8, cudaMemcpyHostToDevice, stream_));
+                x0 = ar_.at<double>(o_x0_[l]);
+            }
+            if (in.p0 && o_p0_[l] != SIZE_MAX - 1) {
+                UBQP_CK(cudaMemcpyAsync(ar_.at<double>(o_p0_[l]), in.p0, n * 8, cudaMemcpyHostToDevice, stream_));
+                p0 = ar_.at<double>(o_p0_[l]);
+            }
+            lane_init_[l].phase = in.phase;
+            lane_init_[l].start_kind = in.start_kind;
+            lane_init_[l].inst = in.inst;
+            lane_init_[l].restart = in.restart;
+            lane_init_[l].x0 = x0;
+            lane_init_[l].p0 = p0;
+        }
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        inexact_ = false;
+        for (int v : inexact) inexact_ |= (v != 0);
+        // ---- lane descriptors
+        std::vector<int2> items;
+        items.reserve((size_t)nitems);
+        for (size_t l = 0; l < lanes.size(); ++l) {
+            const LaneIn& in = lanes[l];
+            InstDev& I = inst_[in.inst];
+            LaneDev& L = lanes_[l];
+            L.Qoff = tc ? nullptr : ar_.at<float>(I.o_Qoff);
+            L.Qeval = tc ? nullptr : ar_.at<double>(I.o_Qeval);
+            L.d = ar_.at<float>(I.o_d);
+            L.bprime = ar_.at<float>(I.o_bp);
+            L.oabs = ar_.at<float>(I.o_oabs);
+            L.rabs = ar_.at<float>(I.o_rabs);
+            L.tsum = ar_.at<float>(I.o_tsum);
+            L.borig = ar_.at<double>(I.o_borig);
+            L.qdb = ar_.at<double>(I.o_qdb);
+            L.vec = ar_.at<float>(o_vec_[l]);
+            L.best_x = ar_.at<uint8_t>(o_bx_[l]);
+            L.part = ar_.at<Partial>(o_part_[l]);
+            L.st = ar_.at<LaneState>(o_states_) + l;
+            if (tc) {
+                L.u_hi = ar_.at<__nv_bfloat16>(I.o_Uhi) + (size_t)in.restart * I.ld;
+                L.u_lo = I.o_Ulo ? ar_.at<__nv_bfloat16>(I.o_Ulo) + (size_t)in.restart * I.ld : nullptr;
+            }
+            L.trace_x = in.trace_len > 0 ? ar_.at<float>(o_trace_x_[l]) : nullptr;
+            L.trace_alpha = in.trace_len > 0 ? ar_.at<float>(o_trace_a_[l]) : nullptr;
+            L.qmax_off = scal[4 * in.inst + 0];
+            L.rabs_max = scal[4 * in.inst + 1];
+            if (!tc)
+                for (int b = 0; b < L.nblk; ++b) items.push_back(make_int2((int)l, b));
+        }
+        UBQP_CK(cudaMemcpyAsync(ar_.at<LaneDev>(o_lanes_), lanes_.data(), lanes_.size() * sizeof(LaneDev),
+                                cudaMemcpyHostToDevice, stream_));
+        UBQP_CK(cudaMemcpyAsync(ar_.at<LaneInit>(o_linit_), lane_init_.data(), lane_init_.size() * sizeof(LaneInit),
+                                cudaMemcpyHostToDevice, stream_));
+        if (!items.empty())
+            UBQP_CK(cudaMemcpyAsync(ar_.at<int2>(o_items_), items.data(), items.size() * sizeof(int2),
+                                    cudaMemcpyHostToDevice, stream_));
+        if (tc) {
+            for (InstDev& I : inst_) {
+                int rpad = (int)round_up((size_t)I.nl, 16);
+                UBQP_CK(cudaMemsetAsync(ar_.at<char>(I.o_Uhi), 0, (size_t)rpad * I.ld * 2, stream_));
+                if (I.o_Ulo) UBQP_CK(cudaMemsetAsync(ar_.at<char>(I.o_Ulo), 0, (size_t)rpad * I.ld * 2, stream_));
+            }
+        }
+        LaneInitArgs lia;
+        lia.lanes = ar_.at<LaneDev>(o_lanes_);
+        lia.init = ar_.at<LaneInit>(o_linit_);
+        lia.seed = o_.seed;
+        UBQP_CK(launch_lane_init(lia, (int)lanes.size(), stream_));
+        launches_ += 1;
+        // host copies of the vectors are no longer needed; keep them for stats
+        nlanes_ = (int)lanes.size();
+        return UBQP_OK;
+    }
+
+    int run()
+    {
+        TickArgs ta;
+        ta.lanes = ar_.at<LaneDev>(o_lanes_);
+        ta.items = ar_.at<int2>(o_items_);
+        ta.nitems = nitems_;
+        ta.rows_per_item = rows_per_item_;
+        ta.nlanes = nlanes_;
+        ta.max_ld = max_ld_;
+        ta.P = make_params(o_, ar_.at<int64_t>(o_hist_));
+        const bool prof = o_.profile_kernels != 0;
+        if (prof) ta.P.bytes = ar_.at<unsigned long long>(o_bytes_);
+        int32_t* d_active = ar_.at<int32_t>(o_active_);
+        UBQP_CK(cudaMallocHost(&h_active_, sizeof(int32_t)));
+        if (!tc_ && nitems_ > 0) UBQP_CK(prepare_phase_a_gemv(max_ld_));
+        const int T = o_.max_ticks_per_sync;
+        const bool has_a = !tc_ && nitems_ > 0;
+        if (prof && has_a) {
+            evA_.resize(2 * T);
+            for (auto& e : evA_) UBQP_CK(cudaEventCreate(&e));
+        }
+
+        auto enqueue = [&](int nt) -> cudaError_t {
+            for (int t = 0; t < nt; ++t) {
+                cudaError_t e = cudaSuccess;
+                if (prof && has_a) e = cudaEventRecord(evA_[2 * t], stream_);
+                if (e != cudaSuccess) return e;
+                if (has_a) e = launch_phase_a_gemv_f32(ta, stream_);
+                if (e != cudaSuccess) return e;
+                if (prof && has_a) e = cudaEventRecord(evA_[2 * t + 1], stream_);
+                if (e != cudaSuccess) return e;
+                if (t == nt - 1) {
+                    e = cudaMemsetAsync(d_active, 0, sizeof(int32_t), stream_);
+                    if (e != cudaSuccess) return e;
+                }
+                e = launch_phase_b(ta, t == nt - 1 ? d_active : nullptr, stream_);
+                if (e != cudaSuccess) return e;
+            }
+            return cudaMemcpyAsync(h_active_, d_active, sizeof(int32_t), cudaMemcpyDeviceToHost, stream_);
+        };
+        // capture one batch of T ticks into a graph (profiling launches directly so that
+        // the events around every phase-A launch can be timed)
+        bool use_graph = !prof;
+        if (use_graph && cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            cudaError_t e = enqueue(T);
+            cudaError_t e2 = cudaStreamEndCapture(stream_, &graph_);
+            if (e != cudaSuccess || e2 != cudaSuccess ||
+                cudaGraphInstantiate(&gexec_, graph_, 0) != cudaSuccess) {
+                use_graph = false;
+                cudaGetLastError();
+            }
+        } else {
+            use_graph = false;
+            cudaGetLastError();
+        }
+        UBQP_CK(cudaEventRecord(ev0_, stream_));
+        int64_t ticks = 0;
+        const int64_t cap = (int64_t)(o_.jacobi_max_iter + 2) +
+                            (int64_t)(o_.max_outer + 1) * (int64_t)(o_.max_inner + o_.lobpcg_max_iter + 8);
+        for (;;) {
+            if (use_graph) UBQP_CK(cudaGraphLaunch(gexec_, stream_));
+            else UBQP_CK(enqueue(T));
+            launches_ += (int64_t)T * ((has_a ? 1 : 0) + 1);
+            UBQP_CK(cudaStreamSynchronize(stream_));
+            ticks += T;
+            if (prof && has_a) {
+                for (int t = 0; t < T; ++t) {
+                    float ms = 0.f;
+                    UBQP_CK(cudaEventElapsedTime(&ms, evA_[2 * t], evA_[2 * t + 1]));
+                    phase_a_ms_ += ms;
+                }
+                phase_a_launches_ += T;
+            }
+            if (*h_active_ == 0) break;
+            if (ticks > cap) {
+                set_error("tick cap %lld exceeded", (long long)cap);
+                return UBQP_ETIMEOUT;
+            }
+        }
+        UBQP_CK(cudaEventRecord(ev1_, stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0_, ev1_);
+        ms_device_ = ms;
+        ticks_ = ticks;
+        return UBQP_OK;
+    }
+
+    // best lane per instance; x_out entries are host or device pointers
+    int finalize(uint8_t* const* x_out, double* obj_out)
+    {
+        const size_t ni = inst_.size();
+        std::vector<int32_t> l0(ni), nl(ni);
+        std::vector<uint8_t*> xd(ni);
+        size_t off = 0;
+        std::vector<bool> xhost(ni);
+        for (size_t t = 0; t < ni; ++t) {
+            l0[t] = inst_[t].lane0;
+            nl[t] = inst_[t].nl;
+            xhost[t] = !is_device_ptr(x_out[t]);
+            xd[t] = xhost[t] ? ar_.at<uint8_t>(o_final_xbuf_) + off : x_out[t];
+            off += round_up((size_t)inst_[t].n, 256);
+        }
+        UBQP_CK(cudaMemcpyAsync(ar_.at<int32_t>(o_final_lane0_), l0.data(), ni * 4, cudaMemcpyHostToDevice, stream_));
+        UBQP_CK(cudaMemcpyAsync(ar_.at<int32_t>(o_final_nl_), nl.data(), ni * 4, cudaMemcpyHostToDevice, stream_));
+        UBQP_CK(cudaMemcpyAsync(ar_.at<uint8_t*>(o_final_xptr_), xd.data(), ni * sizeof(void*), cudaMemcpyHostToDevice,
+                                stream_));
+        FinalArgs fa;
+        fa.lanes = ar_.at<LaneDev>(o_lanes_);
+        fa.lane0 = ar_.at<int32_t>(o_final_lane0_);
+        fa.nlanes = ar_.at<int32_t>(o_final_nl_);
+        fa.obj = ar_.at<double>(o_final_obj_);
+        fa.best_lane = ar_.at<int32_t>(o_final_best_);
+        fa.x_out = ar_.at<uint8_t*>(o_final_xptr_);
+        UBQP_CK(launch_finalize(fa, (int)ni, stream_));
+        launches_ += 1;
+        for (size_t t = 0; t < ni; ++t)
+            if (xhost[t])
+                UBQP_CK(cudaMemcpyAsync(x_out[t], xd[t], (size_t)inst_[t].n, cudaMemcpyDeviceToHost, stream_));
+        if (is_device_ptr(obj_out))
+            UBQP_CK(cudaMemcpyAsync(obj_out, fa.obj, ni * 8, cudaMemcpyDeviceToDevice, stream_));
+        else
+            UBQP_CK(cudaMemcpyAsync(obj_out, fa.obj, ni * 8, cudaMemcpyDeviceToHost, stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        return UBQP_OK;
+    }
+
+    int states(std::vector<LaneState>& out)
+    {
+        out.resize(nlanes_);
+        UBQP_CK(cudaMemcpyAsync(out.data(), ar_.at<LaneState>(o_states_), nlanes_ * sizeof(LaneState),
+                                cudaMemcpyDeviceToHost, stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        return UBQP_OK;
+    }
+
+    int fill_stats(ubqp_stats* s)
+    {
+        if (!s) return UBQP_OK;
+        std::vector<LaneState> st;
+        int rc = states(st);
+        if (rc) return rc;
+        memset(s, 0, sizeof(*s));
+        for (int l = 0; l < nlanes_; ++l) {
+            const LaneState& S = st[l];
+            s->inner_iters += S.inner_iters;
+            s->inner_steps += S.inner_steps;
+            s->var_updates += S.inner_iters * (int64_t)lanes_[l].n;
+            s->outer_steps += S.s;
+            s->lobpcg_iters += S.lob_iters;
+            s->jacobi_iters += S.jac_iters;
+            s->floor_steps += S.floor_steps;
+            s->lanes_capped += S.status == 1 ? 1 : 0;
+        }
+        s->lanes = nlanes_;
+        s->ticks = ticks_;
+        s->ms_device = ms_device_;
+        s->phase_a_ms = phase_a_ms_;
+        s->phase_a_launches = phase_a_launches_;
+        unsigned long long by = 0;
+        UBQP_CK(cudaMemcpyAsync(&by, ar_.at<unsigned long long>(o_bytes_), sizeof(by), cudaMemcpyDeviceToHost, stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        s->phase_a_bytes = (int64_t)by;
+        s->kernel_launches = launches_;
+        UBQP_CK(cudaMemcpyAsync(s->inner_hist, ar_.at<int64_t>(o_hist_), sizeof(s->inner_hist), cudaMemcpyDeviceToHost,
+                                stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        return UBQP_OK;
+    }
+
+    int lane_vec_f64(int lane, int v, double* out_dev_or_host)
+    {
+        const int n = lanes_[lane].n;
+        bool host = !is_device_ptr(out_dev_or_host);
+        double* dst = out_dev_or_host;
+        double* tmp = nullptr;
+        if (host) UBQP_CK(cudaMallocAsync((void**)&tmp, (size_t)n * 8, stream_));
+        if (host) dst = tmp;
+        UBQP_CK(launch_lane_vec_to_f64(ar_.at<LaneDev>(o_lanes_), lane, v, n, dst, stream_));
+        if (host) {
+            UBQP_CK(cudaMemcpyAsync(out_dev_or_host, tmp, (size_t)n * 8, cudaMemcpyDeviceToHost, stream_));
+            UBQP_CK(cudaFreeAsync(tmp, stream_));
+        }
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        return UBQP_OK;
+    }
+
+    int trace_f64(int lane, int count_rows, double* tx, double* ta)
+    {
+        const int n = lanes_[lane].n;
+        auto copy = [&](const float* src, double* dst, int64_t cnt) -> int {
+            if (!dst || cnt <= 0) return UBQP_OK;
+            bool host = !is_device_ptr(dst);
+            double* d = dst;
+            double* tmp = nullptr;
+            if (host) {
+                UBQP_CK(cudaMallocAsync((void**)&tmp, (size_t)cnt * 8, stream_));
+                d = tmp;
+            }
+            UBQP_CK(launch_trace_to_f64(src, d, cnt, stream_));
+            if (host) {
+                UBQP_CK(cudaMemcpyAsync(dst, tmp, (size_t)cnt * 8, cudaMemcpyDeviceToHost, stream_));
+                UBQP_CK(cudaFreeAsync(tmp, stream_));
+            }
+            UBQP_CK(cudaStreamSynchronize(stream_));
+            return UBQP_OK;
+        };
+        int rc = copy(ar_.at<float>(o_trace_x_[lane]), tx, (int64_t)count_rows * n);
+        if (rc) return rc;
+        return copy(ar_.at<float>(o_trace_a_[lane]), ta, count_rows);
+    }
+
+    int gamma_f64(int inst, double* out)
+    {
+        const size_t n = (size_t)inst_[inst].n;
+        cudaMemcpyKind k = is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        UBQP_CK(cudaMemcpyAsync(out, ar_.at<double>(inst_[inst].o_gamma), n * 8, k, stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        return UBQP_OK;
+    }
+
+    bool inexact() const { return inexact_; }
+    int64_t ticks() const { return ticks_; }
+
+  private:
+    ubqp_opts o_;
+    bool tc_ = false;
+    cudaStream_t stream_ = nullptr;
+    cudaEvent_t ev0_ = nullptr, ev1_ = nullptr;
+    cudaGraph_t graph_ = nullptr;
+    cudaGraphExec_t gexec_ = nullptr;
+    int32_t* h_active_ = nullptr;
+    int num_sms_ = 148;
+    int max_ld_ = 32;
+    int rows_per_item_ = 32;
+    int nitems_ = 0;
+    int nlanes_ = 0;
+    bool inexact_ = false;
+    int64_t ticks_ = 0;
+    double ms_device_ = 0.0;
+    double phase_a_ms_ = 0.0;
+    int64_t launches_ = 0;
+    int64_t phase_a_launches_ = 0;
+    std::vector<cudaEvent_t> evA_;
+    Arena ar_;
+    std::vector<InstDev> inst_;
+    std::vector<LaneDev> lanes_;
+    std::vector<LaneInit> lane_init_;
+    std::vector<size_t> o_vec_, o_bx_, o_part_, o_trace_x_, o_trace_a_, o_x0_, o_p0_;
+    size_t o_scal_ = 0, o_valid_ = 0, o_inexact_ = 0, o_hist_ = 0, o_active_ = 0, o_states_ = 0, o_lanes_ = 0,
+           o_linit_ = 0, o_items_ = 0, o_bytes_ = 0;
+    size_t o_final_lane0_ = 0, o_final_nl_ = 0, o_final_obj_ = 0, o_final_best_ = 0, o_final_xptr_ = 0,
+           o_final_xbuf_ = 0;
+};
+
+}  // namespace ubqp
+
+// =====================================================================================
+// C ABI
+using namespace ubqp;
+
+extern "C" {
+
+void ubqp_opts_default(ubqp_opts* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->method = UBQP_PABB;
+    o->max_outer = 1000;
+    o->max_inner = 10000;
+    o->tol_inner = 1e-5;
+    o->tol_outer = 1e-5;
+    o->eta = 0.9;
+    o->gamma_margin = 1.0;
+    o->alpha_min = 1e-10;
+    o->alpha_max = 1e10;
+    o->tau_z = 1e-12;
+    o->eps_hp_rel = 1e-8;
+    o->lambda_floor_rel = 4.0;
+    o->sigma_rel = 1e-3;
+    o->seed = 0;
+    o->restarts = 1;
+    o->precision = UBQP_FP32;
+    o->lobpcg_max_iter = 64;
+    o->lobpcg_tol = 1e-4;
+    o->jacobi_max_iter = 60;
+    o->max_ticks_per_sync = 64;
+    o->profile_kernels = 0;
+    o->stream = nullptr;
+    o->mu = nullptr;
+    o->x_starts = nullptr;
+    o->stats = nullptr;
+}
+
+const char* ubqp_status_string(int s)
+{
+    switch (s) {
+    case UBQP_OK: return "UBQP_OK";
+    case UBQP_EINVAL: return "UBQP_EINVAL";
+    case UBQP_ENOTSYM: return "UBQP_ENOTSYM";
+    case UBQP_ENONFINITE: return "UBQP_ENONFINITE";
+    case UBQP_ECUDA: return "UBQP_ECUDA";
+    case UBQP_ENOMEM: return "UBQP_ENOMEM";
+    case UBQP_ETIMEOUT: return "UBQP_ETIMEOUT";
+    case UBQP_ENOTSUP: return "UBQP_ENOTSUP";
+    case UBQP_EMAXITER: return "UBQP_EMAXITER";
+    default: return "UBQP_UNKNOWN";
+    }
+}
+
+const char* ubqp_last_error(void) { return g_last_error; }
+
+int ubqp_solve_batched(int32_t num, const int64_t* n, const double* const* Q, const double* const* b,
+                       const ubqp_opts* o_in, uint8_t* const* x_out, double* obj_out)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    g_last_error[0] = 0;
+    if (num < 1 || !n || !Q || !x_out || !obj_out) {
+        set_error("num >= 1 and non-null n, Q, x_out, obj_out are required");
+        return UBQP_EINVAL;
+    }
+    ubqp_opts o;
+    if (o_in) o = *o_in;
+    else ubqp_opts_default(&o);
+    for (int32_t t = 0; t < num; ++t) {
+        if (n[t] < 1 || n[t] > 65536) { set_error("instance %d: n = %lld out of [1, 65536]", t, (long long)n[t]); return UBQP_EINVAL; }
+        if (!Q[t] || !x_out[t]) { set_error("instance %d: null Q or x_out", t); return UBQP_EINVAL; }
+    }
+    const bool tc = o.precision != UBQP_FP32;
+    if (tc) {
+        set_error("tensor-core precision is not available in this build");
+        return UBQP_ENOTSUP;
+    }
+    std::vector<InstIn> insts(num);
+    std::vector<LaneIn> lanes;
+    const int R = std::max(1, o.restarts);
+    for (int32_t t = 0; t < num; ++t) {
+        insts[t].n = n[t];
+        insts[t].Q = Q[t];
+        insts[t].b = b ? b[t] : nullptr;
+        insts[t].mu = o.mu ? o.mu[t] : nullptr;
+        insts[t].starts = o.x_starts ? o.x_starts[t] : nullptr;
+        insts[t].reformulated = false;
+        for (int r = 0; r < R; ++r) {
+            LaneIn l;
+            l.inst = t;
+            l.restart = r;
+            l.phase = r == 0 ? PH_JACOBI : PH_EVAL;
+            l.start_kind = r == 0 ? 0 : 1;
+            l.x0 = (r > 0 && insts[t].starts) ? insts[t].starts + (size_t)(r - 1) * n[t] : nullptr;
+            l.p0 = nullptr;
+            l.stop_after = 0;
+            l.trace_len = 0;
+            lanes.push_back(l);
+        }
+    }
+    Solver S(o);
+    int rc = S.setup(insts, lanes, tc);
+    if (rc) return rc;
+    rc = S.run();
+    if (rc) return rc;
+    rc = S.finalize(x_out, obj_out);
+    if (rc) return rc;
+    ubqp_stats st;
+    rc = S.fill_stats(&st);
+    if (rc) return rc;
+    st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (o.stats) *o.stats = st;
+    return st.lanes_capped > 0 ? UBQP_EMAXITER : UBQP_OK;
+}
+
+int ubqp_solve(const double* Q, const double* b, int64_t n, const ubqp_opts* o, uint8_t* x_out, double* obj_out)
+{
+    const double* Qs[1] = {Q};
+    const double* bs[1] = {b};
+    uint8_t* xs[1] = {x_out};
+    int64_t ns[1] = {n};
+    return ubqp_solve_batched(1, ns, Qs, bs, o, xs, obj_out);
+}
+
+int ubqp_inner_run(const double* Qp, const double* bp, const double* p, const double* x0, int64_t n,
+                   const ubqp_opts* o_in, int32_t trace_len, double* trace_x, double* trace_alpha, double* x_out,
+                   int32_t* steps_out, int32_t* exit_out)
+{
+    g_last_error[0] = 0;
+    if (n < 1 || n > 65536 || !Qp || !bp || !p || !x0 || trace_len < 0) {
+        set_error("ubqp_inner_run: bad arguments");
+        return UBQP_EINVAL;
+    }
+    ubqp_opts o;
+    if (o_in) o = *o_in;
+    else ubqp_opts_default(&o);
+    o.precision = UBQP_FP32;
+    o.restarts = 1;
+    std::vector<InstIn> insts(1);
+    insts[0] = InstIn{n, Qp, bp, nullptr, nullptr, true};
+    std::vector<LaneIn> lanes(1);
+    lanes[0] = LaneIn{0, 0, PH_INNER, 0, x0, p, STOP_INNER, trace_len};
+    Solver S(o);
+    int rc = S.setup(insts, lanes, false);
+    if (rc) return rc;
+    rc = S.run();
+    if (rc) return rc;
+    std::vector<LaneState> st;
+    rc = S.states(st);
+    if (rc) return rc;
+    int rows = std::min<int>(trace_len, st[0].k + 1);
+    if (trace_len > 0) {
+        rc = S.trace_f64(0, rows, trace_x, trace_alpha);
+        if (rc) return rc;
+    }
+    if (x_out) {
+        rc = S.lane_vec_f64(0, V_X, x_out);
+        if (rc) return rc;
+    }
+    if (steps_out) *steps_out = st[0].k;
+    if (exit_out) *exit_out = st[0].last_exit;
+    return UBQP_OK;
+}
+
+int ubqp_penalty_probe(const double* Qp, const double* bp, const double* p, const double* x, int64_t n,
+                       const ubqp_opts* o_in, double* lambda_out, double* alpha_out, int32_t* n_active_out,
+                       int32_t* iters_out)
+{
+    g_last_error[0] = 0;
+    if (n < 1 || n > 65536 || !Qp || !bp || !p || !x) {
+        set_error("ubqp_penalty_probe: bad arguments");
+        return UBQP_EINVAL;
+    }
+    ubqp_opts o;
+    if (o_in) o = *o_in;
+    else ubqp_opts_default(&o);
+    o.precision = UBQP_FP32;
+    o.restarts = 1;
+    if (o.max_outer < 1) o.max_outer = 1;
+    std::vector<InstIn> insts(1);
+    insts[0] = InstIn{n, Qp, bp, nullptr, nullptr, true};
+    std::vector<LaneIn> lanes(1);
+    lanes[0] = LaneIn{0, 0, PH_EVAL, 0, x, p, STOP_LOB, 0};
+    Solver S(o);
+    int rc = S.setup(insts, lanes, false);
+    if (rc) return rc;
+    rc = S.run();
+    if (rc) return rc;
+    std::vector<LaneState> st;
+    rc = S.states(st);
+    if (rc) return rc;
+    if (lambda_out) *lambda_out = st[0].lam;
+    if (alpha_out) *alpha_out = st[0].pen_alpha;
+    if (n_active_out) *n_active_out = st[0].n_active;
+    if (iters_out) *iters_out = (int32_t)st[0].lob_iters;
+    return UBQP_OK;
+}
+
+int ubqp_initial_point(const double* Q, const double* b, const double* mu, int64_t n, const ubqp_opts* o_in,
+                       double* x0_out, double* gamma_out)
+{
+    g_last_error[0] = 0;
+    if (n < 1 || n > 65536 || !Q || !x0_out) {
+        set_error("ubqp_initial_point: bad arguments");
+        return UBQP_EINVAL;
+    }
+    ubqp_opts o;
+    if (o_in) o = *o_in;
+    else ubqp_opts_default(&o);
+    o.precision = UBQP_FP32;
+    o.restarts = 1;
+    std::vector<InstIn> insts(1);
+    insts[0] = InstIn{n, Q, b, mu, nullptr, false};
+    std::vector<LaneIn> lanes(1);
+    lanes[0] = LaneIn{0, 0, PH_JACOBI, 0, nullptr, nullptr, STOP_JACOBI, 0};
+    Solver S(o);
+    int rc = S.setup(insts, lanes, false);
+    if (rc) return rc;
+    rc = S.run();
+    if (rc) return rc;
+    rc = S.lane_vec_f64(0, V_X, x0_out);
+    if (rc) return rc;
+    if (gamma_out) rc = S.gamma_f64(0, gamma_out);
+    return rc;
+}
+
+int ubqp_penalized_eval(const void* Q, const void* b, const void* p, const void* x, int64_t n, int64_t batch,
+                        int dtype, void* h_out, void* g_out, void* stream)
+{
+    g_last_error[0] = 0;
+    if (!Q || !x || n < 1 || n > 65536 || batch < 1 || (dtype != UBQP_DTYPE_F32 && dtype != UBQP_DTYPE_F64)) {
+        set_error("ubqp_penalized_eval: bad arguments");
+        return UBQP_EINVAL;
+    }
+    if (!is_device_ptr(Q) || !is_device_ptr(x) || (b && !is_device_ptr(b)) || (p && !is_device_ptr(p)) ||
+        (h_out && !is_device_ptr(h_out)) || (g_out && !is_device_ptr(g_out))) {
+        set_error("ubqp_penalized_eval: all pointers must be device memory");
+        return UBQP_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t es = dtype == UBQP_DTYPE_F64 ? 8 : 4;
+    int dev = 0, sms = 148;
+    UBQP_CK(cudaGetDevice(&dev));
+    UBQP_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int rb = 8;
+    while (rb < 256 && (int64_t)batch * n / rb > 8 * sms) rb *= 2;
+    const int nblk = (int)((n + rb - 1) / rb);
+    std::vector<LaneDev> lanes((size_t)batch);
+    std::vector<int2> items;
+    items.reserve((size_t)batch * nblk);
+    const size_t bytes_lanes = round_up((size_t)batch * sizeof(LaneDev), 256);
+    const size_t bytes_items = round_up((size_t)batch * nblk * sizeof(int2), 256);
+    const size_t bytes_part = (size_t)batch * nblk * sizeof(Partial);
+    char* scratch = nullptr;
+    UBQP_CK(cudaMallocAsync((void**)&scratch, bytes_lanes + bytes_items + bytes_part, s));
+    LaneDev* d_lanes = reinterpret_cast<LaneDev*>(scratch);
+    int2* d_items = reinterpret_cast<int2*>(scratch + bytes_lanes);
+    Partial* d_part = reinterpret_cast<Partial*>(scratch + bytes_lanes + bytes_items);
+    for (int64_t r = 0; r < batch; ++r) {
+        LaneDev& L = lanes[(size_t)r];
+        memset(&L, 0, sizeof(L));
+        L.n = (int)n;
+        L.ld = (int)n;
+        L.mode = MODE_GRAD;
+        L.nblk = nblk;
+        L.part = d_part + (size_t)r * nblk;
+        L.gQ = Q;
+        L.gb = b;
+        L.gp = p;
+        L.gx = static_cast<const char*>(x) + (size_t)r * n * es;
+        L.gg = g_out ? static_cast<char*>(g_out) + (size_t)r * n * es : nullptr;
+        L.gld = (int)n;
+        for (int blk = 0; blk < nblk; ++blk) items.push_back(make_int2((int)r, blk));
+    }
+    cudaError_t e = cudaMemcpyAsync(d_lanes, lanes.data(), lanes.size() * sizeof(LaneDev), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    TickArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    ta.lanes = d_lanes;
+    ta.items = d_items;
+    ta.nitems = (int)items.size();
+    ta.rows_per_item = rb;
+    ta.nlanes = (int)batch;
+    ta.max_ld = (int)n;
+    if (e == cudaSuccess) e = launch_phase_a_grad(ta, dtype, n, s);
+    if (e == cudaSuccess && h_out) e = launch_grad_reduce(d_lanes, (int)batch, h_out, dtype, s);
+    cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (e == cudaSuccess) e = ef;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_error("ubqp_penalized_eval: %s", cudaGetErrorString(e));
+        return UBQP_ECUDA;
+    }
+    return UBQP_OK;
+}
+
+}  // extern "C"

