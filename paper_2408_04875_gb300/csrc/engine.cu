@@ -240,9 +240,11 @@ class Solver {
         // lanes: rows per phase-A item for the GEMV path
         int64_t total_rows = 0;
         for (const LaneIn& l : lanes) total_rows += insts[l.inst].n;
+        // rows per phase-A item: enough items to fill the GPU with all lanes active, and
+        // at most 16 rows so that a lone large lane still spreads over most SMs
         int target_items = 8 * num_sms_;
         int rb = 8;
-        while (rb < 256 && total_rows / rb > target_items) rb *= 2;
+        while (rb < 16 && total_rows / rb > target_items) rb *= 2;
         rows_per_item_ = rb;
 
         lanes_.assign(lanes.size(), LaneDev());
@@ -288,6 +290,7 @@ class Solver {
             }
         }
         o_states_ = ar_.reserve(lanes.size() * sizeof(LaneState));
+        o_counters_ = ar_.reserve(lanes.size() * sizeof(unsigned int));
         o_lanes_ = ar_.reserve(lanes.size() * sizeof(LaneDev));
         o_linit_ = ar_.reserve(lanes.size() * sizeof(LaneInit));
         o_items_ = ar_.reserve((size_t)std::max<int64_t>(nitems, 1) * sizeof(int2));
@@ -305,6 +308,7 @@ class Solver {
         if (rc) return rc;
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_hist_), 0, UBQP_HIST_BINS * sizeof(int64_t), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_bytes_), 0, sizeof(unsigned long long), stream_));
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_counters_), 0, lanes.size() * sizeof(unsigned int), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_valid_), 0, insts.size() * 4 * sizeof(float), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_scal_), 0, insts.size() * 4 * sizeof(float), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_inexact_), 0, insts.size() * sizeof(int), stream_));
@@ -365,7 +369,7 @@ class Solver {
             a.seed = o_.seed;
             a.Qoff = tc ? nullptr : ar_.at<float>(I.o_Qoff);
             a.Qbf = tc ? ar_.at<__nv_bfloat16>(I.o_Qbf) : nullptr;
-            a.Qeval = tc ? nullptr : ar_.at<double>(I.o_Qeval);
+            a.Qeval = tc ? nullptr : ar_.at<float2>(I.o_Qeval);
             a.d = ar_.at<float>(I.o_d);
             a.bprime = ar_.at<float>(I.o_bp);
             a.oabs = ar_.at<float>(I.o_oabs);
@@ -422,7 +426,7 @@ class Solver {
             InstDev& I = inst_[in.inst];
             LaneDev& L = lanes_[l];
             L.Qoff = tc ? nullptr : ar_.at<float>(I.o_Qoff);
-            L.Qeval = tc ? nullptr : ar_.at<double>(I.o_Qeval);
+            L.Qeval = tc ? nullptr : ar_.at<float2>(I.o_Qeval);
             L.d = ar_.at<float>(I.o_d);
             L.bprime = ar_.at<float>(I.o_bp);
             L.oabs = ar_.at<float>(I.o_oabs);
@@ -434,6 +438,7 @@ class Solver {
             L.best_x = ar_.at<uint8_t>(o_bx_[l]);
             L.part = ar_.at<Partial>(o_part_[l]);
             L.st = ar_.at<LaneState>(o_states_) + l;
+            L.counter = ar_.at<unsigned int>(o_counters_) + l;
             if (tc) {
                 L.u_hi = ar_.at<__nv_bfloat16>(I.o_Uhi) + (size_t)in.restart * I.ld;
                 L.u_lo = I.o_Ulo ? ar_.at<__nv_bfloat16>(I.o_Ulo) + (size_t)in.restart * I.ld : nullptr;
@@ -479,6 +484,8 @@ class Solver {
         ta.rows_per_item = rows_per_item_;
         ta.nlanes = nlanes_;
         ta.max_ld = max_ld_;
+        ta.fused = 0;
+        ta.active_count = nullptr;
         ta.P = make_params(o_, ar_.at<int64_t>(o_hist_));
         const bool prof = o_.profile_kernels != 0;
         if (prof) ta.P.bytes = ar_.at<unsigned long long>(o_bytes_);
@@ -492,21 +499,32 @@ class Solver {
             for (auto& e : evA_) UBQP_CK(cudaEventCreate(&e));
         }
 
+        // GEMV lanes: one fused kernel per tick (the last CTA of each lane updates it);
+        // tensor-core lanes: contraction kernel, then the stand-alone update kernel
+        const bool fused = has_a;
         auto enqueue = [&](int nt) -> cudaError_t {
             for (int t = 0; t < nt; ++t) {
                 cudaError_t e = cudaSuccess;
-                if (prof && has_a) e = cudaEventRecord(evA_[2 * t], stream_);
-                if (e != cudaSuccess) return e;
-                if (has_a) e = launch_phase_a_gemv_f32(ta, stream_);
-                if (e != cudaSuccess) return e;
-                if (prof && has_a) e = cudaEventRecord(evA_[2 * t + 1], stream_);
-                if (e != cudaSuccess) return e;
-                if (t == nt - 1) {
+                const bool last = t == nt - 1;
+                if (last) {
                     e = cudaMemsetAsync(d_active, 0, sizeof(int32_t), stream_);
                     if (e != cudaSuccess) return e;
                 }
-                e = launch_phase_b(ta, t == nt - 1 ? d_active : nullptr, stream_);
+                if (prof && has_a) e = cudaEventRecord(evA_[2 * t], stream_);
                 if (e != cudaSuccess) return e;
+                if (has_a) {
+                    TickArgs tt = ta;
+                    tt.fused = 1;
+                    tt.active_count = last ? d_active : nullptr;
+                    e = launch_phase_a_gemv_f32(tt, stream_);
+                }
+                if (e != cudaSuccess) return e;
+                if (prof && has_a) e = cudaEventRecord(evA_[2 * t + 1], stream_);
+                if (e != cudaSuccess) return e;
+                if (!fused) {
+                    e = launch_phase_b(ta, last ? d_active : nullptr, stream_);
+                    if (e != cudaSuccess) return e;
+                }
             }
             return cudaMemcpyAsync(h_active_, d_active, sizeof(int32_t), cudaMemcpyDeviceToHost, stream_);
         };
@@ -532,7 +550,7 @@ class Solver {
         for (;;) {
             if (use_graph) UBQP_CK(cudaGraphLaunch(gexec_, stream_));
             else UBQP_CK(enqueue(T));
-            launches_ += (int64_t)T * ((has_a ? 1 : 0) + 1);
+            launches_ += (int64_t)T * (fused ? 1 : 2);
             UBQP_CK(cudaStreamSynchronize(stream_));
             ticks += T;
             if (prof && has_a) {
@@ -720,7 +738,7 @@ class Solver {
     std::vector<LaneInit> lane_init_;
     std::vector<size_t> o_vec_, o_bx_, o_part_, o_trace_x_, o_trace_a_, o_x0_, o_p0_;
     size_t o_scal_ = 0, o_valid_ = 0, o_inexact_ = 0, o_hist_ = 0, o_active_ = 0, o_states_ = 0, o_lanes_ = 0,
-           o_linit_ = 0, o_items_ = 0, o_bytes_ = 0;
+           o_linit_ = 0, o_items_ = 0, o_bytes_ = 0, o_counters_ = 0;
     size_t o_final_lane0_ = 0, o_final_nl_ = 0, o_final_obj_ = 0, o_final_best_ = 0, o_final_xptr_ = 0,
            o_final_xbuf_ = 0;
 };

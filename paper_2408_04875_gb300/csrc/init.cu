@@ -167,7 +167,10 @@ __global__ void reformulate_kernel(RefArgs a)
             oabs += fabs(stored);
             offmax = fmaxf(offmax, (float)fabs(stored));
         }
-        if (a.Qeval) a.Qeval[(size_t)i * ld + j] = q;
+        if (a.Qeval) {
+            float hi = (float)q;
+            a.Qeval[(size_t)i * ld + j] = make_float2(hi, (float)(q - (double)hi));
+        }
     }
     oabs = block_sum_d<256>(oabs, shd);
     offmax = block_max<256>(offmax, shf);

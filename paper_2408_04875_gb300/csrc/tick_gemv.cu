@@ -7,7 +7,7 @@
 //
 // The same kernel computes h and grad h for ubqp_penalized_eval (MODE_GRAD lanes), so
 // the autograd path and the inner loop share one gradient kernel.
-#include "ubqp_internal.cuh"
+#include "lane_update.cuh"
 
 namespace ubqp {
 
@@ -47,30 +47,26 @@ __device__ __forceinline__ float row_dot_f32(const float* __restrict__ row, cons
     return a.x + a.y;
 }
 
-// dot of one FP64 row with a 0/1 (or general) FP32 vector, accumulated in FP64
-__device__ __forceinline__ double row_dot_f64(const double* __restrict__ row, const float* su, int ld,
-                                              int lane)
+// dot of one row of the evaluation matrix (each FP64 entry q stored as FP32 hi + lo with
+// hi + lo = q to about 2^-48) with a 0/1 vector: the products are the entries themselves,
+// so TwoSum accumulation of hi and lo gives the FP64 row sum without FP64 arithmetic
+// (exactly, for integer data)
+__device__ __forceinline__ double row_dot_eval(const float2* __restrict__ row, const float* su, int ld,
+                                               int lane)
 {
-    const double2* r2 = reinterpret_cast<const double2*>(row);
+    const float4* r4 = reinterpret_cast<const float4*>(row);   // two entries per 16 bytes
     const float2* u2 = reinterpret_cast<const float2*>(su);
     const int n2 = ld >> 1;
-    double a0 = 0.0, a1 = 0.0;
-    int c = lane;
-    for (; c + 32 < n2; c += 64) {
-        double2 q0 = __ldg(r2 + c), q1 = __ldg(r2 + c + 32);
-        float2 u0 = u2[c], u1 = u2[c + 32];
-        a0 = fma(q0.x, (double)u0.x, fma(q0.y, (double)u0.y, a0));
-        a1 = fma(q1.x, (double)u1.x, fma(q1.y, (double)u1.y, a1));
+    float2 ah = make_float2(0.f, 0.f), al = ah;
+    for (int c = lane; c < n2; c += 32) {
+        float4 q = __ldg(r4 + c);
+        float2 u = u2[c];
+        if (u.x != 0.f) { csum_add(ah, q.x); csum_add(al, q.y); }
+        if (u.y != 0.f) { csum_add(ah, q.z); csum_add(al, q.w); }
     }
-    for (; c < n2; c += 32) {
-        double2 q0 = __ldg(r2 + c);
-        float2 u0 = u2[c];
-        a0 = fma(q0.x, (double)u0.x, fma(q0.y, (double)u0.y, a0));
-    }
-    double a = a0 + a1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    return a;
+    ah = csum_shfl_reduce(ah);
+    al = csum_shfl_reduce(al);
+    return ((double)ah.x + (double)ah.y) + ((double)al.x + (double)al.y);
 }
 
 // generic (unaligned, unpadded) row dot for user matrices of penalized_eval
@@ -92,7 +88,7 @@ __device__ __forceinline__ T row_dot_plain(const T* __restrict__ row, const T* s
 
 // ---------------------------------------------------------------------------------
 // solver lanes (FP32 GEMV path)
-__global__ void __launch_bounds__(kThreads) phase_a_gemv_kernel(TickArgs A)
+__global__ void __launch_bounds__(kThreads, 4) phase_a_gemv_kernel(TickArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* su = reinterpret_cast<float*>(smem_raw);
@@ -118,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) phase_a_gemv_kernel(TickArgs A)
 
     if (ph == PH_EVAL) {
         for (int r = warp; r < rows; r += kWarps) {
-            double v = row_dot_f64(L.Qeval + (size_t)(row0 + r) * ld, su, ld, lane);
+            double v = row_dot_eval(L.Qeval + (size_t)(row0 + r) * ld, su, ld, lane);
             if (lane == 0) sv[r] = v;
         }
     } else {
@@ -140,6 +136,18 @@ __global__ void __launch_bounds__(kThreads) phase_a_gemv_kernel(TickArgs A)
                                 (it.y == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
         atomicAdd(A.P.bytes, by);
     }
+    if (!A.fused) return;
+    // Fused phase B: every CTA publishes its partial and epilogue writes, then counts
+    // itself in; the CTA that completes the count runs the lane's update.  No CTA waits.
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = (atomicAdd(L.counter, 1u) == (unsigned)(L.nblk - 1));
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    lane_update(L, A.P, A.active_count);
+    if (threadIdx.x == 0) *L.counter = 0u;
 }
 
 // ---------------------------------------------------------------------------------

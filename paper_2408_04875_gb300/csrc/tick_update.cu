@@ -1,479 +1,12 @@
-// Phase B: one CTA per lane.  Reduces the lane's phase-A partials, takes the scalar
-// decision of the lane's phase and applies the element-wise update:
-//   INNER   Alg. 2: KKT test of Eq. (cret), alternating BB step of Eq. (bb1) with the
-//           safeguards listed below, projected step of Eq. (x2); or Alg. 1: the
-//           per-coordinate step of Eq. (x1) with H_p of Sec. 3.1.
-//   EVAL    exact objective of the rounded iterate, best-so-far, outer test of Alg. 3.
-//   LOB*    one LOBPCG iteration (Jacobi preconditioned, 3x3 Rayleigh-Ritz) for
-//           lambda_min of Z^-1/2 Qbar_II Z^-1/2 (Lemma 3.1); on convergence the penalty
-//           update p += alpha z of Eq. (pp1) with alpha of Eq. (eq:alpha1).
-//   JACOBI  one sweep for x^0 of Eq. (gamma).
-// Safeguards of the BB step (the paper states none): alpha_0 = 1/(2 ||Qbar||_inf);
-// s^T y <= 0 or a non-finite ratio keeps the previous step; clamp to
-// [alpha_min, alpha_max]; s = 0 stops the subproblem.
-#include "ubqp_internal.cuh"
+// Phase B as a stand-alone kernel: one CTA per lane runs lane_update (lane_update.cuh).
+// Used for tensor-core lanes; GEMV lanes run the same update inside the fused tick.
+#include "lane_update.cuh"
 
 namespace ubqp {
 
-constexpr int kBThreads = 256;
-constexpr int kBWarps = kBThreads / 32;
-
-enum Action : int32_t {
-    A_COPY_W_X = 1 << 0,
-    A_SAVE_BEST = 1 << 1,
-    A_LOB_SETUP = 1 << 2,
-    A_LOB_NORM = 1 << 3,
-    A_LOB_UPDATE = 1 << 4,
-    A_RESID = 1 << 5,
-    A_PENALTY = 1 << 6,
-    A_STEP_PABB = 1 << 7,
-    A_STEP_PPA = 1 << 8,
-    A_TRACE = 1 << 9,
-};
-enum USource : int32_t { U_NONE = 0, U_X, U_ROUND, U_DLX, U_DLW };
-
-struct Decision {
-    int32_t act;
-    int32_t usrc;
-    float alpha;   // BB step / penalty step
-    float lam;     // Ritz value (residual)
-    float c0, cx, cw, cp;
-    float eps_hp;
-    int32_t trace_k;
-};
-
-// deterministic start vector of the eigen-solver: uniform in (-1, 1) from a hash of i
-__device__ __forceinline__ float start_component(int i)
-{
-    uint32_t h = (uint32_t)i * 0x9E3779B1u + 0x7F4A7C15u;
-    h ^= h >> 15;
-    h *= 0x2C1B3C6Du;
-    h ^= h >> 12;
-    h *= 0x297A2D39u;
-    h ^= h >> 15;
-    return ((float)(h >> 8) + 0.5f) * (2.0f / 16777216.0f) - 1.0f;
-}
-
-// smallest eigenpair of a symmetric k x k matrix (k <= 3) by cyclic Jacobi rotations
-__device__ void small_sym_eig_min(int k, double M[3][3], double& lam, double v[3])
-{
-    double V[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
-    for (int sweep = 0; sweep < 12; ++sweep) {
-        double off = 0.0;
-        for (int p = 0; p < k; ++p)
-            for (int q = p + 1; q < k; ++q) off += M[p][q] * M[p][q];
-        if (off < 1e-30) break;
-        for (int p = 0; p < k; ++p)
-            for (int q = p + 1; q < k; ++q) {
-                if (M[p][q] == 0.0) continue;
-                double theta = (M[q][q] - M[p][p]) / (2.0 * M[p][q]);
-                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int r = 0; r < k; ++r) {  // M <- J^T M J
-                    double mrp = M[r][p], mrq = M[r][q];
-                    M[r][p] = c * mrp - s * mrq;
-                    M[r][q] = s * mrp + c * mrq;
-                }
-                for (int r = 0; r < k; ++r) {
-                    double mpr = M[p][r], mqr = M[q][r];
-                    M[p][r] = c * mpr - s * mqr;
-                    M[q][r] = s * mpr + c * mqr;
-                }
-                for (int r = 0; r < k; ++r) {
-                    double vrp = V[r][p], vrq = V[r][q];
-                    V[r][p] = c * vrp - s * vrq;
-                    V[r][q] = s * vrp + c * vrq;
-                }
-            }
-    }
-    int j = 0;
-    for (int t = 1; t < k; ++t)
-        if (M[t][t] < M[j][j]) j = t;
-    lam = M[j][j];
-    for (int r = 0; r < 3; ++r) v[r] = r < k ? V[r][j] : 0.0;
-}
-
-// Rayleigh-Ritz on span{x, w, p} (p only when has_p).  Returns false on breakdown.
-// Gram entries: ga = (xAx, xAw, xAp, wAw, wAp, pAp), gb = (xx, xw, xp, ww, wp, pp).
-__device__ bool rayleigh_ritz(const double ga[6], const double gb[6], bool has_p, double& lam,
-                              double c[3])
-{
-    double A[3][3] = {{ga[0], ga[1], ga[2]}, {ga[1], ga[3], ga[4]}, {ga[2], ga[4], ga[5]}};
-    double B[3][3] = {{gb[0], gb[1], gb[2]}, {gb[1], gb[3], gb[4]}, {gb[2], gb[4], gb[5]}};
-    int k = has_p ? 3 : 2;
-    if (!(B[0][0] > 0.0)) return false;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        if (k < 2) return false;
-        double sc[3];
-        bool bad = false;
-        for (int t = 0; t < k; ++t) {
-            if (!(B[t][t] > 0.0)) { bad = true; break; }
-            sc[t] = 1.0 / sqrt(B[t][t]);
-        }
-        if (bad) { k -= 1; continue; }
-        double As[3][3], Bs[3][3];
-        for (int r = 0; r < k; ++r)
-            for (int q = 0; q < k; ++q) {
-                As[r][q] = A[r][q] * sc[r] * sc[q];
-                Bs[r][q] = B[r][q] * sc[r] * sc[q];
-            }
-        // Cholesky Bs = L L^T with a conditioning guard (FP32 Gram entries)
-        double Lc[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        for (int j = 0; j < k && !bad; ++j) {
-            double s = Bs[j][j];
-            for (int t = 0; t < j; ++t) s -= Lc[j][t] * Lc[j][t];
-            if (!(s > 1e-6)) { bad = true; break; }
-            Lc[j][j] = sqrt(s);
-            for (int i = j + 1; i < k; ++i) {
-                double u = Bs[i][j];
-                for (int t = 0; t < j; ++t) u -= Lc[i][t] * Lc[j][t];
-                Lc[i][j] = u / Lc[j][j];
-            }
-        }
-        if (bad) { k -= 1; continue; }
-        // Li = L^-1 (lower triangular)
-        double Li[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        for (int j = 0; j < k; ++j) {
-            Li[j][j] = 1.0 / Lc[j][j];
-            for (int i = j + 1; i < k; ++i) {
-                double u = 0.0;
-                for (int t = j; t < i; ++t) u -= Lc[i][t] * Li[t][j];
-                Li[i][j] = u / Lc[i][i];
-            }
-        }
-        double M[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-        for (int r = 0; r < k; ++r)
-            for (int q = 0; q < k; ++q) {
-                double u = 0.0;
-                for (int a = 0; a < k; ++a)
-                    for (int b = 0; b < k; ++b) u += Li[r][a] * As[a][b] * Li[q][b];
-                M[r][q] = u;
-            }
-        double v[3];
-        small_sym_eig_min(k, M, lam, v);
-        for (int r = 0; r < 3; ++r) {  // c = sc * L^-T v
-            double u = 0.0;
-            for (int a = r; a < k; ++a) u += Li[a][r] * v[a];
-            c[r] = r < k ? u * sc[r] : 0.0;
-        }
-        return isfinite(lam);
-    }
-    return false;
-}
-
-__device__ __forceinline__ double csum_value(float2 v) { return (double)v.x + (double)v.y; }
-
-// Scalar decision of one lane (thread 0).  S is the lane state (shared memory).
-__device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, const Params& P, Decision& D)
-{
-    D.act = 0;
-    D.usrc = U_NONE;
-    D.alpha = 0.f;
-    D.lam = 0.f;
-    D.c0 = D.cx = D.cw = D.cp = 0.f;
-    D.eps_hp = P.eps_hp_rel * fmaxf(1.f, L.rabs_max);
-    D.trace_k = -1;
-    switch (S.phase) {
-    case PH_JACOBI: {
-        S.it += 1;
-        S.jac_iters += 1;
-        D.act |= A_COPY_W_X;
-        bool conv = R.m[0] <= P.jac_tol * fmaxf(R.m[1], 1e-30f) || S.it >= P.jac_max;
-        if (!conv) { D.usrc = U_X; break; }
-        S.it = 0;
-        if (L.stop_after & STOP_JACOBI) { S.phase = PH_DONE; break; }
-        S.phase = PH_EVAL;
-        D.usrc = U_ROUND;
-        break;
-    }
-    case PH_EVAL: {
-        double f = R.f;
-        float bin = R.m[0];
-        int active = (int)(R.s[0].x + R.s[0].y);
-        S.rho = fmaxf(fmaxf(1.f, 2.f * L.qmax_off), fmaxf(2.f * R.m[1], R.m[2]));
-        S.n_active = active;
-        if (f < S.best_f) {
-            S.best_f = f;
-            S.best_s = S.s;
-            D.act |= A_SAVE_BEST;
-        }
-        if (bin <= P.tol_outer || active == 0) { S.phase = PH_DONE; S.status = 0; break; }
-        if (S.s >= P.max_outer) { S.phase = PH_DONE; S.status = 1; break; }
-        S.phase = PH_LOB_INIT;
-        S.it = 0;
-        S.has_p = 0;
-        D.act |= A_LOB_SETUP;
-        D.usrc = U_DLX;
-        break;
-    }
-    case PH_LOB_INIT: {
-        double xax = csum_value(R.s[0]), xx = csum_value(R.s[1]);
-        double lam = xx > 0.0 ? xax / xx : 0.0;
-        S.lam = (float)lam;
-        S.has_p = 0;
-        S.it = 0;
-        D.act |= A_LOB_NORM | A_RESID;
-        D.c0 = xx > 0.0 ? (float)(1.0 / sqrt(xx)) : 0.f;
-        D.lam = (float)lam;
-        S.phase = PH_LOB;
-        D.usrc = U_DLW;
-        break;
-    }
-    case PH_LOB: {
-        S.it += 1;
-        S.lob_iters += 1;
-        double ga[6], gb[6];
-        for (int t = 0; t < 6; ++t) {
-            ga[t] = csum_value(R.s[t]);
-            gb[t] = csum_value(R.s[6 + t]);
-        }
-        bool conv = false;
-        double lam_old = S.lam, lam_new = lam_old, c[3] = {1, 0, 0};
-        if (!(gb[3] > 0.0)) {
-            conv = true;  // zero residual: x is an eigenvector
-        } else if (!rayleigh_ritz(ga, gb, S.has_p != 0, lam_new, c)) {
-            conv = true;  // breakdown: keep the last Ritz value
-            lam_new = lam_old;
-        } else if (lam_new > lam_old + 1e-3 * fabs(lam_old)) {
-            conv = true;  // LOBPCG is monotone in exact arithmetic: an increase is noise
-            lam_new = lam_old;
-        } else {
-            conv = (fabs(lam_new - lam_old) <= P.lob_tol * fmax(fabs(lam_new), 1e-30) && S.it >= 2) ||
-                   S.it >= P.lob_max;
-            S.lam = (float)lam_new;
-        }
-        if (!conv) {
-            D.act |= A_LOB_UPDATE | A_RESID;
-            D.cx = (float)c[0];
-            D.cw = (float)c[1];
-            D.cp = (float)c[2];
-            D.lam = (float)lam_new;
-            S.has_p = 1;
-            D.usrc = U_DLW;
-            break;
-        }
-        // Sec. 3.4: alpha = eta * lambda_min, or the resolution floor (see the design doc reading)
-        float lam = (float)lam_new;
-        float F = P.lambda_floor_rel * P.tol_inner * S.rho;
-        float alpha;
-        if (lam > F) {
-            alpha = P.eta * lam;
-            S.consec_fb = 0;
-        } else {
-            alpha = P.eta * ldexpf(F, min(S.consec_fb, 60));
-            S.consec_fb += 1;
-            S.floor_steps += 1;
-        }
-        S.lam = lam;
-        S.pen_alpha = alpha;
-        if (L.stop_after & STOP_LOB) { S.phase = PH_DONE; break; }
-        D.act |= A_PENALTY;
-        D.alpha = alpha;
-        S.phase = PH_INNER;
-        S.k = 0;
-        D.usrc = U_X;
-        break;
-    }
-    case PH_INNER: {
-        S.inner_iters += 1;
-        const int k = S.k;
-        if (k == 0) {
-            S.rho = fmaxf(fmaxf(1.f, 2.f * L.qmax_off), fmaxf(2.f * R.m[1], R.m[2]));
-            S.alpha = R.m[3] > 0.f ? 1.f / (2.f * R.m[3]) : 1.f;
-        }
-        int exit_code = -1;
-        if (R.m[0] / S.rho < P.tol_inner) exit_code = 0;
-        else if (k >= P.max_inner) exit_code = 1;
-        else if (L.method == 0 && k >= 1) {
-            double ss = csum_value(R.s[0]), sy = csum_value(R.s[1]), yy = csum_value(R.s[2]);
-            if (ss == 0.0) exit_code = 2;
-            else {
-                double a = (k & 1) ? ss / sy : sy / yy;
-                if (!(sy > 0.0) || !isfinite(a)) a = S.alpha;
-                a = fmin(fmax(a, (double)P.alpha_min), (double)P.alpha_max);
-                S.alpha = (float)a;
-            }
-        }
-        if (L.trace_len > 0 && k < L.trace_len && exit_code < 0) {
-            D.act |= A_TRACE;
-            D.trace_k = k;
-        }
-        if (L.trace_len > 0 && k < L.trace_len && exit_code >= 0) {
-            D.act |= A_TRACE;  // final iterate of the trace
-            D.trace_k = k;
-        }
-        if (exit_code < 0) {
-            D.act |= (L.method == 0) ? A_STEP_PABB : A_STEP_PPA;
-            D.alpha = S.alpha;
-            S.k = k + 1;
-            S.inner_steps += 1;
-            D.usrc = U_X;
-            break;
-        }
-        S.last_exit = exit_code;
-        S.s += 1;
-        if (P.hist) atomicAdd((unsigned long long*)&P.hist[min(k / 100, 100)], 1ull);
-        if (L.stop_after & STOP_INNER) { S.phase = PH_DONE; break; }
-        S.phase = PH_EVAL;
-        D.usrc = U_ROUND;
-        break;
-    }
-    default: break;
-    }
-}
-
 __global__ void __launch_bounds__(kBThreads) phase_b_kernel(TickArgs A, int32_t* active_count)
 {
-    __shared__ LaneState S;
-    __shared__ Partial R;
-    __shared__ Decision D;
-    __shared__ int32_t phase0;
-
-    const LaneDev& L = A.lanes[blockIdx.x];
-    if (L.mode == MODE_GRAD) return;
-    if (threadIdx.x == 0) {
-        S = *L.st;
-        phase0 = S.phase;
-    }
-    __syncthreads();
-    const int ph = phase0;
-    if (ph == PH_DONE) return;
-
-    // ---- reduce the partials of this lane
-    {
-        Acc a;
-        a.zero();
-        const int ns = phase_nsum(ph), nm = phase_nmax(ph);
-        for (int b = threadIdx.x; b < L.nblk; b += kBThreads) {
-            const Partial& p = L.part[b];
-#pragma unroll
-            for (int t = 0; t < 12; ++t)
-                if (t < ns) a.s[t] = csum_merge(a.s[t], p.s[t]);
-#pragma unroll
-            for (int t = 0; t < 6; ++t)
-                if (t < nm) a.m[t] = fmaxf(a.m[t], p.m[t]);
-            a.f += p.f;
-        }
-        __shared__ float2 sh_s[kBWarps][12];
-        __shared__ float sh_m[kBWarps][6];
-        __shared__ double sh_f[kBWarps];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-        for (int t = 0; t < 12; ++t)
-            if (t < ns) a.s[t] = csum_shfl_reduce(a.s[t]);
-#pragma unroll
-        for (int t = 0; t < 6; ++t)
-            if (t < nm) a.m[t] = max_shfl_reduce(a.m[t]);
-        a.f = dsum_shfl_reduce(a.f);
-        if (lane == 0) {
-#pragma unroll
-            for (int t = 0; t < 12; ++t) sh_s[warp][t] = a.s[t];
-#pragma unroll
-            for (int t = 0; t < 6; ++t) sh_m[warp][t] = a.m[t];
-            sh_f[warp] = a.f;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int t = 0; t < 12; ++t) R.s[t] = make_float2(0.f, 0.f);
-            for (int t = 0; t < 6; ++t) R.m[t] = 0.f;
-            R.f = 0.0;
-            for (int w = 0; w < kBWarps; ++w) {
-                for (int t = 0; t < 12; ++t) R.s[t] = csum_merge(R.s[t], sh_s[w][t]);
-                for (int t = 0; t < 6; ++t) R.m[t] = fmaxf(R.m[t], sh_m[w][t]);
-                R.f += sh_f[w];
-            }
-            decide(L, S, R, A.P, D);
-        }
-        __syncthreads();
-    }
-
-    // ---- element-wise update
-    const int n = L.n, ld = L.ld;
-    float* vec = L.vec;
-    const int act = D.act, usrc = D.usrc;
-    for (int i = threadIdx.x; i < n; i += kBThreads) {
-        float x = vec[V_X * ld + i];
-        if (act & A_TRACE) L.trace_x[(size_t)D.trace_k * n + i] = x;
-        if (act & A_COPY_W_X) {
-            x = vec[V_W * ld + i];
-            vec[V_X * ld + i] = x;
-        }
-        if (act & A_SAVE_BEST) L.best_x[i] = x > 0.5f ? 1 : 0;
-        if (act & A_LOB_SETUP) {
-            // Eq. (eq:alpha): z = x - x^2, I_alpha = {z > tau_z}, scaling z^-1/2
-            float z = x - x * x;
-            bool in = z > A.P.tau_z;
-            float Dz = in ? 1.0f / sqrtf(z) : 0.f;
-            float dmp = vec[V_DMP * ld + i];
-            vec[V_D * ld + i] = Dz;
-            vec[V_T * ld + i] = in ? z / fmaxf(fabsf(dmp), 1e-30f) : 0.f;
-            vec[V_LX * ld + i] = in ? start_component(i) : 0.f;
-            vec[V_LP * ld + i] = 0.f;
-            vec[V_LAP * ld + i] = 0.f;
-        }
-        if (act & A_LOB_NORM) {
-            float lx = vec[V_LX * ld + i] * D.c0;
-            vec[V_LX * ld + i] = lx;
-            vec[V_LAX * ld + i] = vec[V_W * ld + i] * D.c0;
-        }
-        if (act & A_LOB_UPDATE) {
-            float lx = vec[V_LX * ld + i], lw = vec[V_LW * ld + i], lp = vec[V_LP * ld + i];
-            float lax = vec[V_LAX * ld + i], aw = vec[V_W * ld + i], lap = vec[V_LAP * ld + i];
-            float np = fmaf(D.cw, lw, D.cp * lp);
-            float nap = fmaf(D.cw, aw, D.cp * lap);
-            vec[V_LX * ld + i] = fmaf(D.cx, lx, np);
-            vec[V_LAX * ld + i] = fmaf(D.cx, lax, nap);
-            vec[V_LP * ld + i] = np;
-            vec[V_LAP * ld + i] = nap;
-        }
-        if (act & A_RESID) {
-            float r = vec[V_LAX * ld + i] - D.lam * vec[V_LX * ld + i];
-            vec[V_LW * ld + i] = vec[V_T * ld + i] * r;
-        }
-        if (act & A_PENALTY) {
-            // Eq. (pp1): p <- p + alpha z with z = x - x^2
-            float z = x - x * x;
-            float p = fmaf(D.alpha, z, vec[V_P * ld + i]);
-            vec[V_P * ld + i] = p;
-            vec[V_DMP * ld + i] = L.d[i] - p;
-            vec[V_BBAR * ld + i] = L.bprime[i] + p;
-        }
-        if (act & A_STEP_PABB) {
-            // Eq. (x2): x <- P(x - alpha g)
-            vec[V_XPREV * ld + i] = x;
-            x = fminf(fmaxf(fmaf(-D.alpha, vec[V_G * ld + i], x), 0.f), 1.f);
-            vec[V_X * ld + i] = x;
-        }
-        if (act & A_STEP_PPA) {
-            // Eq. (x1): x <- P(x - g / (2 h_p)),  h_p = max(sum_j |Q'_ij| - p_i, eps)
-            float hp = fmaxf(L.rabs[i] - vec[V_P * ld + i], D.eps_hp);
-            vec[V_XPREV * ld + i] = x;
-            x = fminf(fmaxf(x - vec[V_G * ld + i] / (2.f * hp), 0.f), 1.f);
-            vec[V_X * ld + i] = x;
-        }
-        float u;
-        switch (usrc) {
-        case U_X: u = x; break;
-        case U_ROUND: u = x > 0.5f ? 1.f : 0.f; break;
-        case U_DLX: u = vec[V_D * ld + i] * vec[V_LX * ld + i]; break;
-        case U_DLW: u = vec[V_D * ld + i] * vec[V_LW * ld + i]; break;
-        default: u = 0.f; break;
-        }
-        if (usrc != U_NONE) {
-            if (L.mode == MODE_TC) {
-                __nv_bfloat16 hi = __float2bfloat16_rn(u);
-                L.u_hi[i] = hi;
-                if (L.u_lo) L.u_lo[i] = __float2bfloat16_rn(u - __bfloat162float(hi));
-            } else {
-                vec[V_U * ld + i] = u;
-            }
-        }
-    }
-    if (threadIdx.x == 0) {
-        if ((act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
-        *L.st = S;
-        if (S.phase != PH_DONE && active_count) atomicAdd(active_count, 1);
-    }
+    lane_update(A.lanes[blockIdx.x], A.P, active_count);
 }
 
 cudaError_t launch_phase_b(const TickArgs& a, int32_t* active_count, cudaStream_t s)

@@ -17,7 +17,7 @@ struct RefArgs {
     uint64_t seed;
     float* Qoff;            // GEMV: n x ld FP32 (or null)
     __nv_bfloat16* Qbf;     // TC: ld x ld BF16 (or null)
-    double* Qeval;          // GEMV: n x ld original (or null)
+    float2* Qeval;          // GEMV: n x ld original as (hi, lo) FP32 pairs (or null)
     float *d, *bprime, *oabs, *rabs, *tsum;   // tsum = d + b' formed in FP64
     double *borig, *qdb, *gamma;
     float* scal;            // [0] max_{i!=j} |Q'_ij| stored, [1] max rabs

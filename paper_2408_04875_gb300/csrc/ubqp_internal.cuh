@@ -100,7 +100,7 @@ struct LaneDev {
     int32_t restart;    // index of this start within its instance (TC operand row)
     int32_t trace_len;
     const float* Qoff;     // GEMV lanes: n x ld FP32, off-diagonal of Q' (zero diagonal)
-    const double* Qeval;   // GEMV lanes: n x ld FP64, the original Q
+    const float2* Qeval;   // GEMV lanes: n x ld, the original Q as FP32 (hi, lo) pairs
     const float* d;        // diag(Q')
     const float* bprime;   // b - gamma
     const float* tsum;     // diag(Q') + b' = (Q + mu)_ii + b_i, formed in FP64
@@ -112,6 +112,7 @@ struct LaneDev {
     uint8_t* best_x;       // ld bytes
     Partial* part;         // nblk partials
     LaneState* st;
+    unsigned int* counter; // phase-A blocks of the current tick that have finished
     __nv_bfloat16* u_hi;   // TC lanes: this lane's row of the packed B operand
     __nv_bfloat16* u_lo;
     float* trace_x;        // test hook: trace_len x n
@@ -369,6 +370,8 @@ struct TickArgs {
     int32_t rows_per_item;
     int32_t nlanes;
     int32_t max_ld;        // widest lane (shared-memory size of the GEMV kernel)
+    int32_t fused;         // GEMV lanes: the last phase-A CTA of a lane runs its update
+    int32_t* active_count; // incremented by every lane still active after this tick
     Params P;
 };
 
