@@ -166,6 +166,26 @@ int ubqp_penalized_eval(const void* Q, const void* b, const void* p, const void*
                         int64_t batch, int dtype, void* h_out, void* g_out, void* stream);
 
 /*
+ * ubqp_penalized_eval_noalloc - the computation of ubqp_penalized_eval (h and grad h of
+ * problem (p) for `batch` points, same arguments, same kernels) without any device
+ * allocation, for callers that cannot call cudaMalloc/cudaFree: code that owns all device
+ * memory through its own pool or a fixed memory budget, and code that cannot afford the
+ * device-wide synchronization those calls may cause.  The paper has no counterpart; this
+ * is an interface variant of this library.
+ *   Scratch: a static device array of UBQP_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ *   library holds until the process exits.  Limits: batch <= 256, n * element size <=
+ *   200 KiB, and batch * ceil(n / 256) <= 16384; larger requests return UBQP_EINVAL.
+ *   The first call on a device resolves the array's device address (cudaGetSymbolAddress),
+ *   so make that first call before any stream capture on that device.
+ *   All calls share the array and it keeps the last call's contents (each call rewrites
+ *   what it reads); calls that overlap on the GPU (other streams, other host threads) race.
+ *   All pointers are device memory; returns after synchronizing `stream`.
+ */
+#define UBQP_NOALLOC_SCRATCH_BYTES 2293760
+int ubqp_penalized_eval_noalloc(const void* Q, const void* b, const void* p, const void* x, int64_t n,
+                                int64_t batch, int dtype, void* h_out, void* g_out, void* stream);
+
+/*
  * ubqp_inner_run - test entry: Alg. 2 (or Alg. 1 when o->method = UBQP_PPA) on the
  * subproblem (p1) with a GIVEN reformulated matrix Qp = Q' (n x n, diagonal included),
  * bp = b', penalty p and start x0 (all FP64, host or device), on the FP32 GPU path.

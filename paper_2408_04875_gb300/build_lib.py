@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libubqp.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["engine.cu", "tick_gemv.cu", "tick_update.cu", "init.cu", "tc_gemm.cu"]
+SOURCES = ["engine.cu", "tick_gemv.cu", "tick_update.cu", "init.cu", "noalloc.cu", "tc_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
