@@ -58,7 +58,7 @@ __device__ __forceinline__ float start_component(int i)
 // smallest eigenpair of a symmetric k x k matrix (k <= 3) by cyclic Jacobi rotations.
 // FP32 throughout: FP64 runs at a small fraction of the FP32 rate on this part, and the
 // preconditioned basis keeps the 3 x 3 Gram matrices well scaled.
-__device__ void small_sym_eig_min(int k, float M[3][3], float& lam, float v[3])
+static __device__ void small_sym_eig_min(int k, float M[3][3], float& lam, float v[3])
 {
     float V[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
     for (int sweep = 0; sweep < 8; ++sweep) {
@@ -100,7 +100,7 @@ __device__ void small_sym_eig_min(int k, float M[3][3], float& lam, float v[3])
 
 // Rayleigh-Ritz on span{x, w, p} (p only when has_p), FP32.  Returns false on breakdown.
 // Gram entries: ga = (xAx, xAw, xAp, wAw, wAp, pAp), gb = (xx, xw, xp, ww, wp, pp).
-__device__ bool rayleigh_ritz(const float ga[6], const float gb[6], bool has_p, float& lam, float c[3])
+static __device__ bool rayleigh_ritz(const float ga[6], const float gb[6], bool has_p, float& lam, float c[3])
 {
     const float A[3][3] = {{ga[0], ga[1], ga[2]}, {ga[1], ga[3], ga[4]}, {ga[2], ga[4], ga[5]}};
     const float B[3][3] = {{gb[0], gb[1], gb[2]}, {gb[1], gb[3], gb[4]}, {gb[2], gb[4], gb[5]}};
@@ -169,7 +169,7 @@ __device__ bool rayleigh_ritz(const float ga[6], const float gb[6], bool has_p, 
 __device__ __forceinline__ float csum_value(float2 v) { return v.x + v.y; }
 
 // Scalar decision of one lane (thread 0).  S is the lane state (shared memory).
-__device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, const Params& P, Decision& D)
+static __device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, const Params& P, Decision& D)
 {
     D.act = 0;
     D.usrc = U_NONE;
@@ -329,7 +329,7 @@ __device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, const P
 
 // The update of one lane by one CTA of kBThreads threads (phase B).  Called by the
 // stand-alone phase-B kernel and by the last phase-A CTA of a lane in the fused GEMV tick.
-__device__ void lane_update(const LaneDev& L, const Params& P, int32_t* active_count)
+static __device__ void lane_update(const LaneDev& L, const Params& P, int32_t* active_count)
 {
     __shared__ LaneState S;
     __shared__ Partial R;
