@@ -216,6 +216,16 @@ int ubqp_penalty_probe(const double* Qp, const double* bp, const double* p, cons
 int ubqp_initial_point(const double* Q, const double* b, const double* mu, int64_t n,
                        const ubqp_opts* o, double* x0_out, double* gamma_out);
 
+/*
+ * ubqp_tc_matmul_probe - test entry: the tensor-core contraction of the batched path on
+ * its own, D = A (B_hi + B_lo)^T with FP32 accumulation, returned raw.
+ *   A n x n, B_hi and B_lo (B_lo may be NULL) R x n, all BF16 bit patterns in HOST memory,
+ *   row-major; D_out R x n FP32 host memory (row r = lane r).  cluster: CTAs splitting K
+ *   (1..8), 0 = picked by the library.  1 <= n <= 32768, 1 <= R <= 1024.
+ */
+int ubqp_tc_matmul_probe(const uint16_t* A, const uint16_t* B_hi, const uint16_t* B_lo, int64_t n, int64_t R,
+                         int32_t cluster, float* D_out);
+
 #ifdef __cplusplus
 }
 #endif

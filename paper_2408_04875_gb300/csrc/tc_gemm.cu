@@ -1,0 +1,535 @@
+// Phase A on the 5th-generation tensor cores: the matvecs of all starts of an instance as
+// one contraction  D = Q_off * U^T  (Q_off in BF16, U = the lanes' inputs as BF16 hi + lo
+// rows, FP32 accumulation in TMEM), for the batched-restart and ragged paths.
+//
+// Tiling.  One CTA owns a 128-row M tile of one instance, an N tile of up to 256 lanes and
+// a slice of the K dimension; the S CTAs of a thread-block cluster share the M/N tile and
+// split K.  A (128 x 64) and B (N x 64) k-blocks arrive by TMA in 128-byte-swizzled tiles
+// into a shared-memory ring; one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
+// M = 128, K = 16 per instruction, the lo term as a second MMA into the same accumulator)
+// and tcgen05.commit frees ring slots.  The accumulators are then read with tcgen05.ld,
+// parked in shared memory and summed across the cluster through distributed shared memory;
+// every CTA finishes a subset of the lanes with the per-row epilogue of the lane's phase.
+//
+// Every mbarrier wait is bounded (2 s of globaltimer); on expiry the CTA records an error,
+// stops issuing work, still passes every cluster barrier and frees its TMEM.
+#include <cooperative_groups.h>
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "../../include/ubqp.h"
+#include "ubqp_engine.cuh"
+#include "ubqp_tc.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ubqp {
+
+namespace {
+
+constexpr int kTcThreads = 128;       // 4 warps: TMA producer, MMA issuer, then all 4 do the epilogue
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bounded parity wait: false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t addr = smem_u32(bar);
+    const uint64_t t0 = globaltimer();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major operand in 128-byte-swizzled 8-row atoms
+// (rows of 128 bytes, 1024 bytes between 8-row groups), descriptor version 1
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;            // leading byte offset (not used by swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;            // version
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
+{
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// warp-level reduction of one lane's accumulator into its partial record (lane 0 writes)
+__device__ __forceinline__ void warp_reduce_write(Acc& a, int ph, Partial* out, bool has_f)
+{
+    const int ns = phase_nsum(ph), nm = phase_nmax(ph);
+#pragma unroll
+    for (int t = 0; t < 12; ++t)
+        if (t < ns) a.s[t] = csum_shfl_reduce(a.s[t]);
+#pragma unroll
+    for (int t = 0; t < 6; ++t)
+        if (t < nm) a.m[t] = max_shfl_reduce(a.m[t]);
+    if (has_f) a.f = dsum_shfl_reduce(a.f);
+    if ((threadIdx.x & 31) == 0) {
+        Partial P;
+#pragma unroll
+        for (int t = 0; t < 12; ++t) P.s[t] = a.s[t];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) P.m[t] = a.m[t];
+        P.f = has_f ? a.f : 0.0;
+        *out = P;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned ring
+    unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ uint64_t full_bar[kTcMaxStages], empty_bar[kTcMaxStages], accum_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_inst, s_mt, s_nt, s_skip;
+    __shared__ int s_fail;
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int S = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // ---- which tile: clusters are consecutive blocks
+    if (threadIdx.x == 0) {
+        const int c = blockIdx.x / S;
+        int lo = 0, hi = A.ninst - 1;   // last instance whose first cluster index <= c
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (A.inst[mid].cluster0 <= c) lo = mid; else hi = mid - 1;
+        }
+        const TcInst& I = A.inst[lo];
+        const int local = c - I.cluster0;
+        s_inst = lo;
+        s_mt = local / I.n_tiles;
+        s_nt = local % I.n_tiles;
+        s_fail = 0;
+        // a tile whose lanes are all finished is skipped by every CTA of the cluster
+        int alive = A.raw ? 1 : 0;
+        if (!A.raw) {
+            const int r0 = s_nt * I.bn, r1 = min(I.R, r0 + I.bn);
+            for (int r = r0; r < r1 && !alive; ++r) alive = A.lanes[I.lane0 + r].st->phase != PH_DONE;
+        }
+        s_skip = !alive;
+    }
+    __syncthreads();
+    const TcInst& I = A.inst[s_inst];
+    const int mt = s_mt, nt = s_nt;
+    const int BN = I.bn;
+    const bool two = I.two_terms != 0;
+    const int kb_total = I.ld / 64;
+    const int kb0 = (int)((int64_t)kb_total * rank / S), kb1 = (int)((int64_t)kb_total * (rank + 1) / S);
+    const int nkb = kb1 - kb0;
+    const uint32_t a_bytes = 128 * 128, b_bytes = (uint32_t)BN * 128;
+    const uint32_t stage_bytes = a_bytes + b_bytes * (two ? 2u : 1u);
+    const int NS = A.stages;
+
+    if (!s_skip) {
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < NS; ++s) {
+                mbar_init(&full_bar[s], 1);
+                mbar_init(&empty_bar[s], 1);
+            }
+            mbar_init(&accum_bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        if (warp == 1) tmem_alloc(&tmem_base, (uint32_t)A.tmem_cols);
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+
+    if (!s_skip && nkb > 0) {
+        const uint32_t tmem = tmem_base;
+        if (warp == 0 && lane == 0) {
+            // TMA producer
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % NS;
+                if (kb >= NS && !mbar_wait(&empty_bar[s], (uint32_t)((kb / NS - 1) & 1))) { s_fail = 1; break; }
+                issued = kb + 1;
+                unsigned char* st = ring + (size_t)s * stage_bytes;
+                mbar_expect_tx(&full_bar[s], stage_bytes);
+                const int kx = (kb0 + kb) * 64;
+                tma_load_2d(st, &I.tmA, &full_bar[s], kx, mt * 128);
+                tma_load_2d(st + a_bytes, &I.tmBhi, &full_bar[s], kx, nt * BN);
+                if (two) tma_load_2d(st + a_bytes + b_bytes, &I.tmBlo, &full_bar[s], kx, nt * BN);
+            }
+            if (s_fail) {
+                // a wait ran out: let every copy already issued land before the ring is reused
+                for (int kb = (issued > NS ? issued - NS : 0); kb < issued; ++kb)
+                    mbar_wait(&full_bar[kb % NS], (uint32_t)((kb / NS) & 1));
+            }
+        } else if (warp == 1 && lane == 0) {
+            // MMA issuer: 4 K-steps of 16 per 64-wide k-block, hi then lo term
+            const uint32_t idesc = idesc_bf16(128, BN);
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % NS;
+                if (!mbar_wait(&full_bar[s], (uint32_t)((kb / NS) & 1))) { s_fail = 1; break; }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(ring + (size_t)s * stage_bytes);
+                const uint32_t sb = sa + a_bytes;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint64_t ad = sdesc_sw128(sa + k * 32);
+                    umma_bf16(tmem, ad, sdesc_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+                    if (two) umma_bf16(tmem, ad, sdesc_sw128(sb + b_bytes + k * 32), idesc, 1u);
+                }
+                umma_commit(&empty_bar[s]);
+            }
+            umma_commit(&accum_bar);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // ---- accumulators -> shared memory P[col][row] (the ring is free once accum_bar fired)
+    float* P = reinterpret_cast<float*>(ring);
+    if (!s_skip) {
+        bool ok = true;
+        if (nkb > 0) {
+            ok = !s_fail && mbar_wait(&accum_bar, 0u);
+            tc_fence_after();
+        }
+        const int row = warp * 32 + lane;
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            float v[32];
+            if (nkb > 0 && ok) {
+                tmem_ld32(tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) P[(c0 + i) * 128 + row] = v[i];
+        }
+        if (!ok) {
+            s_fail = 1;
+            if (A.err) atomicExch(A.err, 1);
+        }
+        tc_fence_before();
+    }
+    cluster.sync();
+
+    // ---- sum the cluster's partial accumulators and run the epilogue for this CTA's lanes
+    if (!s_skip) {
+        const int nreal = min(BN, I.R - nt * BN);
+        const int c0 = (int)((int64_t)nreal * rank / S), c1 = (int)((int64_t)nreal * (rank + 1) / S);
+        float* peers[8];
+        for (int q = 0; q < S; ++q) peers[q] = cluster.map_shared_rank(P, q);
+        for (int c = c0 + warp; c < c1; c += 4) {
+            const int r = nt * BN + c;  // restart index within the instance
+            float vv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int row = lane + 32 * j;
+                float acc = 0.f;
+                for (int q = 0; q < S; ++q) acc += peers[q][c * 128 + row];
+                vv[j] = acc;
+            }
+            if (A.raw) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = mt * 128 + lane + 32 * j;
+                    if (i < I.n) A.raw[(size_t)r * I.ld + i] = vv[j];
+                }
+                continue;
+            }
+            const LaneDev& L = A.lanes[I.lane0 + r];
+            const int ph = L.st->phase;
+            if (ph == PH_DONE) continue;
+            const int k = L.st->k;
+            Acc a;
+            a.zero();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = mt * 128 + lane + 32 * j;
+                if (i < I.n) row_epilogue(L, ph, k, i, (double)vv[j], a, A.P.tau_z);
+            }
+            warp_reduce_write(a, ph, L.part + mt, ph == PH_EVAL);
+        }
+    }
+    cluster.sync();  // peers' shared memory stays alive until every CTA has read it
+
+    if (!s_skip) {
+        __syncthreads();
+        if (warp == 1) {
+            tc_fence_after();
+            tmem_dealloc(tmem_base, (uint32_t)A.tmem_cols);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+static int pow2_at_least(int v)
+{
+    int p = 32;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+size_t tc_smem_bytes(int bn, bool two, int stages)
+{
+    const size_t stage = 128 * 128 + (size_t)bn * 128 * (two ? 2 : 1);
+    const size_t ring = std::max(stage * stages, (size_t)bn * 128 * 4);  // reused for the accumulators
+    return ring + 1024;  // alignment slack
+}
+
+int tc_pick_stages(int bn, bool two)
+{
+    const size_t stage = 128 * 128 + (size_t)bn * 128 * (two ? 2 : 1);
+    int s = (int)((200 * 1024) / stage);
+    if (s > kTcMaxStages) s = kTcMaxStages;
+    if (s < 2) s = 2;
+    return s;
+}
+
+cudaError_t tc_launch(const TcArgs& a, int total_clusters, int S, cudaStream_t st)
+{
+    size_t smem = tc_smem_bytes(a.max_bn, a.two_any != 0, a.stages);
+    cudaError_t e = cudaFuncSetAttribute(phase_a_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(total_clusters * S), 1, 1);
+    cfg.blockDim = dim3(kTcThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, phase_a_tc_kernel, a);
+}
+
+int tc_max_active_clusters(int bn, bool two, int stages, int S)
+{
+    size_t smem = tc_smem_bytes(bn, two, stages);
+    if (cudaFuncSetAttribute(phase_a_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(S * 64), 1, 1);
+    cfg.blockDim = dim3(kTcThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, phase_a_tc_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+int tc_tmem_cols(int bn) { return pow2_at_least(bn); }
+
+int tc_pick_cluster(int tiles, int kb_min, int bn, bool two, int stages, int num_sms)
+{
+    int best = 1;
+    for (int S = 1; S <= 8; ++S) {
+        if (tiles * S > num_sms) break;
+        if (kb_min / S < 2 && S > 1) break;
+        if (tc_max_active_clusters(bn, two, stages, S) < tiles) continue;
+        best = S;
+    }
+    return best;
+}
+
+// 2-D BF16 tensor map over a row-major [rows][cols] array, box 64 (cols) x box_rows
+CUresult tc_encode_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1u, 1u};
+    return cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+}
+
+}  // namespace ubqp
+
+// =====================================================================================
+// Test entry: D = A * (B_hi + B_lo)^T through the tensor-core kernel, raw output.
+using namespace ubqp;
+
+extern "C" int ubqp_tc_matmul_probe(const uint16_t* A, const uint16_t* Bhi, const uint16_t* Blo, int64_t n,
+                                    int64_t R, int32_t cluster, float* D_out)
+{
+    if (!A || !Bhi || !D_out || n < 1 || n > 32768 || R < 1 || R > 1024 || cluster < 0 || cluster > 8)
+        return UBQP_EINVAL;
+    const int ld = (int)((n + 127) / 128 * 128);
+    const int rpad = (int)((R + 15) / 16 * 16);
+    const int bn = rpad < 256 ? rpad : 256;
+    const int n_tiles = (rpad + bn - 1) / bn;
+    const int rows_b = n_tiles * bn;
+    const bool two = Blo != nullptr;
+    int dev = 0, nsm = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess) return UBQP_ECUDA;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t bytesA = (size_t)ld * ld * 2, bytesB = (size_t)rows_b * ld * 2, bytesD = (size_t)R * ld * 4;
+    char* buf = nullptr;
+    const size_t off_bhi = (bytesA + 255) / 256 * 256;
+    const size_t off_blo = off_bhi + (bytesB + 255) / 256 * 256;
+    const size_t off_d = off_blo + (bytesB + 255) / 256 * 256;
+    const size_t off_inst = off_d + (bytesD + 255) / 256 * 256;
+    const size_t off_err = off_inst + 1024;
+    if (cudaMalloc(&buf, off_err + 256) != cudaSuccess) return UBQP_ENOMEM;
+    int rc = UBQP_OK;
+    do {
+        if (cudaMemset(buf, 0, off_err + 256) != cudaSuccess) { rc = UBQP_ECUDA; break; }
+        if (cudaMemcpy2D(buf, (size_t)ld * 2, A, (size_t)n * 2, (size_t)n * 2, (size_t)n, cudaMemcpyHostToDevice) !=
+                cudaSuccess ||
+            cudaMemcpy2D(buf + off_bhi, (size_t)ld * 2, Bhi, (size_t)n * 2, (size_t)n * 2, (size_t)R,
+                         cudaMemcpyHostToDevice) != cudaSuccess ||
+            (two && cudaMemcpy2D(buf + off_blo, (size_t)ld * 2, Blo, (size_t)n * 2, (size_t)n * 2, (size_t)R,
+                                 cudaMemcpyHostToDevice) != cudaSuccess)) {
+            rc = UBQP_ECUDA;
+            break;
+        }
+        TcInst h;
+        memset(&h, 0, sizeof(h));
+        if (tc_encode_map(&h.tmA, buf, ld, ld, 128) != CUDA_SUCCESS ||
+            tc_encode_map(&h.tmBhi, buf + off_bhi, rows_b, ld, bn) != CUDA_SUCCESS ||
+            tc_encode_map(&h.tmBlo, buf + off_blo, rows_b, ld, bn) != CUDA_SUCCESS) {
+            rc = UBQP_ECUDA;
+            break;
+        }
+        h.n = (int)n;
+        h.ld = ld;
+        h.R = (int)R;
+        h.lane0 = 0;
+        h.m_tiles = ld / 128;
+        h.n_tiles = n_tiles;
+        h.bn = bn;
+        h.two_terms = two ? 1 : 0;
+        h.cluster0 = 0;
+        if (cudaMemcpy(buf + off_inst, &h, sizeof(h), cudaMemcpyHostToDevice) != cudaSuccess) { rc = UBQP_ECUDA; break; }
+        TcArgs a;
+        memset(&a, 0, sizeof(a));
+        a.inst = reinterpret_cast<const TcInst*>(buf + off_inst);
+        a.ninst = 1;
+        a.stages = tc_pick_stages(bn, two);
+        a.tmem_cols = tc_tmem_cols(bn);
+        a.max_bn = bn;
+        a.two_any = two ? 1 : 0;
+        a.raw = reinterpret_cast<float*>(buf + off_d);
+        a.err = reinterpret_cast<int32_t*>(buf + off_err);
+        const int tiles = h.m_tiles * h.n_tiles;
+        const int S = cluster > 0 ? cluster : tc_pick_cluster(tiles, ld / 64, bn, two, a.stages, nsm);
+        if (tc_launch(a, tiles, S, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+            rc = UBQP_ECUDA;
+            break;
+        }
+        int32_t err = 0;
+        cudaMemcpy(&err, a.err, 4, cudaMemcpyDeviceToHost);
+        if (err) { rc = UBQP_ETIMEOUT; break; }
+        if (cudaMemcpy2D(D_out, (size_t)n * 4, a.raw, (size_t)ld * 4, (size_t)n * 4, (size_t)R,
+                         cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = UBQP_ECUDA;
+    } while (0);
+    cudaFree(buf);
+    return rc;
+}

@@ -1,0 +1,48 @@
+// Tensor-core phase A (tc_gemm.cu): per-instance tile table and launch arguments.
+#pragma once
+
+#include <cuda.h>
+
+#include "ubqp_internal.cuh"
+
+namespace ubqp {
+
+constexpr int kTcMaxStages = 4;
+
+// One instance of the batched path: BF16 Q_off (ld x ld) and its lanes' packed inputs
+// (hi and lo terms, R rows of ld), with the TMA descriptors of all three.
+struct alignas(128) TcInst {
+    CUtensorMap tmA;     // Q_off, box 64 x 128
+    CUtensorMap tmBhi;   // lane inputs (hi term), box 64 x bn
+    CUtensorMap tmBlo;   // lane inputs (lo term), box 64 x bn
+    int32_t n, ld, R, lane0;
+    int32_t m_tiles, n_tiles, bn, two_terms;
+    int32_t cluster0;    // first cluster of this instance in the launch
+    int32_t pad_[3];
+};
+
+struct TcArgs {
+    const TcInst* inst;
+    int32_t ninst;
+    int32_t stages;
+    int32_t tmem_cols;
+    int32_t max_bn;
+    int32_t two_any;     // some instance carries the lo term (shared-memory sizing)
+    const LaneDev* lanes;
+    float* raw;          // probe mode: D written as [lane][row] (ld stride) instead of the epilogue
+    int32_t* err;        // set when a bounded wait ran out
+    Params P;
+};
+
+size_t tc_smem_bytes(int bn, bool two, int stages);
+int tc_pick_stages(int bn, bool two);
+cudaError_t tc_launch(const TcArgs& a, int total_clusters, int S, cudaStream_t st);
+int tc_max_active_clusters(int bn, bool two, int stages, int S);
+int tc_tmem_cols(int bn);
+CUresult tc_encode_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows);
+
+// cluster size for a launch of `tiles` output tiles: the largest S <= 8 such that every
+// cluster is resident at once, one CTA per SM, and each CTA keeps >= 2 k-blocks
+int tc_pick_cluster(int tiles, int kb_min, int bn, bool two, int stages, int num_sms);
+
+}  // namespace ubqp
