@@ -74,6 +74,11 @@ typedef struct {
     int64_t phase_a_bytes;   /* algorithmic bytes of those launches: stored matrix     */
                              /* entries of every active lane once, plus its vectors    */
     int64_t kernel_launches; /* launches of this library's kernels during the call      */
+    double ms_to_target;     /* device time until some lane's best objective reached    */
+                             /* opts->target_objective (-1: not reached / not set)      */
+    int64_t phase_a_flops;   /* algorithmic flops of the tensor-core launches timed     */
+    int32_t cluster_size;    /* CTAs per cluster of the tensor-core launches (0: none)  */
+    int32_t pad_;
     int64_t inner_hist[UBQP_HIST_BINS]; /* projected steps per subproblem (Fig. 5)   */
 } ubqp_stats;
 
@@ -102,6 +107,10 @@ typedef struct {
     int jacobi_max_iter;     /* sweeps for x^0: 60                                      */
     int max_ticks_per_sync;  /* ticks launched between host checks: 64                 */
     int profile_kernels;     /* 1: time every phase-A launch with CUDA events: 0       */
+    int stop_at_target;      /* 1: stop once target_objective is reached: 0            */
+    int tc_cluster;          /* CTAs splitting K in the tensor-core kernel, 1..8;      */
+                             /* 0 = chosen by the library's tuner                      */
+    double target_objective; /* objective to time against (used when finite)           */
     void* stream;            /* cudaStream_t, NULL = default stream                    */
     const double* const* mu; /* optional perturbations, one n x n matrix per instance   */
                              /* (symmetric); NULL = drawn from seed when sigma_rel > 0 */
@@ -145,7 +154,10 @@ int ubqp_solve(const double* Q, const double* b, int64_t n, const ubqp_opts* o,
  * With o->precision = UBQP_BF16X2_TC / UBQP_BF16_TC the matvecs of all starts of an
  * instance run as one BF16 tensor-core contraction (Q off-diagonal in BF16, the iterate
  * split into two BF16 terms for X2, FP32 accumulation); the perturbation then touches
- * only the diagonal (kept in FP32), since BF16 cannot carry it off the diagonal.
+ * only the diagonal (kept in FP32), since BF16 cannot carry it off the diagonal.  These
+ * precisions require every off-diagonal entry to be exactly representable in BF16 (for
+ * example integers of magnitude <= 256), so that rounded points are evaluated exactly;
+ * otherwise the call returns UBQP_ENOTSUP.
  */
 int ubqp_solve_batched(int32_t num, const int64_t* n, const double* const* Q,
                        const double* const* b, const ubqp_opts* o, uint8_t* const* x_out,

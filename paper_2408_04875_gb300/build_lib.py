@@ -64,7 +64,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             if lg.strip():
                 print(f"--- {s}\n{lg}", file=sys.stderr)
     tmp = OUT + f".{os.getpid()}.tmp"
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcuda", "-lcudart"]
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

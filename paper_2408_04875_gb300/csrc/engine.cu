@@ -19,6 +19,7 @@
 
 #include "../../include/ubqp.h"
 #include "ubqp_engine.cuh"
+#include "ubqp_tc.cuh"
 
 namespace ubqp {
 
@@ -129,6 +130,7 @@ static int check_opts(const ubqp_opts& o)
     if (o.lobpcg_max_iter < 1 || o.jacobi_max_iter < 1) { set_error("iteration caps must be >= 1"); return UBQP_EINVAL; }
     if (o.max_ticks_per_sync < 1 || o.max_ticks_per_sync > 4096) { set_error("max_ticks_per_sync out of range"); return UBQP_EINVAL; }
     if (!(o.sigma_rel >= 0.0) || !(o.gamma_margin > 0.0)) { set_error("sigma_rel >= 0 and gamma_margin > 0 required"); return UBQP_EINVAL; }
+    if (o.tc_cluster < 0 || o.tc_cluster > 8) { set_error("tc_cluster must be in [0, 8]"); return UBQP_EINVAL; }
     return UBQP_OK;
 }
 
@@ -157,6 +159,7 @@ struct InstDev {
     bool Q_host, b_host, mu_host, starts_host;
     size_t o_Qoff, o_Qbf, o_Qeval, o_d, o_bp, o_oabs, o_rabs, o_tsum, o_borig, o_qdb, o_gamma;
     size_t o_Uhi, o_Ulo;
+    int bn, n_tiles, rows_b;   // tensor-core tiling of this instance's lanes
     int lane0, nl;
 };
 
@@ -284,11 +287,17 @@ class Solver {
         }
         if (tc) {
             for (InstDev& I : inst_) {
-                int rpad = (int)round_up((size_t)I.nl, 16);
-                I.o_Uhi = ar_.reserve((size_t)rpad * I.ld * 2);
-                I.o_Ulo = o_.precision == UBQP_BF16X2_TC ? ar_.reserve((size_t)rpad * I.ld * 2) : 0;
+                const int rpad = (int)round_up((size_t)I.nl, 16);
+                I.bn = rpad < 256 ? rpad : 256;
+                I.n_tiles = (rpad + I.bn - 1) / I.bn;
+                I.rows_b = I.n_tiles * I.bn;
+                I.o_Uhi = ar_.reserve((size_t)I.rows_b * I.ld * 2);
+                I.o_Ulo = o_.precision == UBQP_BF16X2_TC ? ar_.reserve((size_t)I.rows_b * I.ld * 2) : 0;
             }
+            o_tcinst_ = ar_.reserve(inst_.size() * sizeof(TcInst));
+            o_tcerr_ = ar_.reserve(sizeof(int32_t));
         }
+        o_flops_ = ar_.reserve(sizeof(unsigned long long));
         o_states_ = ar_.reserve(lanes.size() * sizeof(LaneState));
         o_counters_ = ar_.reserve(lanes.size() * sizeof(unsigned int));
         o_lanes_ = ar_.reserve(lanes.size() * sizeof(LaneDev));
@@ -308,6 +317,7 @@ class Solver {
         if (rc) return rc;
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_hist_), 0, UBQP_HIST_BINS * sizeof(int64_t), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_bytes_), 0, sizeof(unsigned long long), stream_));
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_flops_), 0, sizeof(unsigned long long), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_counters_), 0, lanes.size() * sizeof(unsigned int), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_valid_), 0, insts.size() * 4 * sizeof(float), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_scal_), 0, insts.size() * 4 * sizeof(float), stream_));
@@ -418,6 +428,11 @@ class Solver {
         UBQP_CK(cudaStreamSynchronize(stream_));
         inexact_ = false;
         for (int v : inexact) inexact_ |= (v != 0);
+        if (tc && inexact_) {
+            set_error("tensor-core precision needs every off-diagonal entry exactly representable in BF16; "
+                      "use UBQP_FP32 for this data");
+            return UBQP_ENOTSUP;
+        }
         // ---- lane descriptors
         std::vector<int2> items;
         items.reserve((size_t)nitems);
@@ -459,10 +474,46 @@ class Solver {
                                     cudaMemcpyHostToDevice, stream_));
         if (tc) {
             for (InstDev& I : inst_) {
-                int rpad = (int)round_up((size_t)I.nl, 16);
-                UBQP_CK(cudaMemsetAsync(ar_.at<char>(I.o_Uhi), 0, (size_t)rpad * I.ld * 2, stream_));
-                if (I.o_Ulo) UBQP_CK(cudaMemsetAsync(ar_.at<char>(I.o_Ulo), 0, (size_t)rpad * I.ld * 2, stream_));
+                UBQP_CK(cudaMemsetAsync(ar_.at<char>(I.o_Uhi), 0, (size_t)I.rows_b * I.ld * 2, stream_));
+                if (I.o_Ulo) UBQP_CK(cudaMemsetAsync(ar_.at<char>(I.o_Ulo), 0, (size_t)I.rows_b * I.ld * 2, stream_));
             }
+            UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_tcerr_), 0, sizeof(int32_t), stream_));
+            // tile table with the TMA descriptors of every instance
+            std::vector<TcInst> ti(inst_.size());
+            int cl = 0, kb_min = 1 << 30;
+            max_bn_ = 16;
+            for (size_t t = 0; t < inst_.size(); ++t) {
+                InstDev& I = inst_[t];
+                TcInst& h = ti[t];
+                memset(&h, 0, sizeof(h));
+                const void* ub = ar_.at<char>(I.o_Uhi);
+                const void* lb = I.o_Ulo ? (const void*)ar_.at<char>(I.o_Ulo) : ub;
+                if (tc_encode_map(&h.tmA, ar_.at<char>(I.o_Qbf), I.ld, I.ld, 128) != CUDA_SUCCESS ||
+                    tc_encode_map(&h.tmBhi, ub, I.rows_b, I.ld, I.bn) != CUDA_SUCCESS ||
+                    tc_encode_map(&h.tmBlo, lb, I.rows_b, I.ld, I.bn) != CUDA_SUCCESS) {
+                    set_error("cuTensorMapEncodeTiled failed for instance %zu", t);
+                    return UBQP_ECUDA;
+                }
+                h.n = (int)I.n;
+                h.ld = I.ld;
+                h.R = I.nl;
+                h.lane0 = I.lane0;
+                h.m_tiles = I.ld / 128;
+                h.n_tiles = I.n_tiles;
+                h.bn = I.bn;
+                h.two_terms = I.o_Ulo ? 1 : 0;
+                h.cluster0 = cl;
+                cl += h.m_tiles * h.n_tiles;
+                kb_min = std::min(kb_min, I.ld / 64);
+                max_bn_ = std::max(max_bn_, I.bn);
+            }
+            tc_tiles_ = cl;
+            UBQP_CK(cudaMemcpyAsync(ar_.at<TcInst>(o_tcinst_), ti.data(), ti.size() * sizeof(TcInst),
+                                    cudaMemcpyHostToDevice, stream_));
+            const bool two = o_.precision == UBQP_BF16X2_TC;
+            tc_stages_ = tc_pick_stages(max_bn_, two);
+            tc_S_ = o_.tc_cluster > 0 ? o_.tc_cluster
+                                      : tc_pick_cluster(tc_tiles_, kb_min, max_bn_, two, tc_stages_, num_sms_);
         }
         LaneInitArgs lia;
         lia.lanes = ar_.at<LaneDev>(o_lanes_);
@@ -493,7 +544,22 @@ class Solver {
         UBQP_CK(cudaMallocHost(&h_active_, sizeof(int32_t)));
         if (!tc_ && nitems_ > 0) UBQP_CK(prepare_phase_a_gemv(max_ld_));
         const int T = o_.max_ticks_per_sync;
-        const bool has_a = !tc_ && nitems_ > 0;
+        const bool has_a = (!tc_ && nitems_ > 0) || (tc_ && tc_tiles_ > 0);
+        TcArgs tca;
+        memset(&tca, 0, sizeof(tca));
+        if (tc_) {
+            tca.inst = ar_.at<TcInst>(o_tcinst_);
+            tca.ninst = (int)inst_.size();
+            tca.stages = tc_stages_;
+            tca.tmem_cols = tc_tmem_cols(max_bn_);
+            tca.max_bn = max_bn_;
+            tca.two_any = o_.precision == UBQP_BF16X2_TC ? 1 : 0;
+            tca.lanes = ar_.at<LaneDev>(o_lanes_);
+            tca.raw = nullptr;
+            tca.err = ar_.at<int32_t>(o_tcerr_);
+            tca.flops = prof ? ar_.at<unsigned long long>(o_flops_) : nullptr;
+            tca.P = ta.P;
+        }
         if (prof && has_a) {
             evA_.resize(2 * T);
             for (auto& e : evA_) UBQP_CK(cudaEventCreate(&e));
@@ -501,7 +567,7 @@ class Solver {
 
         // GEMV lanes: one fused kernel per tick (the last CTA of each lane updates it);
         // tensor-core lanes: contraction kernel, then the stand-alone update kernel
-        const bool fused = has_a;
+        const bool fused = has_a && !tc_;
         auto enqueue = [&](int nt) -> cudaError_t {
             for (int t = 0; t < nt; ++t) {
                 cudaError_t e = cudaSuccess;
@@ -512,11 +578,13 @@ class Solver {
                 }
                 if (prof && has_a) e = cudaEventRecord(evA_[2 * t], stream_);
                 if (e != cudaSuccess) return e;
-                if (has_a) {
+                if (has_a && !tc_) {
                     TickArgs tt = ta;
                     tt.fused = 1;
                     tt.active_count = last ? d_active : nullptr;
                     e = launch_phase_a_gemv_f32(tt, stream_);
+                } else if (has_a) {
+                    e = tc_launch(tca, tc_tiles_, tc_S_, stream_);
                 }
                 if (e != cudaSuccess) return e;
                 if (prof && has_a) e = cudaEventRecord(evA_[2 * t + 1], stream_);
@@ -560,6 +628,29 @@ class Solver {
                     phase_a_ms_ += ms;
                 }
                 phase_a_launches_ += T;
+            }
+            if (tc_) {
+                int32_t err = 0;
+                UBQP_CK(cudaMemcpy(&err, ar_.at<int32_t>(o_tcerr_), sizeof(err), cudaMemcpyDeviceToHost));
+                if (err) {
+                    set_error("a bounded wait in the tensor-core kernel ran out");
+                    return UBQP_ETIMEOUT;
+                }
+            }
+            if (std::isfinite(o_.target_objective) && ms_to_target_ < 0.0) {
+                std::vector<LaneState> st(nlanes_);
+                UBQP_CK(cudaMemcpy(st.data(), ar_.at<LaneState>(o_states_), st.size() * sizeof(LaneState),
+                                   cudaMemcpyDeviceToHost));
+                double best = INFINITY;
+                for (const LaneState& x : st) best = std::min(best, x.best_f);
+                if (best <= o_.target_objective) {
+                    UBQP_CK(cudaEventRecord(ev1_, stream_));
+                    UBQP_CK(cudaEventSynchronize(ev1_));
+                    float m = 0.f;
+                    cudaEventElapsedTime(&m, ev0_, ev1_);
+                    ms_to_target_ = m;
+                    if (o_.stop_at_target) break;
+                }
             }
             if (*h_active_ == 0) break;
             if (ticks > cap) {
@@ -652,6 +743,12 @@ class Solver {
         UBQP_CK(cudaStreamSynchronize(stream_));
         s->phase_a_bytes = (int64_t)by;
         s->kernel_launches = launches_;
+        s->ms_to_target = ms_to_target_;
+        unsigned long long fl = 0;
+        UBQP_CK(cudaMemcpyAsync(&fl, ar_.at<unsigned long long>(o_flops_), sizeof(fl), cudaMemcpyDeviceToHost, stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        s->phase_a_flops = (int64_t)fl;
+        s->cluster_size = tc_ ? tc_S_ : 0;
         UBQP_CK(cudaMemcpyAsync(s->inner_hist, ar_.at<int64_t>(o_hist_), sizeof(s->inner_hist), cudaMemcpyDeviceToHost,
                                 stream_));
         UBQP_CK(cudaStreamSynchronize(stream_));
@@ -729,6 +826,7 @@ class Solver {
     int64_t ticks_ = 0;
     double ms_device_ = 0.0;
     double phase_a_ms_ = 0.0;
+    double ms_to_target_ = -1.0;
     int64_t launches_ = 0;
     int64_t phase_a_launches_ = 0;
     std::vector<cudaEvent_t> evA_;
@@ -738,7 +836,9 @@ class Solver {
     std::vector<LaneInit> lane_init_;
     std::vector<size_t> o_vec_, o_bx_, o_part_, o_trace_x_, o_trace_a_, o_x0_, o_p0_;
     size_t o_scal_ = 0, o_valid_ = 0, o_inexact_ = 0, o_hist_ = 0, o_active_ = 0, o_states_ = 0, o_lanes_ = 0,
-           o_linit_ = 0, o_items_ = 0, o_bytes_ = 0, o_counters_ = 0;
+           o_linit_ = 0, o_items_ = 0, o_bytes_ = 0, o_counters_ = 0, o_tcinst_ = 0, o_tcerr_ = 0,
+           o_flops_ = 0;
+    int tc_tiles_ = 0, tc_S_ = 1, tc_stages_ = 2, max_bn_ = 16;
     size_t o_final_lane0_ = 0, o_final_nl_ = 0, o_final_obj_ = 0, o_final_best_ = 0, o_final_xptr_ = 0,
            o_final_xbuf_ = 0;
 };
@@ -776,6 +876,9 @@ void ubqp_opts_default(ubqp_opts* o)
     o->jacobi_max_iter = 60;
     o->max_ticks_per_sync = 64;
     o->profile_kernels = 0;
+    o->stop_at_target = 0;
+    o->tc_cluster = 0;
+    o->target_objective = INFINITY;
     o->stream = nullptr;
     o->mu = nullptr;
     o->x_starts = nullptr;
@@ -817,10 +920,6 @@ int ubqp_solve_batched(int32_t num, const int64_t* n, const double* const* Q, co
         if (!Q[t] || !x_out[t]) { set_error("instance %d: null Q or x_out", t); return UBQP_EINVAL; }
     }
     const bool tc = o.precision != UBQP_FP32;
-    if (tc) {
-        set_error("tensor-core precision is not available in this build");
-        return UBQP_ENOTSUP;
-    }
     std::vector<InstIn> insts(num);
     std::vector<LaneIn> lanes;
     const int R = std::max(1, o.restarts);

@@ -15,6 +15,7 @@
 // stops issuing work, still passes every cluster barrier and frees its TMEM.
 #include <cooperative_groups.h>
 #include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cstring>
@@ -309,6 +310,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
     // ---- sum the cluster's partial accumulators and run the epilogue for this CTA's lanes
     if (!s_skip) {
         const int nreal = min(BN, I.R - nt * BN);
+        if (A.flops && rank == 0 && threadIdx.x == 0)   // 2 n flops per (row, lane), single term
+            atomicAdd(A.flops, 2ull * (unsigned long long)min(128, I.n - mt * 128) * (unsigned long long)I.n *
+                                   (unsigned long long)nreal);
         const int c0 = (int)((int64_t)nreal * rank / S), c1 = (int)((int64_t)nreal * (rank + 1) / S);
         float* peers[8];
         for (int q = 0; q < S; ++q) peers[q] = cluster.map_shared_rank(P, q);
@@ -438,15 +442,33 @@ int tc_pick_cluster(int tiles, int kb_min, int bn, bool two, int stages, int num
 }
 
 // 2-D BF16 tensor map over a row-major [rows][cols] array, box 64 (cols) x box_rows
+// cuTensorMapEncodeTiled is a driver entry point; resolving it through the runtime keeps
+// the library loadable (for its CPU-side checks) on machines without a driver
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
 CUresult tc_encode_map(CUtensorMap* map, const void* base, int64_t rows, int64_t cols, int box_rows)
 {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return CUDA_ERROR_NOT_FOUND;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
     cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1u, 1u};
-    return cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
-                                  estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
 }
 
 }  // namespace ubqp

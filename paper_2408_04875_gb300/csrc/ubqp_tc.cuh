@@ -31,6 +31,7 @@ struct TcArgs {
     const LaneDev* lanes;
     float* raw;          // probe mode: D written as [lane][row] (ld stride) instead of the epilogue
     int32_t* err;        // set when a bounded wait ran out
+    unsigned long long* flops;  // algorithmic flops of the tiles computed (may be null)
     Params P;
 };
 
