@@ -106,7 +106,8 @@ typedef struct {
     double lobpcg_tol;       /* relative change of the Ritz value to stop: 1e-4        */
     int jacobi_max_iter;     /* sweeps for x^0: 60                                      */
     int max_ticks_per_sync;  /* ticks launched between host checks: 64                 */
-    int profile_kernels;     /* 1: time every phase-A launch with CUDA events: 0       */
+    int profile_kernels;     /* 1: time every phase-A launch with CUDA events; 2: also  */
+                             /* keep a per-tick timeline (ubqp_profile_timeline): 0     */
     int stop_at_target;      /* 1: stop once target_objective is reached: 0            */
     int tc_cluster;          /* CTAs splitting K in the tensor-core kernel, 1..8;      */
                              /* 0 = chosen by the library's tuner                      */
@@ -227,6 +228,14 @@ int ubqp_penalty_probe(const double* Qp, const double* bp, const double* p, cons
  */
 int ubqp_initial_point(const double* Q, const double* b, const double* mu, int64_t n,
                        const ubqp_opts* o, double* x0_out, double* gamma_out);
+
+/*
+ * ubqp_profile_timeline - the per-tick record of the last call on this thread that ran
+ * with profile_kernels = 2: the phase-A duration of every tick (ms, CUDA events) and the
+ * algorithmic bytes (FP32 path) or flops (tensor-core path) that tick processed.  Copies up
+ * to `cap` entries into host arrays (either may be NULL) and returns the number recorded.
+ */
+int64_t ubqp_profile_timeline(float* ms_out, int64_t* work_out, int64_t cap);
 
 /*
  * ubqp_tc_matmul_probe - test entry: the tensor-core contraction of the batched path on

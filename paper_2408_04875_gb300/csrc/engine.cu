@@ -24,6 +24,8 @@
 namespace ubqp {
 
 static thread_local char g_last_error[512] = "";
+static thread_local std::vector<float> g_tl_ms;
+static thread_local std::vector<int64_t> g_tl_work;
 
 static void set_error(const char* fmt, ...)
 {
@@ -288,7 +290,7 @@ class Solver {
         if (tc) {
             for (InstDev& I : inst_) {
                 const int rpad = (int)round_up((size_t)I.nl, 16);
-                I.bn = rpad < 256 ? rpad : 256;
+                I.bn = rpad < kTcMaxBn ? rpad : kTcMaxBn;
                 I.n_tiles = (rpad + I.bn - 1) / I.bn;
                 I.rows_b = I.n_tiles * I.bn;
                 I.o_Uhi = ar_.reserve((size_t)I.rows_b * I.ld * 2);
@@ -300,6 +302,7 @@ class Solver {
         o_flops_ = ar_.reserve(sizeof(unsigned long long));
         o_states_ = ar_.reserve(lanes.size() * sizeof(LaneState));
         o_counters_ = ar_.reserve(lanes.size() * sizeof(unsigned int));
+        o_queue_ = ar_.reserve(2 * sizeof(int32_t));
         o_lanes_ = ar_.reserve(lanes.size() * sizeof(LaneDev));
         o_linit_ = ar_.reserve(lanes.size() * sizeof(LaneInit));
         o_items_ = ar_.reserve((size_t)std::max<int64_t>(nitems, 1) * sizeof(int2));
@@ -319,6 +322,7 @@ class Solver {
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_bytes_), 0, sizeof(unsigned long long), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_flops_), 0, sizeof(unsigned long long), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_counters_), 0, lanes.size() * sizeof(unsigned int), stream_));
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_queue_), 0, 2 * sizeof(int32_t), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_valid_), 0, insts.size() * 4 * sizeof(float), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_scal_), 0, insts.size() * 4 * sizeof(float), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_inexact_), 0, insts.size() * sizeof(int), stream_));
@@ -462,8 +466,13 @@ class Solver {
             L.trace_alpha = in.trace_len > 0 ? ar_.at<float>(o_trace_a_[l]) : nullptr;
             L.qmax_off = scal[4 * in.inst + 0];
             L.rabs_max = scal[4 * in.inst + 1];
-            if (!tc)
-                for (int b = 0; b < L.nblk; ++b) items.push_back(make_int2((int)l, b));
+        }
+        if (!tc) {   // largest lanes first in the GEMV work queue
+            std::vector<int> order(lanes.size());
+            for (size_t l = 0; l < lanes.size(); ++l) order[l] = (int)l;
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lanes_[a].n > lanes_[b].n; });
+            for (int l : order)
+                for (int b = 0; b < lanes_[l].nblk; ++b) items.push_back(make_int2(l, b));
         }
         UBQP_CK(cudaMemcpyAsync(ar_.at<LaneDev>(o_lanes_), lanes_.data(), lanes_.size() * sizeof(LaneDev),
                                 cudaMemcpyHostToDevice, stream_));
@@ -537,12 +546,18 @@ class Solver {
         ta.max_ld = max_ld_;
         ta.fused = 0;
         ta.active_count = nullptr;
+        ta.work = ar_.at<int32_t>(o_queue_);
+        ta.done = ar_.at<int32_t>(o_queue_) + 1;
+        ta.grid = 0;
         ta.P = make_params(o_, ar_.at<int64_t>(o_hist_));
         const bool prof = o_.profile_kernels != 0;
         if (prof) ta.P.bytes = ar_.at<unsigned long long>(o_bytes_);
         int32_t* d_active = ar_.at<int32_t>(o_active_);
         UBQP_CK(cudaMallocHost(&h_active_, sizeof(int32_t)));
-        if (!tc_ && nitems_ > 0) UBQP_CK(prepare_phase_a_gemv(max_ld_));
+        if (!tc_ && nitems_ > 0) {
+            UBQP_CK(prepare_phase_a_gemv(max_ld_));
+            ta.grid = gemv_grid(max_ld_, nitems_);
+        }
         const int T = o_.max_ticks_per_sync;
         const bool has_a = (!tc_ && nitems_ > 0) || (tc_ && tc_tiles_ > 0);
         TcArgs tca;
@@ -560,9 +575,17 @@ class Solver {
             tca.flops = prof ? ar_.at<unsigned long long>(o_flops_) : nullptr;
             tca.P = ta.P;
         }
+        const bool timeline = o_.profile_kernels >= 2;
+        unsigned long long* d_work_ctr = tc_ ? ar_.at<unsigned long long>(o_flops_) : ar_.at<unsigned long long>(o_bytes_);
+        unsigned long long* d_snap = nullptr;
         if (prof && has_a) {
             evA_.resize(2 * T);
             for (auto& e : evA_) UBQP_CK(cudaEventCreate(&e));
+            if (timeline) {
+                g_tl_ms.clear();
+                g_tl_work.clear();
+                UBQP_CK(cudaMallocAsync((void**)&d_snap, (size_t)T * sizeof(unsigned long long), stream_));
+            }
         }
 
         // GEMV lanes: one fused kernel per tick (the last CTA of each lane updates it);
@@ -588,6 +611,9 @@ class Solver {
                 }
                 if (e != cudaSuccess) return e;
                 if (prof && has_a) e = cudaEventRecord(evA_[2 * t + 1], stream_);
+                if (e != cudaSuccess) return e;
+                if (d_snap) e = cudaMemcpyAsync(d_snap + t, d_work_ctr, sizeof(unsigned long long),
+                                                cudaMemcpyDeviceToDevice, stream_);
                 if (e != cudaSuccess) return e;
                 if (!fused) {
                     e = launch_phase_b(ta, last ? d_active : nullptr, stream_);
@@ -622,10 +648,19 @@ class Solver {
             UBQP_CK(cudaStreamSynchronize(stream_));
             ticks += T;
             if (prof && has_a) {
+                std::vector<unsigned long long> snap(d_snap ? T : 0);
+                if (d_snap)
+                    UBQP_CK(cudaMemcpy(snap.data(), d_snap, (size_t)T * sizeof(unsigned long long),
+                                       cudaMemcpyDeviceToHost));
                 for (int t = 0; t < T; ++t) {
                     float ms = 0.f;
                     UBQP_CK(cudaEventElapsedTime(&ms, evA_[2 * t], evA_[2 * t + 1]));
                     phase_a_ms_ += ms;
+                    if (d_snap) {
+                        g_tl_ms.push_back(ms);
+                        g_tl_work.push_back((int64_t)(snap[t] - tl_prev_));
+                        tl_prev_ = snap[t];
+                    }
                 }
                 phase_a_launches_ += T;
             }
@@ -659,6 +694,7 @@ class Solver {
             }
         }
         UBQP_CK(cudaEventRecord(ev1_, stream_));
+        if (d_snap) UBQP_CK(cudaFreeAsync(d_snap, stream_));
         UBQP_CK(cudaStreamSynchronize(stream_));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0_, ev1_);
@@ -827,6 +863,7 @@ class Solver {
     double ms_device_ = 0.0;
     double phase_a_ms_ = 0.0;
     double ms_to_target_ = -1.0;
+    unsigned long long tl_prev_ = 0;
     int64_t launches_ = 0;
     int64_t phase_a_launches_ = 0;
     std::vector<cudaEvent_t> evA_;
@@ -837,7 +874,7 @@ class Solver {
     std::vector<size_t> o_vec_, o_bx_, o_part_, o_trace_x_, o_trace_a_, o_x0_, o_p0_;
     size_t o_scal_ = 0, o_valid_ = 0, o_inexact_ = 0, o_hist_ = 0, o_active_ = 0, o_states_ = 0, o_lanes_ = 0,
            o_linit_ = 0, o_items_ = 0, o_bytes_ = 0, o_counters_ = 0, o_tcinst_ = 0, o_tcerr_ = 0,
-           o_flops_ = 0;
+           o_flops_ = 0, o_queue_ = 0;
     int tc_tiles_ = 0, tc_S_ = 1, tc_stages_ = 2, max_bn_ = 16;
     size_t o_final_lane0_ = 0, o_final_nl_ = 0, o_final_obj_ = 0, o_final_best_ = 0, o_final_xptr_ = 0,
            o_final_xbuf_ = 0;
@@ -902,6 +939,17 @@ const char* ubqp_status_string(int s)
 }
 
 const char* ubqp_last_error(void) { return g_last_error; }
+
+int64_t ubqp_profile_timeline(float* ms_out, int64_t* work_out, int64_t cap)
+{
+    const int64_t n = (int64_t)g_tl_ms.size();
+    const int64_t m = cap < n ? cap : n;
+    for (int64_t i = 0; i < m; ++i) {
+        if (ms_out) ms_out[i] = g_tl_ms[(size_t)i];
+        if (work_out) work_out[i] = g_tl_work[(size_t)i];
+    }
+    return n;
+}
 
 int ubqp_solve_batched(int32_t num, const int64_t* n, const double* const* Q, const double* const* b,
                        const ubqp_opts* o_in, uint8_t* const* x_out, double* obj_out)

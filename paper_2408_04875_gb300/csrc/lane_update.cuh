@@ -329,7 +329,7 @@ static __device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, 
 
 // The update of one lane by one CTA of kBThreads threads (phase B).  Called by the
 // stand-alone phase-B kernel and by the last phase-A CTA of a lane in the fused GEMV tick.
-static __device__ void lane_update(const LaneDev& L, const Params& P, int32_t* active_count)
+static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& P, int32_t* active_count)
 {
     __shared__ LaneState S;
     __shared__ Partial R;
@@ -396,7 +396,39 @@ static __device__ void lane_update(const LaneDev& L, const Params& P, int32_t* a
     const int n = L.n, ld = L.ld;
     float* vec = L.vec;
     const int act = D.act, usrc = D.usrc;
-    for (int i = threadIdx.x; i < n; i += kBThreads) {
+    if (act == A_STEP_PABB && usrc == U_X) {
+        // the common tick: x_prev <- x, x <- P(x - alpha g), u <- x over the padded length in
+        // 16-byte pieces (padding stays zero: x = g = 0 there)
+        const float al = D.alpha;
+        float4* X4 = reinterpret_cast<float4*>(vec + (size_t)V_X * ld);
+        float4* XP4 = reinterpret_cast<float4*>(vec + (size_t)V_XPREV * ld);
+        const float4* G4 = reinterpret_cast<const float4*>(vec + (size_t)V_G * ld);
+        float4* U4 = reinterpret_cast<float4*>(vec + (size_t)V_U * ld);
+        for (int q = threadIdx.x; q < (ld >> 2); q += kBThreads) {
+            const float4 x = X4[q], g = G4[q];
+            XP4[q] = x;
+            float4 y;
+            y.x = fminf(fmaxf(fmaf(-al, g.x, x.x), 0.f), 1.f);
+            y.y = fminf(fmaxf(fmaf(-al, g.y, x.y), 0.f), 1.f);
+            y.z = fminf(fmaxf(fmaf(-al, g.z, x.z), 0.f), 1.f);
+            y.w = fminf(fmaxf(fmaf(-al, g.w, x.w), 0.f), 1.f);
+            X4[q] = y;
+            if (L.mode == MODE_TC) {
+                const __nv_bfloat162 h01 = __floats2bfloat162_rn(y.x, y.y), h23 = __floats2bfloat162_rn(y.z, y.w);
+                reinterpret_cast<__nv_bfloat162*>(L.u_hi)[2 * q] = h01;
+                reinterpret_cast<__nv_bfloat162*>(L.u_hi)[2 * q + 1] = h23;
+                if (L.u_lo) {
+                    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+                    reinterpret_cast<__nv_bfloat162*>(L.u_lo)[2 * q] = __floats2bfloat162_rn(y.x - f01.x, y.y - f01.y);
+                    reinterpret_cast<__nv_bfloat162*>(L.u_lo)[2 * q + 1] =
+                        __floats2bfloat162_rn(y.z - f23.x, y.w - f23.y);
+                }
+            } else {
+                U4[q] = y;
+            }
+        }
+    }
+    for (int i = threadIdx.x; i < n && !(act == A_STEP_PABB && usrc == U_X); i += kBThreads) {
         float x = vec[V_X * ld + i];
         if (act & A_TRACE) L.trace_x[(size_t)D.trace_k * n + i] = x;
         if (act & A_COPY_W_X) {

@@ -30,7 +30,7 @@ namespace ubqp {
 
 namespace {
 
-constexpr int kTcThreads = 128;       // 4 warps: TMA producer, MMA issuer, then all 4 do the epilogue
+constexpr int kTcThreads = 256;       // 8 warps: TMA producer, MMA issuer, then all 8 drain TMEM / run the epilogue
 constexpr uint64_t kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -144,6 +144,20 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // warp-level reduction of one lane's accumulator into its partial record (lane 0 writes)
@@ -279,27 +293,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
     }
     __syncthreads();
 
-    // ---- accumulators -> shared memory P[col][row] (the ring is free once accum_bar fired)
+    // ---- accumulators -> shared memory P[col][row] (the ring is free once accum_bar fired).
+    // One thread waits on the barrier; the rest sleep at __syncthreads.
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) s_ok = (!s_skip && nkb > 0) ? (!s_fail && mbar_wait(&accum_bar, 0u)) : 1;
+    __syncthreads();
     float* P = reinterpret_cast<float*>(ring);
     if (!s_skip) {
-        bool ok = true;
-        if (nkb > 0) {
-            ok = !s_fail && mbar_wait(&accum_bar, 0u);
-            tc_fence_after();
-        }
-        const int row = warp * 32 + lane;
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            float v[32];
-            if (nkb > 0 && ok) {
-                tmem_ld32(tmem_base + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        const bool have = nkb > 0 && s_ok;
+        if (nkb > 0) tc_fence_after();
+        const int row = (warp & 3) * 32 + lane;   // TMEM lanes reachable by this warp
+        for (int q = warp >> 2; q < BN / 16; q += 2) {   // 16-column chunks split over the two warpgroups
+            float v[16];
+            if (have) {
+                tmem_ld16(tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q * 16), v);
             } else {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = 0.f;
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
             }
 #pragma unroll
-            for (int i = 0; i < 32; ++i) P[(c0 + i) * 128 + row] = v[i];
+            for (int i = 0; i < 16; ++i) P[(q * 16 + i) * 128 + row] = v[i];
         }
-        if (!ok) {
+        if (!s_ok && threadIdx.x == 0) {
             s_fail = 1;
             if (A.err) atomicExch(A.err, 1);
         }
@@ -308,15 +323,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
     cluster.sync();
 
     // ---- sum the cluster's partial accumulators and run the epilogue for this CTA's lanes
+    __shared__ int s_ph[kTcMaxBn], s_k[kTcMaxBn];
     if (!s_skip) {
         const int nreal = min(BN, I.R - nt * BN);
+        const int c0 = (int)((int64_t)nreal * rank / S), c1 = (int)((int64_t)nreal * (rank + 1) / S);
         if (A.flops && rank == 0 && threadIdx.x == 0)   // 2 n flops per (row, lane), single term
             atomicAdd(A.flops, 2ull * (unsigned long long)min(128, I.n - mt * 128) * (unsigned long long)I.n *
                                    (unsigned long long)nreal);
-        const int c0 = (int)((int64_t)nreal * rank / S), c1 = (int)((int64_t)nreal * (rank + 1) / S);
+        if (!A.raw)
+            for (int c = c0 + (int)threadIdx.x; c < c1; c += kTcThreads) {
+                const LaneState* st = A.lanes[I.lane0 + nt * BN + c].st;
+                s_ph[c - c0] = st->phase;
+                s_k[c - c0] = st->k;
+            }
+        __syncthreads();
         float* peers[8];
         for (int q = 0; q < S; ++q) peers[q] = cluster.map_shared_rank(P, q);
-        for (int c = c0 + warp; c < c1; c += 4) {
+        for (int c = c0 + warp; c < c1; c += kTcThreads / 32) {
             const int r = nt * BN + c;  // restart index within the instance
             float vv[4];
 #pragma unroll
@@ -334,16 +357,53 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
                 }
                 continue;
             }
-            const LaneDev& L = A.lanes[I.lane0 + r];
-            const int ph = L.st->phase;
+            const int ph = s_ph[c - c0];
             if (ph == PH_DONE) continue;
-            const int k = L.st->k;
+            const int k = s_k[c - c0];
+            const LaneDev& L = A.lanes[I.lane0 + r];
             Acc a;
             a.zero();
+            if (ph == PH_INNER) {
+                // Alg. 2 gradient for four rows: all operands loaded before any result is stored
+                float* vec = L.vec;
+                const int ld = L.ld;
+                float x[4], dmp[4], ts[4], xp[4], go[4], oa[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int i = mt * 128 + lane + 32 * j;
-                if (i < I.n) row_epilogue(L, ph, k, i, (double)vv[j], a, A.P.tau_z);
+                for (int j = 0; j < 4; ++j) {
+                    const int i = min(mt * 128 + lane + 32 * j, I.n - 1);
+                    x[j] = vec[V_X * ld + i];
+                    dmp[j] = vec[V_DMP * ld + i];
+                    ts[j] = L.tsum[i];
+                    xp[j] = vec[V_XPREV * ld + i];
+                    go[j] = vec[V_G * ld + i];
+                    oa[j] = L.oabs[i];
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = mt * 128 + lane + 32 * j;
+                    if (i >= I.n) continue;
+                    const float g = fmaf(dmp[j], 2.f * x[j] - 1.f, fmaf(2.f, vv[j], ts[j]));
+                    if (k >= 1) {
+                        const float sj = x[j] - xp[j], yj = g - go[j];
+                        csum_add(a.s[0], sj * sj);
+                        csum_add(a.s[1], sj * yj);
+                        csum_add(a.s[2], yj * yj);
+                    } else {
+                        a.m[1] = fmaxf(a.m[1], fabsf(dmp[j]));
+                        a.m[2] = fmaxf(a.m[2], fabsf(vec[V_BBAR * ld + i]));
+                        a.m[3] = fmaxf(a.m[3], oa[j] + fabsf(dmp[j]));
+                    }
+                    vec[V_G * ld + i] = g;
+                    const float viol = (x[j] > 0.f && x[j] < 1.f) ? fabsf(g)
+                                       : (x[j] <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
+                    a.m[0] = fmaxf(a.m[0], viol);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = mt * 128 + lane + 32 * j;
+                    if (i < I.n) row_epilogue(L, ph, k, i, (double)vv[j], a, A.P.tau_z);
+                }
             }
             warp_reduce_write(a, ph, L.part + mt, ph == PH_EVAL);
         }
@@ -484,7 +544,7 @@ extern "C" int ubqp_tc_matmul_probe(const uint16_t* A, const uint16_t* Bhi, cons
         return UBQP_EINVAL;
     const int ld = (int)((n + 127) / 128 * 128);
     const int rpad = (int)((R + 15) / 16 * 16);
-    const int bn = rpad < 256 ? rpad : 256;
+    const int bn = rpad < kTcMaxBn ? rpad : kTcMaxBn;
     const int n_tiles = (rpad + bn - 1) / bn;
     const int rows_b = n_tiles * bn;
     const bool two = Blo != nullptr;

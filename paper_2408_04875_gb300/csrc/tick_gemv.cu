@@ -14,16 +14,59 @@ namespace ubqp {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-// dot of one row with u (shared), FP32 row, 16-byte loads.  Each product is split
-// exactly (p + e with e = fma(q, u, -p)) and accumulated with TwoSum, so v carries about
-// twice the FP32 precision at no cost to a kernel bound by the bytes of Q.
+// dot of one row with u (shared), FP32 row, 16-byte loads.  The four products of each
+// 16-byte group are summed with FMAs and the group sum is added to a TwoSum-compensated
+// accumulator: the error stays near 4 eps times the sum of |terms| instead of growing with
+// the row length, at under 3 FP32 operations per matrix entry.
 __device__ __forceinline__ void cacc4(float2& acc, float4 q, float4 u)
 {
-    float p, e, s, t;
-    p = __fmul_rn(q.x, u.x); e = fmaf(q.x, u.x, -p); two_sum(acc.x, p, s, t); acc.x = s; acc.y += t + e;
-    p = __fmul_rn(q.y, u.y); e = fmaf(q.y, u.y, -p); two_sum(acc.x, p, s, t); acc.x = s; acc.y += t + e;
-    p = __fmul_rn(q.z, u.z); e = fmaf(q.z, u.z, -p); two_sum(acc.x, p, s, t); acc.x = s; acc.y += t + e;
-    p = __fmul_rn(q.w, u.w); e = fmaf(q.w, u.w, -p); two_sum(acc.x, p, s, t); acc.x = s; acc.y += t + e;
+    float t = __fmul_rn(q.x, u.x);
+    t = fmaf(q.y, u.y, t);
+    t = fmaf(q.z, u.z, t);
+    t = fmaf(q.w, u.w, t);
+    float s, e;
+    two_sum(acc.x, t, s, e);
+    acc.x = s;
+    acc.y += e;
+}
+
+__device__ __forceinline__ float4 ldg_stream(const float4* p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// two rows at once (independent load streams), same arithmetic as row_dot_f32
+__device__ __forceinline__ void row_dot2_f32(const float* __restrict__ ra, const float* __restrict__ rb,
+                                             const float* su, int ld, int lane, float& va, float& vb)
+{
+    const float4* a4 = reinterpret_cast<const float4*>(ra);
+    const float4* b4 = reinterpret_cast<const float4*>(rb);
+    const float4* u4 = reinterpret_cast<const float4*>(su);
+    const int n4 = ld >> 2;
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+    int c = lane;
+    for (; c + 32 < n4; c += 64) {
+        const float4 qa0 = ldg_stream(a4 + c), qa1 = ldg_stream(a4 + c + 32);
+        const float4 qb0 = ldg_stream(b4 + c), qb1 = ldg_stream(b4 + c + 32);
+        const float4 u0 = u4[c], u1 = u4[c + 32];
+        cacc4(a0, qa0, u0);
+        cacc4(b0, qb0, u0);
+        cacc4(a1, qa1, u1);
+        cacc4(b1, qb1, u1);
+    }
+    for (; c < n4; c += 32) {
+        const float4 u0 = u4[c];
+        cacc4(a0, ldg_stream(a4 + c), u0);
+        cacc4(b0, ldg_stream(b4 + c), u0);
+    }
+    float2 a = csum_shfl_reduce(csum_merge(a0, a1));
+    float2 b = csum_shfl_reduce(csum_merge(b0, b1));
+    va = a.x + a.y;
+    vb = b.x + b.y;
 }
 
 __device__ __forceinline__ float row_dot_f32(const float* __restrict__ row, const float* su, int ld,
@@ -90,64 +133,94 @@ __device__ __forceinline__ T row_dot_plain(const T* __restrict__ row, const T* s
 // solver lanes (FP32 GEMV path)
 __global__ void __launch_bounds__(kThreads, 4) phase_a_gemv_kernel(TickArgs A)
 {
+    // Persistent: CTAs pull (lane, row-block) items from a queue until it is empty; the
+    // items of the largest lanes come first.  u stays in shared memory while consecutive
+    // items belong to the same lane.
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* su = reinterpret_cast<float*>(smem_raw);
     __shared__ double sv[kThreads];
-
-    const int2 it = A.items[blockIdx.x];
-    const LaneDev& L = A.lanes[it.x];
-    const int ph = L.st->phase;
-    if (ph == PH_DONE || ph == PH_GRAD) return;
-    const int k = L.st->k;
-    const int ld = L.ld;
-    const int row0 = it.y * A.rows_per_item;
-    const int rows = min(A.rows_per_item, L.n - row0);
+    __shared__ int s_item, s_ulane, is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-
-    // u (written by phase B of the previous tick, zero beyond n)
-    {
-        const float4* g4 = reinterpret_cast<const float4*>(L.vec + (size_t)V_U * ld);
-        float4* s4 = reinterpret_cast<float4*>(su);
-        for (int c = threadIdx.x; c < (ld >> 2); c += kThreads) s4[c] = g4[c];
-    }
-    __syncthreads();
-
-    if (ph == PH_EVAL) {
-        for (int r = warp; r < rows; r += kWarps) {
-            double v = row_dot_eval(L.Qeval + (size_t)(row0 + r) * ld, su, ld, lane);
-            if (lane == 0) sv[r] = v;
+    if (threadIdx.x == 0) s_ulane = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(A.work, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= A.nitems) break;
+        const int2 it = A.items[item];
+        const LaneDev& L = A.lanes[it.x];
+        const int ph = L.st->phase;
+        if (ph == PH_DONE || ph == PH_GRAD) {
+            __syncthreads();
+            continue;
         }
-    } else {
-        for (int r = warp; r < rows; r += kWarps) {
-            float v = row_dot_f32(L.Qoff + (size_t)(row0 + r) * ld, su, ld, lane);
-            if (lane == 0) sv[r] = (double)v;
-        }
-    }
-    __syncthreads();
+        const int k = L.st->k;
+        const int ld = L.ld;
+        const int row0 = it.y * A.rows_per_item;
+        const int rows = min(A.rows_per_item, L.n - row0);
 
-    Acc a;
-    a.zero();
-    if ((int)threadIdx.x < rows) row_epilogue(L, ph, k, row0 + threadIdx.x, sv[threadIdx.x], a, A.P.tau_z);
-    block_reduce_write<kWarps>(a, ph, L.part + it.y, ph == PH_EVAL);
-    if (A.P.bytes && threadIdx.x == 0) {
-        // stored entries of these rows once (FP32, or FP64 for the evaluation), the input
-        // vector once per lane, and the per-row vectors the epilogue touches
-        unsigned long long by = (unsigned long long)rows * L.n * (ph == PH_EVAL ? 8ull : 4ull) +
-                                (it.y == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
-        atomicAdd(A.P.bytes, by);
+        // u (written by the update of the previous tick, zero beyond n)
+        if (s_ulane != it.x) {
+            const float4* g4 = reinterpret_cast<const float4*>(L.vec + (size_t)V_U * ld);
+            float4* s4 = reinterpret_cast<float4*>(su);
+            for (int c = threadIdx.x; c < (ld >> 2); c += kThreads) s4[c] = g4[c];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_ulane = it.x;
+
+        if (ph == PH_EVAL) {
+            for (int r = warp; r < rows; r += kWarps) {
+                double v = row_dot_eval(L.Qeval + (size_t)(row0 + r) * ld, su, ld, lane);
+                if (lane == 0) sv[r] = v;
+            }
+        } else {
+            for (int r = warp; r < rows; r += 2 * kWarps) {
+                const int r2 = r + kWarps < rows ? r + kWarps : r;
+                float va, vb;
+                row_dot2_f32(L.Qoff + (size_t)(row0 + r) * ld, L.Qoff + (size_t)(row0 + r2) * ld, su, ld, lane,
+                             va, vb);
+                if (lane == 0) {
+                    sv[r] = (double)va;
+                    sv[r2] = (double)vb;
+                }
+            }
+        }
+        __syncthreads();
+
+        Acc a;
+        a.zero();
+        if ((int)threadIdx.x < rows) row_epilogue(L, ph, k, row0 + threadIdx.x, sv[threadIdx.x], a, A.P.tau_z);
+        block_reduce_write<kWarps>(a, ph, L.part + it.y, ph == PH_EVAL);
+        if (A.P.bytes && threadIdx.x == 0) {
+            // stored entries of these rows once (FP32, or the 8-byte evaluation matrix), the
+            // input vector once per lane, and the per-row vectors the epilogue touches
+            unsigned long long by = (unsigned long long)rows * L.n * (ph == PH_EVAL ? 8ull : 4ull) +
+                                    (it.y == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
+            atomicAdd(A.P.bytes, by);
+        }
+        if (A.fused) {
+            // every CTA publishes its partial and epilogue writes, then counts itself in; the
+            // CTA that completes the lane's count runs the lane's update.  No CTA waits.
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) is_last = (atomicAdd(L.counter, 1u) == (unsigned)(L.nblk - 1));
+            __syncthreads();
+            if (is_last) {
+                __threadfence();
+                lane_update(L, A.P, A.active_count);
+                if (threadIdx.x == 0) {
+                    *L.counter = 0u;
+                    s_ulane = -1;
+                }
+            }
+        }
+        __syncthreads();
     }
-    if (!A.fused) return;
-    // Fused phase B: every CTA publishes its partial and epilogue writes, then counts
-    // itself in; the CTA that completes the count runs the lane's update.  No CTA waits.
-    __shared__ int is_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = (atomicAdd(L.counter, 1u) == (unsigned)(L.nblk - 1));
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    lane_update(L, A.P, A.active_count);
-    if (threadIdx.x == 0) *L.counter = 0u;
+    // the last CTA to leave resets the queue for the next tick
+    if (threadIdx.x == 0 && atomicAdd(A.done, 1) == (int)gridDim.x - 1) {
+        *A.work = 0;
+        *A.done = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -219,11 +292,25 @@ cudaError_t prepare_phase_a_gemv(int max_ld)
     return cudaFuncSetAttribute(phase_a_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+int gemv_grid(int max_ld, int nitems)
+{
+    int dev = 0, sms = 148, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, phase_a_gemv_kernel, kThreads,
+                                                      (size_t)max_ld * sizeof(float)) != cudaSuccess || per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    int g = sms * per;
+    return nitems < g ? nitems : g;
+}
+
 cudaError_t launch_phase_a_gemv_f32(const TickArgs& a, cudaStream_t s)
 {
     // shared: u of the widest lane (ld floats); rows_per_item <= kThreads
     size_t smem = (size_t)a.max_ld * sizeof(float);
-    phase_a_gemv_kernel<<<a.nitems, kThreads, smem, s>>>(a);
+    phase_a_gemv_kernel<<<a.grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -371,11 +371,15 @@ struct TickArgs {
     int32_t nlanes;
     int32_t max_ld;        // widest lane (shared-memory size of the GEMV kernel)
     int32_t fused;         // GEMV lanes: the last phase-A CTA of a lane runs its update
+    int32_t grid;          // persistent GEMV grid size
     int32_t* active_count; // incremented by every lane still active after this tick
+    int32_t* work;         // GEMV work queue head (reset by the last CTA of a tick)
+    int32_t* done;         // CTAs of the tick that have left the queue
     Params P;
 };
 
 cudaError_t prepare_phase_a_gemv(int max_ld);
+int gemv_grid(int max_ld, int nitems);
 cudaError_t launch_phase_a_gemv_f32(const TickArgs& a, cudaStream_t s);
 cudaError_t launch_phase_a_grad(const TickArgs& a, int dtype, int64_t n, cudaStream_t s);
 cudaError_t launch_phase_b(const TickArgs& a, int32_t* active_count, cudaStream_t s);

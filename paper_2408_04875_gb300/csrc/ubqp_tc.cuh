@@ -8,6 +8,7 @@
 namespace ubqp {
 
 constexpr int kTcMaxStages = 4;
+constexpr int kTcMaxBn = 128;   // lanes per N tile (UMMA N)
 
 // One instance of the batched path: BF16 Q_off (ld x ld) and its lanes' packed inputs
 // (hi and lo terms, R rows of ld), with the TMA descriptors of all three.
