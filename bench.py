@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "inner PG iters/s (batch×n) and time-to-oracle-objective vs plain FP32 path"
 UNIT = "lane-var-updates/s"
+GEMV_KERNELS = {1: "phase_a_gemv_kernel", 2: "lane_loop_kernel"}
 SIZES = (250, 500, 1000, 2500)
 SEEDS_PER_SIZE = 10
 WORKLOAD = ("plain PSDP sweep: n in {250,500,1000,2500} x 10 seeded instances, density 0.1, "
@@ -237,7 +238,7 @@ def run_gpu(args):
     Qd = [torch.from_numpy(Q).cuda() for Q in Qs]
     Md = [torch.from_numpy(m).cuda() for m in mus]
     torch.cuda.synchronize()
-    kw = dict(profile_kernels=0 if args.no_profile else 1)
+    kw = dict(profile_kernels=0 if args.no_profile else 1, gemv_kernel=args.gemv_kernel)
     if args.max_outer is not None:
         kw["max_outer"] = args.max_outer
     for _ in range(args.warmup):
@@ -294,7 +295,7 @@ def run_gpu(args):
                        "ticks_per_step": stats[-1]["ticks"], "best_objectives_first3": [float(v) for v in objs[:3]]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
-                         "kernel": "phase_a_gemv_kernel", "launches": pa_n,
+                         "kernel": GEMV_KERNELS.get(stats[-1]["gemv_kernel"], "?"), "launches": pa_n,
                          "avg_launch_us": pa_ms * 1e3 / max(pa_n, 1),
                          "algorithmic_bytes_per_launch": pa_bytes / max(pa_n, 1), "peak_kind": peak_kind},
             "e2e": None if st_e2e is None else {"value": st_e2e["var_updates"] / e2e_s, "unit": UNIT,
@@ -327,6 +328,8 @@ def main():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c4"])
     ap.add_argument("--restarts", type=int, default=256)
+    ap.add_argument("--gemv-kernel", type=int, default=0, choices=[0, 1, 2],
+                    help="FP32 matrix-vector kernel: 0 library's choice, 1 register-streamed, 2 bulk-copy")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

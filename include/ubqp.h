@@ -78,7 +78,8 @@ typedef struct {
                              /* opts->target_objective (-1: not reached / not set)      */
     int64_t phase_a_flops;   /* algorithmic flops of the tensor-core launches timed     */
     int32_t cluster_size;    /* CTAs per cluster of the tensor-core launches (0: none)  */
-    int32_t pad_;
+    int32_t gemv_kernel;     /* scheduler that ran the FP32 lanes: 1 lock-step, 2 lane  */
+                             /* loop (0: tensor-core lanes)                             */
     int64_t inner_hist[UBQP_HIST_BINS]; /* projected steps per subproblem (Fig. 5)   */
 } ubqp_stats;
 
@@ -111,6 +112,11 @@ typedef struct {
     int stop_at_target;      /* 1: stop once target_objective is reached: 0            */
     int tc_cluster;          /* CTAs splitting K in the tensor-core kernel, 1..8;      */
                              /* 0 = chosen by the library's tuner                      */
+    int gemv_kernel;         /* scheduler of the FP32 lanes: 1 lock-step (one launch   */
+                             /* per step of all lanes), 2 persistent lane loop (lanes  */
+                             /* advance independently inside one launch); 0 = 2, or 1  */
+                             /* when profile_kernels == 2 (per-step timeline)          */
+    int lane_budget;         /* lane loop: steps per lane between host checks; 0 = 1024 */
     double target_objective; /* objective to time against (used when finite)           */
     void* stream;            /* cudaStream_t, NULL = default stream                    */
     const double* const* mu; /* optional perturbations, one n x n matrix per instance   */

@@ -17,7 +17,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libubqp.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["engine.cu", "tick_gemv.cu", "tick_update.cu", "init.cu", "noalloc.cu", "tc_gemm.cu"]
+SOURCES = ["engine.cu", "tick_gemv.cu", "lane_loop.cu", "tick_update.cu", "init.cu", "noalloc.cu", "tc_gemm.cu"]
+# the lane loop reads, within one launch, lane vectors that CTAs on other SMs wrote: its
+# plain loads are cached in L2 only
+EXTRA = {"lane_loop.cu": ["-Xptxas", "-dlcm=cg"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -51,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
     def compile_one(src, obj):
-        cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(extra)
+        cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj] + _flags(list(extra) + EXTRA.get(src, []))
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -133,6 +133,8 @@ static int check_opts(const ubqp_opts& o)
     if (o.max_ticks_per_sync < 1 || o.max_ticks_per_sync > 4096) { set_error("max_ticks_per_sync out of range"); return UBQP_EINVAL; }
     if (!(o.sigma_rel >= 0.0) || !(o.gamma_margin > 0.0)) { set_error("sigma_rel >= 0 and gamma_margin > 0 required"); return UBQP_EINVAL; }
     if (o.tc_cluster < 0 || o.tc_cluster > 8) { set_error("tc_cluster must be in [0, 8]"); return UBQP_EINVAL; }
+    if (o.gemv_kernel < 0 || o.gemv_kernel > 2) { set_error("gemv_kernel must be 0, 1 or 2"); return UBQP_EINVAL; }
+    if (o.lane_budget < 0) { set_error("lane_budget must be >= 0"); return UBQP_EINVAL; }
     return UBQP_OK;
 }
 
@@ -316,6 +318,30 @@ class Solver {
         for (InstDev& I : inst_) xbuf += round_up((size_t)I.n, 256);
         o_final_xbuf_ = ar_.reserve(xbuf);
         nitems_ = (int)nitems;
+        if (!tc && nitems > 0) {
+            // scheduler of the FP32 lanes: the persistent lane loop, unless the lock-step
+            // tick kernel is asked for (or the per-tick timeline, which needs one launch per
+            // tick); ring entries hold lane and block indices in 16 bits each
+            int max_nblk = 0;
+            for (const LaneDev& L : lanes_) max_nblk = std::max(max_nblk, L.nblk);
+            const bool fits = lanes.size() < 0xFFFEu && max_nblk <= 0xFFFF;
+            if (o_.gemv_kernel == 2 && !fits) {
+                set_error("the lane loop takes at most 65533 lanes of at most 65535 row blocks");
+                return UBQP_ENOTSUP;
+            }
+            loop_ = fits && (o_.gemv_kernel == 2 || (o_.gemv_kernel == 0 && o_.profile_kernels < 2));
+            if (loop_) {
+                UBQP_CK(prepare_lane_loop(max_ld));
+                loop_grid_ = lane_loop_grid(max_ld);
+                loop_cap_ = 1024;
+                while (loop_cap_ < 2 * ((uint64_t)nitems + (uint64_t)loop_grid_)) loop_cap_ *= 2;
+                loop_budget_ = o_.lane_budget > 0 ? o_.lane_budget : 1024;
+                o_ring_ = ar_.reserve(loop_cap_ * sizeof(unsigned long long));
+                o_ht_ = ar_.reserve(2 * sizeof(unsigned long long));
+                o_loopctr_ = ar_.reserve(3 * sizeof(int32_t));
+                o_budget_ = ar_.reserve(lanes.size() * sizeof(int32_t));
+            }
+        }
         rc = ar_.commit();
         if (rc) return rc;
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_hist_), 0, UBQP_HIST_BINS * sizeof(int64_t), stream_));
@@ -481,6 +507,11 @@ class Solver {
         if (!items.empty())
             UBQP_CK(cudaMemcpyAsync(ar_.at<int2>(o_items_), items.data(), items.size() * sizeof(int2),
                                     cudaMemcpyHostToDevice, stream_));
+        if (loop_) {
+            UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_ring_), 0, loop_cap_ * sizeof(unsigned long long), stream_));
+            UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_ht_), 0, 2 * sizeof(unsigned long long), stream_));
+            UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_loopctr_), 0, 3 * sizeof(int32_t), stream_));
+        }
         if (tc) {
             for (InstDev& I : inst_) {
                 UBQP_CK(cudaMemsetAsync(ar_.at<char>(I.o_Uhi), 0, (size_t)I.rows_b * I.ld * 2, stream_));
@@ -537,6 +568,7 @@ class Solver {
 
     int run()
     {
+        if (loop_) return run_loop();
         TickArgs ta;
         ta.lanes = ar_.at<LaneDev>(o_lanes_);
         ta.items = ar_.at<int2>(o_items_);
@@ -672,21 +704,10 @@ class Solver {
                     return UBQP_ETIMEOUT;
                 }
             }
-            if (std::isfinite(o_.target_objective) && ms_to_target_ < 0.0) {
-                std::vector<LaneState> st(nlanes_);
-                UBQP_CK(cudaMemcpy(st.data(), ar_.at<LaneState>(o_states_), st.size() * sizeof(LaneState),
-                                   cudaMemcpyDeviceToHost));
-                double best = INFINITY;
-                for (const LaneState& x : st) best = std::min(best, x.best_f);
-                if (best <= o_.target_objective) {
-                    UBQP_CK(cudaEventRecord(ev1_, stream_));
-                    UBQP_CK(cudaEventSynchronize(ev1_));
-                    float m = 0.f;
-                    cudaEventElapsedTime(&m, ev0_, ev1_);
-                    ms_to_target_ = m;
-                    if (o_.stop_at_target) break;
-                }
-            }
+            bool stop = false;
+            int rc = check_target(stop);
+            if (rc) return rc;
+            if (stop) break;
             if (*h_active_ == 0) break;
             if (ticks > cap) {
                 set_error("tick cap %lld exceeded", (long long)cap);
@@ -700,6 +721,120 @@ class Solver {
         cudaEventElapsedTime(&ms, ev0_, ev1_);
         ms_device_ = ms;
         ticks_ = ticks;
+        return UBQP_OK;
+    }
+
+    // time to the target objective (when one is set): the first host check at which some
+    // lane's best exact objective reaches it
+    int check_target(bool& stop)
+    {
+        stop = false;
+        if (!std::isfinite(o_.target_objective) || ms_to_target_ >= 0.0) return UBQP_OK;
+        std::vector<LaneState> st(nlanes_);
+        UBQP_CK(cudaMemcpy(st.data(), ar_.at<LaneState>(o_states_), st.size() * sizeof(LaneState),
+                           cudaMemcpyDeviceToHost));
+        double best = INFINITY;
+        for (const LaneState& x : st) best = std::min(best, x.best_f);
+        if (best <= o_.target_objective) {
+            UBQP_CK(cudaEventRecord(ev1_, stream_));
+            UBQP_CK(cudaEventSynchronize(ev1_));
+            float m = 0.f;
+            cudaEventElapsedTime(&m, ev0_, ev1_);
+            ms_to_target_ = m;
+            stop = o_.stop_at_target != 0;
+        }
+        return UBQP_OK;
+    }
+
+    // FP32 lanes on the persistent lane loop: each launch (seed + loop, one graph) lets
+    // every lane take up to loop_budget_ steps; the host checks between launches
+    int run_loop()
+    {
+        LoopArgs la;
+        memset(&la, 0, sizeof(la));
+        la.lanes = ar_.at<LaneDev>(o_lanes_);
+        la.items = ar_.at<int2>(o_items_);
+        la.nitems = nitems_;
+        la.nlanes = nlanes_;
+        la.rows_per_item = rows_per_item_;
+        la.max_ld = max_ld_;
+        la.budget = loop_budget_;
+        la.grid = loop_grid_;
+        la.ring = ar_.at<unsigned long long>(o_ring_);
+        la.cap = loop_cap_;
+        la.head = ar_.at<unsigned long long>(o_ht_);
+        la.tail = la.head + 1;
+        int32_t* ctr = ar_.at<int32_t>(o_loopctr_);
+        la.running = ctr;
+        la.active_after = ctr + 1;
+        la.err = ctr + 2;
+        la.budget_left = ar_.at<int32_t>(o_budget_);
+        la.P = make_params(o_, ar_.at<int64_t>(o_hist_));
+        const bool prof = o_.profile_kernels != 0;
+        if (prof) la.P.bytes = ar_.at<unsigned long long>(o_bytes_);
+        UBQP_CK(cudaMallocHost(&h_active_, sizeof(int32_t)));
+        if (prof) {
+            evA_.resize(2);
+            for (auto& e : evA_) UBQP_CK(cudaEventCreate(&e));
+        }
+        auto enqueue = [&]() -> cudaError_t {
+            cudaError_t e = prof ? cudaEventRecord(evA_[0], stream_) : cudaSuccess;
+            if (e == cudaSuccess) e = launch_lane_loop(la, stream_);
+            if (e == cudaSuccess && prof) e = cudaEventRecord(evA_[1], stream_);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_active_, la.active_after, sizeof(int32_t), cudaMemcpyDeviceToHost, stream_);
+            return e;
+        };
+        bool use_graph = !prof;
+        if (use_graph && cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            cudaError_t e = enqueue();
+            cudaError_t e2 = cudaStreamEndCapture(stream_, &graph_);
+            if (e != cudaSuccess || e2 != cudaSuccess || cudaGraphInstantiate(&gexec_, graph_, 0) != cudaSuccess) {
+                use_graph = false;
+                cudaGetLastError();
+            }
+        } else {
+            use_graph = false;
+            cudaGetLastError();
+        }
+        UBQP_CK(cudaEventRecord(ev0_, stream_));
+        const int64_t cap = (int64_t)(o_.jacobi_max_iter + 2) +
+                            (int64_t)(o_.max_outer + 1) * (int64_t)(o_.max_inner + o_.lobpcg_max_iter + 8);
+        int64_t granted = 0;   // steps granted to each lane so far
+        for (;;) {
+            if (use_graph) UBQP_CK(cudaGraphLaunch(gexec_, stream_));
+            else UBQP_CK(enqueue());
+            launches_ += 2;
+            granted += loop_budget_;
+            UBQP_CK(cudaStreamSynchronize(stream_));
+            if (prof) {
+                float ms = 0.f;
+                UBQP_CK(cudaEventElapsedTime(&ms, evA_[0], evA_[1]));
+                phase_a_ms_ += ms;
+                phase_a_launches_ += 1;
+            }
+            int32_t err = 0;
+            UBQP_CK(cudaMemcpy(&err, la.err, sizeof(err), cudaMemcpyDeviceToHost));
+            if (err) {
+                set_error("a bounded wait in the lane loop ran out");
+                return UBQP_ETIMEOUT;
+            }
+            bool stop = false;
+            int rc = check_target(stop);
+            if (rc) return rc;
+            if (stop) break;
+            if (*h_active_ == 0) break;
+            if (granted > cap) {
+                set_error("step cap %lld exceeded", (long long)cap);
+                return UBQP_ETIMEOUT;
+            }
+        }
+        UBQP_CK(cudaEventRecord(ev1_, stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0_, ev1_);
+        ms_device_ = ms;
+        ticks_ = -1;   // filled from the lanes' own step counts
         return UBQP_OK;
     }
 
@@ -770,7 +905,9 @@ class Solver {
             s->lanes_capped += S.status == 1 ? 1 : 0;
         }
         s->lanes = nlanes_;
-        s->ticks = ticks_;
+        int64_t most = 0;
+        for (const LaneState& S : st) most = std::max<int64_t>(most, S.updates);
+        s->ticks = ticks_ >= 0 ? ticks_ : most;
         s->ms_device = ms_device_;
         s->phase_a_ms = phase_a_ms_;
         s->phase_a_launches = phase_a_launches_;
@@ -785,6 +922,7 @@ class Solver {
         UBQP_CK(cudaStreamSynchronize(stream_));
         s->phase_a_flops = (int64_t)fl;
         s->cluster_size = tc_ ? tc_S_ : 0;
+        s->gemv_kernel = tc_ ? 0 : (loop_ ? 2 : 1);
         UBQP_CK(cudaMemcpyAsync(s->inner_hist, ar_.at<int64_t>(o_hist_), sizeof(s->inner_hist), cudaMemcpyDeviceToHost,
                                 stream_));
         UBQP_CK(cudaStreamSynchronize(stream_));
@@ -856,6 +994,9 @@ class Solver {
     int num_sms_ = 148;
     int max_ld_ = 32;
     int rows_per_item_ = 32;
+    bool loop_ = false;          // FP32 lanes on the persistent lane loop
+    int loop_grid_ = 0, loop_budget_ = 0;
+    uint64_t loop_cap_ = 0;
     int nitems_ = 0;
     int nlanes_ = 0;
     bool inexact_ = false;
@@ -873,7 +1014,7 @@ class Solver {
     std::vector<LaneInit> lane_init_;
     std::vector<size_t> o_vec_, o_bx_, o_part_, o_trace_x_, o_trace_a_, o_x0_, o_p0_;
     size_t o_scal_ = 0, o_valid_ = 0, o_inexact_ = 0, o_hist_ = 0, o_active_ = 0, o_states_ = 0, o_lanes_ = 0,
-           o_linit_ = 0, o_items_ = 0, o_bytes_ = 0, o_counters_ = 0, o_tcinst_ = 0, o_tcerr_ = 0,
+           o_linit_ = 0, o_items_ = 0, o_bytes_ = 0, o_counters_ = 0, o_tcinst_ = 0, o_tcerr_ = 0, o_ring_ = 0, o_ht_ = 0, o_loopctr_ = 0, o_budget_ = 0,
            o_flops_ = 0, o_queue_ = 0;
     int tc_tiles_ = 0, tc_S_ = 1, tc_stages_ = 2, max_bn_ = 16;
     size_t o_final_lane0_ = 0, o_final_nl_ = 0, o_final_obj_ = 0, o_final_best_ = 0, o_final_xptr_ = 0,
@@ -915,6 +1056,8 @@ void ubqp_opts_default(ubqp_opts* o)
     o->profile_kernels = 0;
     o->stop_at_target = 0;
     o->tc_cluster = 0;
+    o->gemv_kernel = 0;
+    o->lane_budget = 0;
     o->target_objective = INFINITY;
     o->stream = nullptr;
     o->mu = nullptr;

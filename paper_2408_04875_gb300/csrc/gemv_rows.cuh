@@ -1,0 +1,141 @@
+// Row kernels shared by the two schedulers of phase A on CUDA cores (the lock-step tick
+// kernel and the persistent lane loop): the dot products of matrix rows with the lane's
+// input u held in shared memory, and the work of one (lane, row block) item.  Both
+// schedulers call the same functions, so a lane's arithmetic does not depend on which one
+// runs it.
+#pragma once
+
+#include "lane_update.cuh"
+
+namespace ubqp {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+// dot of one row with u (shared), FP32 row, 16-byte loads.  The four products of each
+// 16-byte group are summed with FMAs and the group sum is added to a TwoSum-compensated
+// accumulator: the error stays near 4 eps times the sum of |terms| instead of growing with
+// the row length, at under 3 FP32 operations per matrix entry.
+__device__ __forceinline__ void cacc4(float2& acc, float4 q, float4 u)
+{
+    float t = __fmul_rn(q.x, u.x);
+    t = fmaf(q.y, u.y, t);
+    t = fmaf(q.z, u.z, t);
+    t = fmaf(q.w, u.w, t);
+    float s, e;
+    two_sum(acc.x, t, s, e);
+    acc.x = s;
+    acc.y += e;
+}
+
+__device__ __forceinline__ float4 ldg_stream(const float4* p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// two rows at once (independent load streams)
+__device__ __forceinline__ void row_dot2_f32(const float* __restrict__ ra, const float* __restrict__ rb,
+                                             const float* su, int ld, int lane, float& va, float& vb)
+{
+    const float4* a4 = reinterpret_cast<const float4*>(ra);
+    const float4* b4 = reinterpret_cast<const float4*>(rb);
+    const float4* u4 = reinterpret_cast<const float4*>(su);
+    const int n4 = ld >> 2;
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+    int c = lane;
+    for (; c + 32 < n4; c += 64) {
+        const float4 qa0 = ldg_stream(a4 + c), qa1 = ldg_stream(a4 + c + 32);
+        const float4 qb0 = ldg_stream(b4 + c), qb1 = ldg_stream(b4 + c + 32);
+        const float4 u0 = u4[c], u1 = u4[c + 32];
+        cacc4(a0, qa0, u0);
+        cacc4(b0, qb0, u0);
+        cacc4(a1, qa1, u1);
+        cacc4(b1, qb1, u1);
+    }
+    for (; c < n4; c += 32) {
+        const float4 u0 = u4[c];
+        cacc4(a0, ldg_stream(a4 + c), u0);
+        cacc4(b0, ldg_stream(b4 + c), u0);
+    }
+    float2 a = csum_shfl_reduce(csum_merge(a0, a1));
+    float2 b = csum_shfl_reduce(csum_merge(b0, b1));
+    va = a.x + a.y;
+    vb = b.x + b.y;
+}
+
+// dot of one row of the evaluation matrix (each FP64 entry q stored as FP32 hi + lo with
+// hi + lo = q to about 2^-48) with a 0/1 vector: the products are the entries themselves,
+// so TwoSum accumulation of hi and lo gives the FP64 row sum without FP64 arithmetic
+// (exactly, for integer data)
+__device__ __forceinline__ double row_dot_eval(const float2* __restrict__ row, const float* su, int ld,
+                                               int lane)
+{
+    const float4* r4 = reinterpret_cast<const float4*>(row);   // two entries per 16 bytes
+    const float2* u2 = reinterpret_cast<const float2*>(su);
+    const int n2 = ld >> 1;
+    float2 ah = make_float2(0.f, 0.f), al = ah;
+    for (int c = lane; c < n2; c += 32) {
+        float4 q = __ldg(r4 + c);
+        float2 u = u2[c];
+        if (u.x != 0.f) { csum_add(ah, q.x); csum_add(al, q.y); }
+        if (u.y != 0.f) { csum_add(ah, q.z); csum_add(al, q.w); }
+    }
+    ah = csum_shfl_reduce(ah);
+    al = csum_shfl_reduce(al);
+    return ((double)ah.x + (double)ah.y) + ((double)al.x + (double)al.y);
+}
+
+// u (written by the lane's last update, zero beyond n) into shared memory
+__device__ __forceinline__ void item_load_u(const LaneDev& L, float* su)
+{
+    const float4* g4 = reinterpret_cast<const float4*>(L.vec + (size_t)V_U * L.ld);
+    float4* s4 = reinterpret_cast<float4*>(su);
+    for (int c = threadIdx.x; c < (L.ld >> 2); c += kThreads) s4[c] = g4[c];
+}
+
+// v_r = (row row0 + r of the phase's matrix) . u for r < rows, into sv[r]
+__device__ __forceinline__ void item_rows(const LaneDev& L, int ph, int row0, int rows, const float* su, double* sv)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ld = L.ld;
+    if (ph == PH_EVAL) {
+        for (int r = warp; r < rows; r += kWarps) {
+            double v = row_dot_eval(L.Qeval + (size_t)(row0 + r) * ld, su, ld, lane);
+            if (lane == 0) sv[r] = v;
+        }
+    } else {
+        for (int r = warp; r < rows; r += 2 * kWarps) {
+            const int r2 = r + kWarps < rows ? r + kWarps : r;
+            float va, vb;
+            row_dot2_f32(L.Qoff + (size_t)(row0 + r) * ld, L.Qoff + (size_t)(row0 + r2) * ld, su, ld, lane, va, vb);
+            if (lane == 0) {
+                sv[r] = (double)va;
+                sv[r2] = (double)vb;
+            }
+        }
+    }
+}
+
+// per-row epilogue of the item's rows and its partial L.part[blk]; also counts the
+// algorithmic bytes of the item when P.bytes is set: the stored entries of these rows once
+// (FP32, or 8 bytes per entry of the evaluation matrix), the input vector once per lane
+// (charged to block 0), and the per-row vectors the epilogue touches
+__device__ __forceinline__ void item_finish(const LaneDev& L, int ph, int k, int blk, int row0, int rows,
+                                            const double* sv, const Params& P)
+{
+    Acc a;
+    a.zero();
+    if ((int)threadIdx.x < rows) row_epilogue(L, ph, k, row0 + threadIdx.x, sv[threadIdx.x], a, P.tau_z);
+    block_reduce_write<kWarps>(a, ph, L.part + blk, ph == PH_EVAL);
+    if (P.bytes && threadIdx.x == 0) {
+        unsigned long long by = (unsigned long long)rows * L.n * (ph == PH_EVAL ? 8ull : 4ull) +
+                                (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
+        atomicAdd(P.bytes, by);
+    }
+}
+
+}  // namespace ubqp

@@ -508,6 +508,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
     }
     if (threadIdx.x == 0) {
         if ((act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
+        S.updates += 1;
         *L.st = S;
         if (S.phase != PH_DONE && active_count) atomicAdd(active_count, 1);
     }

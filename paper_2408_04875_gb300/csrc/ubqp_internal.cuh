@@ -87,6 +87,7 @@ struct __align__(16) LaneState {
     int64_t lob_iters;
     int64_t jac_iters;
     int64_t floor_steps;
+    int64_t updates;    // steps (updates) this lane has taken
 };
 
 // static description of one lane (written by the host, read-only on the device)
@@ -382,6 +383,30 @@ cudaError_t prepare_phase_a_gemv(int max_ld);
 int gemv_grid(int max_ld, int nitems);
 cudaError_t launch_phase_a_gemv_f32(const TickArgs& a, cudaStream_t s);
 cudaError_t launch_phase_a_grad(const TickArgs& a, int dtype, int64_t n, cudaStream_t s);
+// persistent lane loop (GEMV lanes): a ring of (lane, row block) entries shared by all CTAs
+struct LoopArgs {
+    const LaneDev* lanes;
+    const int2* items;          // every lane's blocks, largest lanes first (seeding order)
+    int32_t nitems;
+    int32_t nlanes;
+    int32_t rows_per_item;
+    int32_t max_ld;
+    int32_t budget;             // steps each lane may take in one launch
+    int32_t grid;               // CTAs of the loop kernel
+    unsigned long long* ring;   // cap slots: (sequence << 32) | (lane << 16) | block
+    unsigned long long cap;     // power of two >= 2 (nitems + grid)
+    unsigned long long* head;   // positions popped
+    unsigned long long* tail;   // positions pushed
+    int32_t* running;           // lanes that may still push in this launch
+    int32_t* active_after;      // lanes unfinished when the launch ends
+    int32_t* err;               // set when a bounded wait runs out
+    int32_t* budget_left;       // per lane
+    Params P;
+};
+
+cudaError_t prepare_lane_loop(int max_ld);
+int lane_loop_grid(int max_ld);
+cudaError_t launch_lane_loop(const LoopArgs& a, cudaStream_t s);   // seed + loop kernels
 cudaError_t launch_phase_b(const TickArgs& a, int32_t* active_count, cudaStream_t s);
 cudaError_t launch_grad_reduce(const LaneDev* lanes, int nlanes, void* h_out, int dtype,
                                cudaStream_t s);

@@ -174,6 +174,40 @@ def test_ragged_batch_matches_single_solves(ub):
         assert f1 == f and np.array_equal(x1, x)
 
 
+@pytest.mark.parametrize("specs", [[(37, 1)], [(1000, 2)], [(2500, 3)], [(250, 4), (1000, 5), (61, 6)]])
+def test_schedulers_agree_bitwise(ub, specs):
+    """The lock-step scheduler (one launch per step of all lanes) and the persistent lane
+    loop (lanes advance independently inside one launch) run the same row kernels in the
+    same order of operations, so every solve is bit-identical: single lanes of 1, 63 and
+    157 row blocks and a ragged batch of three sizes."""
+    Qs = [I.random_ubqp(n, 0.1, s)[0] for n, s in specs]
+    mus = [I.perturbation(Q, s) for Q, (n, s) in zip(Qs, specs)]
+    kw = dict(max_outer=4)
+    x1, f1, s1 = ub.solve_batched(Qs, None, mus, gemv_kernel=1, **kw)
+    x2, f2, s2 = ub.solve_batched(Qs, None, mus, gemv_kernel=2, **kw)
+    assert s1["gemv_kernel"] == 1 and s2["gemv_kernel"] == 2
+    assert np.array_equal(f1, f2) and all(np.array_equal(a, b) for a, b in zip(x1, x2))
+    for key in ("inner_iters", "outer_steps", "lobpcg_iters", "jacobi_iters", "var_updates"):
+        assert s1[key] == s2[key], key
+    _, _, s0 = ub.solve_batched(Qs, None, mus, **kw)
+    assert s0["gemv_kernel"] == 2                       # the default
+
+
+def test_lane_loop_small_budget_relaunches(ub):
+    """A budget of 3 steps per launch makes the host relaunch the loop hundreds of times;
+    lanes that finish early stay in the seeded ring as skip entries.  Same bits as one
+    long launch, and the step count is the busiest lane's."""
+    specs = [(300, 7), (64, 8), (129, 9)]
+    Qs = [I.random_ubqp(n, 0.1, s)[0] for n, s in specs]
+    mus = [I.perturbation(Q, s) for Q, (n, s) in zip(Qs, specs)]
+    x1, f1, s1 = ub.solve_batched(Qs, None, mus, gemv_kernel=2)
+    x2, f2, s2 = ub.solve_batched(Qs, None, mus, gemv_kernel=2, lane_budget=3)
+    assert np.array_equal(f1, f2) and all(np.array_equal(a, b) for a, b in zip(x1, x2))
+    assert s1["ticks"] == s2["ticks"] and s2["kernel_launches"] > s1["kernel_launches"] + 100
+    _, _, s3 = ub.solve_batched(Qs, None, mus, profile_kernels=2, max_outer=2)
+    assert s3["gemv_kernel"] == 1                       # the per-step timeline runs lock-step
+
+
 def test_restarts_keep_best_and_are_exact(ub):
     Q, b = I.random_ubqp(80, 0.2, 9, b_range=(-20, 20))
     mu = I.perturbation(Q, 9)
