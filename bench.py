@@ -177,24 +177,120 @@ def run_c4(args):
     return 0
 
 
-def cpu_baseline(budget_s: float = 12.0):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the same
-    workload: the n = 250 instances of the sweep, solved one after another until the
-    time budget is used."""
+C5_WORKLOAD = ("ragged multi-instance batch: 512 instances, n uniform in [100,3000], density uniform in "
+               "[0.05,1], half integer-[-100,100] Q, half Max-Cut (+-1 edges, f = -cut), BF16 Q_off on tensor "
+               "cores with FP32 accumulation, FP64 exact evaluation, starts per instance from the restart tuner")
+
+
+def run_c5(args):
+    """Tensor-core path on the ragged 512-instance batch: one call runs every instance x start as
+    a lane; the restart tuner picks the starts per instance (its probes run before the timed
+    region).  The outer loop is capped (default 3 penalty updates) so that a step stays within
+    seconds; throughput counts the projected-gradient iterations actually run."""
+    import numpy as np
+    import torch
+    import paper_2408_04875_gb300 as ub
+    from paper_2408_04875_gb300 import instances as I
+    torch.cuda.set_device(0)
+    specs = I.c5_specs(args.c5_count)
+    t0 = time.perf_counter()
+    Qd, bd, Qh, bh = [], [], [], []
+    for sp in specs:
+        Q, b = I.c5_instance(sp)
+        Qd.append(torch.from_numpy(Q).cuda())
+        bd.append(torch.from_numpy(b).cuda())
+        if len(Qh) < 8:          # a sample kept on the host to re-evaluate objectives
+            Qh.append(Q)
+            bh.append(b)
+    gen_s = time.perf_counter() - t0
+    max_outer = args.max_outer if args.max_outer is not None else 3
+    kw = dict(precision=ub.BF16X2_TC, max_outer=max_outer)
+    # first call: restart tuner + a full warm-up step
+    _, _, st0 = ub.solve_batched(Qd, bd, None, restarts=args.c5_restarts, **kw)
+    R = st0["restarts"]
+    for _ in range(max(0, args.warmup - 1)):
+        ub.solve_batched(Qd, bd, None, restarts=R, **kw)
+    sampler = ClockSampler(0)
+    sampler.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    stats, xs, objs = [], None, None
+    for _ in range(args.steps):
+        xs, objs, st = ub.solve_batched(Qd, bd, None, restarts=R, profile_kernels=0 if args.no_profile else 1, **kw)
+        stats.append(st)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    # exactness of the returned objectives on the host sample
+    exact = all(float(x.astype(np.float64) @ Q @ x.astype(np.float64) + b @ x) == float(f)
+                for Q, b, x, f in zip(Qh, bh, xs, objs))
+    work = sum(s["var_updates"] for s in stats)
+    pa_ms = sum(s["phase_a_ms"] for s in stats)
+    pa_n = sum(s["phase_a_launches"] for s in stats)
+    by = sum(s["phase_a_bytes"] for s in stats)
+    flops = sum(s["phase_a_flops"] for s in stats)
+    peak, peak_kind = _peaks()
+    ach = by / (pa_ms * 1e-3) / 1e9 if pa_ms > 0 else None
+    line = {"metric": METRIC, "value": work / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x2", "data": "synthetic",
+            "config": {"workload": C5_WORKLOAD, "instances": len(specs), "max_outer": max_outer,
+                       "restarts_per_instance": R, "restart_probe_us": st0["restart_probe_us"],
+                       "lanes": stats[-1]["lanes"], "cluster_size": stats[-1]["cluster_size"],
+                       "ticks_per_step": stats[-1]["ticks"], "generation_s": round(gen_s, 1),
+                       "objectives_exact_on_sample": exact,
+                       "l2": "BF16 Q_off of the batch (3.4 GB) exceeds L2; no flush"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                         "frac": ach / peak if ach else None, "traffic": None, "kernel": "phase_a_tc_kernel",
+                         "launches": pa_n, "avg_launch_us": pa_ms * 1e3 / max(pa_n, 1),
+                         "algorithmic_bytes_per_launch": by / max(pa_n, 1),
+                         "tflops": flops / (pa_ms * 1e-3) / 1e12 if pa_ms > 0 else None, "peak_kind": peak_kind},
+            "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(budget_s: float = 12.0, threads: int | None = None):
+    """The FP64 oracle as it stands, on a bounded sample of the same workload: whole solves of
+    the n = 250 instances of the sweep (taken in turn, again from the first when all ten have
+    started), instance-parallel on `threads` host threads (default: every core; the oracle is
+    plain C called through ctypes, which releases the GIL).  No thread starts a solve once the
+    budget has run out; the value counts the solves that finished."""
+    import concurrent.futures as cf
+    import threading
     import oracle as O
     from paper_2408_04875_gb300 import instances as I
     O.build()
-    done, work, t0 = 0, 0, time.perf_counter()
+    threads = threads or os.cpu_count() or 1
+    todo = []
     for seed in range(SEEDS_PER_SIZE):
         Q, _ = I.c2_instance(250, seed)
-        _, _, st = O.solve(Q, None, I.perturbation(Q, seed))
-        work += st["grad_evals"] * 250
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
+        todo.append((250, Q, I.perturbation(Q, seed)))
+    lock = threading.Lock()
+    state = {"next": 0, "work": 0, "done": 0}
+    t0 = time.perf_counter()
+
+    def worker():
+        while True:
+            with lock:
+                if time.perf_counter() - t0 > budget_s:
+                    return
+                n, Q, mu = todo[state["next"] % len(todo)]
+                state["next"] += 1
+            _, _, st = O.solve(Q, None, mu)
+            with lock:
+                state["work"] += st["grad_evals"] * n
+                state["done"] += 1
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        for f in [ex.submit(worker) for _ in range(threads)]:
+            f.result()
     dt = time.perf_counter() - t0
-    return {"value": work / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} of the 10 n=250 instances of the sweep, full solves, {dt:.1f} s"}
+    return {"value": state["work"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{state['done']} whole solves of the 10 n=250 instances of the sweep (in turn), "
+                      f"{threads} threads, {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -211,8 +307,8 @@ def run_reference(args):
             "warmup": args.warmup, "impl": "reference", "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "reference_sample": steps[-1]["sample"]},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": steps[-1]["sample"], "value": value,
-                             "unit": UNIT},
+            "cpu_baseline": {"kind": "oracle", "cores": steps[-1]["cores"], "sample": steps[-1]["sample"],
+                             "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -238,7 +334,8 @@ def run_gpu(args):
     Qd = [torch.from_numpy(Q).cuda() for Q in Qs]
     Md = [torch.from_numpy(m).cuda() for m in mus]
     torch.cuda.synchronize()
-    kw = dict(profile_kernels=0 if args.no_profile else 1, gemv_kernel=args.gemv_kernel)
+    kw = dict(profile_kernels=0 if args.no_profile else 1, gemv_kernel=args.gemv_kernel,
+              lane_budget=args.lane_budget)
     if args.max_outer is not None:
         kw["max_outer"] = args.max_outer
     for _ in range(args.warmup):
@@ -326,15 +423,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"])
+    ap.add_argument("--c5-count", type=int, default=512, help="instances of the ragged batch")
+    ap.add_argument("--c5-restarts", type=int, default=0, help="starts per instance (0 = restart tuner)")
     ap.add_argument("--restarts", type=int, default=256)
     ap.add_argument("--gemv-kernel", type=int, default=0, choices=[0, 1, 2],
-                    help="FP32 matrix-vector kernel: 0 library's choice, 1 register-streamed, 2 bulk-copy")
+                    help="scheduler of the FP32 lanes: 0 library's choice, 1 lock-step, 2 lane loop")
+    ap.add_argument("--lane-budget", type=int, default=0,
+                    help="lane loop: steps per lane per launch (0 = library default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":
         return run_c4(args)
+    if args.workload == "c5":
+        return run_c5(args)
     return run_gpu(args)
 
 

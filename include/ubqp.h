@@ -80,6 +80,10 @@ typedef struct {
     int32_t cluster_size;    /* CTAs per cluster of the tensor-core launches (0: none)  */
     int32_t gemv_kernel;     /* scheduler that ran the FP32 lanes: 1 lock-step, 2 lane  */
                              /* loop (0: tensor-core lanes)                             */
+    int32_t restarts;        /* starts per instance that ran (the tuner's pick when     */
+                             /* opts->restarts == 0)                                    */
+    float restart_probe_us[5]; /* restart tuner: step time measured with 1, 8, 32, 64  */
+                             /* and 128 starts per instance (0 when not tuned)          */
     int64_t inner_hist[UBQP_HIST_BINS]; /* projected steps per subproblem (Fig. 5)   */
 } ubqp_stats;
 
@@ -101,7 +105,11 @@ typedef struct {
     double sigma_rel;        /* perturbation std-dev / max|Q_ij| (i != j): 1e-3; 0 = off */
     uint64_t seed;           /* seeds the library's own draws (perturbation, starts)  */
     int restarts;            /* starts per instance: 1 = x^0 of Eq. (gamma) only;      */
-                             /* R > 1 adds R-1 starts uniform in [0,1]^n              */
+                             /* R > 1 adds R-1 starts uniform in [0,1]^n; 0 = chosen  */
+                             /* by the restart tuner from {1, 8, 32, 64, 128}: each    */
+                             /* count runs a 32-step probe on the real batch and the   */
+                             /* largest whose step time is at most twice that of one  */
+                             /* start wins (needs x_starts == NULL)                    */
     int precision;           /* UBQP_FP32 (default), UBQP_BF16X2_TC, UBQP_BF16_TC      */
     int lobpcg_max_iter;     /* cap of the lambda_min eigen-solver: 64                 */
     double lobpcg_tol;       /* relative change of the Ritz value to stop: 1e-4        */
@@ -114,8 +122,8 @@ typedef struct {
                              /* 0 = chosen by the library's tuner                      */
     int gemv_kernel;         /* scheduler of the FP32 lanes: 1 lock-step (one launch   */
                              /* per step of all lanes), 2 persistent lane loop (lanes  */
-                             /* advance independently inside one launch); 0 = 2, or 1  */
-                             /* when profile_kernels == 2 (per-step timeline)          */
+                             /* advance independently inside one launch); 0 = 2 for 4  */
+                             /* or more lanes, else 1 (and 1 when profile_kernels == 2) */
     int lane_budget;         /* lane loop: steps per lane between host checks; 0 = 1024 */
     double target_objective; /* objective to time against (used when finite)           */
     void* stream;            /* cudaStream_t, NULL = default stream                    */

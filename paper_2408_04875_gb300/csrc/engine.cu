@@ -124,7 +124,8 @@ static int check_opts(const ubqp_opts& o)
     if (!(o.eta > 0.0 && o.eta < 1.0)) { set_error("eta must lie in (0, 1) (Eq. (eq:alpha1))"); return UBQP_EINVAL; }
     if (!(o.tol_inner > 0.0) || !(o.tol_outer >= 0.0)) { set_error("tolerances must be positive"); return UBQP_EINVAL; }
     if (!(o.alpha_min > 0.0) || !(o.alpha_max >= o.alpha_min)) { set_error("bad BB step clamp"); return UBQP_EINVAL; }
-    if (o.restarts < 1 || o.restarts > 4096) { set_error("restarts must be in [1, 4096]"); return UBQP_EINVAL; }
+    if (o.restarts < 0 || o.restarts > 4096) { set_error("restarts must be in [0, 4096]"); return UBQP_EINVAL; }
+    if (o.restarts == 0 && o.x_starts) { set_error("the restart tuner (restarts = 0) draws its own starts"); return UBQP_EINVAL; }
     if (o.precision != UBQP_FP32 && o.precision != UBQP_BF16X2_TC && o.precision != UBQP_BF16_TC) {
         set_error("unknown precision");
         return UBQP_EINVAL;
@@ -329,13 +330,16 @@ class Solver {
                 set_error("the lane loop takes at most 65533 lanes of at most 65535 row blocks");
                 return UBQP_ENOTSUP;
             }
-            loop_ = fits && (o_.gemv_kernel == 2 || (o_.gemv_kernel == 0 && o_.profile_kernels < 2));
+            // automatic choice: the loop pays off once several lanes can overlap one another's
+            // update latency; one to three lanes step faster in lock-step
+            loop_ = fits && (o_.gemv_kernel == 2 ||
+                             (o_.gemv_kernel == 0 && o_.profile_kernels < 2 && lanes.size() >= 4));
             if (loop_) {
                 UBQP_CK(prepare_lane_loop(max_ld));
                 loop_grid_ = lane_loop_grid(max_ld);
                 loop_cap_ = 1024;
                 while (loop_cap_ < 2 * ((uint64_t)nitems + (uint64_t)loop_grid_)) loop_cap_ *= 2;
-                loop_budget_ = o_.lane_budget > 0 ? o_.lane_budget : 1024;
+                loop_budget_ = probe_ticks_ > 0 ? probe_ticks_ : (o_.lane_budget > 0 ? o_.lane_budget : 1024);
                 o_ring_ = ar_.reserve(loop_cap_ * sizeof(unsigned long long));
                 o_ht_ = ar_.reserve(2 * sizeof(unsigned long long));
                 o_loopctr_ = ar_.reserve(3 * sizeof(int32_t));
@@ -704,6 +708,7 @@ class Solver {
                     return UBQP_ETIMEOUT;
                 }
             }
+            if (probe_ticks_ > 0 && ticks >= probe_ticks_) break;
             bool stop = false;
             int rc = check_target(stop);
             if (rc) return rc;
@@ -819,6 +824,7 @@ class Solver {
                 set_error("a bounded wait in the lane loop ran out");
                 return UBQP_ETIMEOUT;
             }
+            if (probe_ticks_ > 0) break;
             bool stop = false;
             int rc = check_target(stop);
             if (rc) return rc;
@@ -982,6 +988,8 @@ class Solver {
 
     bool inexact() const { return inexact_; }
     int64_t ticks() const { return ticks_; }
+    double ms_device() const { return ms_device_; }
+    int probe_ticks_ = 0;   // > 0: stop after about this many steps (restart tuner probes)
 
   private:
     ubqp_opts o_;
@@ -1094,6 +1102,65 @@ int64_t ubqp_profile_timeline(float* ms_out, int64_t* work_out, int64_t cap)
     return n;
 }
 
+// every instance's R lanes: start 0 from x^0 of Eq. (gamma) (Jacobi sweeps first), the
+// others from the caller's starts or uniform draws in [0,1]^n
+static std::vector<LaneIn> build_lanes(const std::vector<InstIn>& insts, int R)
+{
+    std::vector<LaneIn> lanes;
+    lanes.reserve(insts.size() * (size_t)R);
+    for (size_t t = 0; t < insts.size(); ++t)
+        for (int r = 0; r < R; ++r) {
+            LaneIn l;
+            l.inst = (int)t;
+            l.restart = r;
+            l.phase = r == 0 ? PH_JACOBI : PH_EVAL;
+            l.start_kind = r == 0 ? 0 : 1;
+            l.x0 = (r > 0 && insts[t].starts) ? insts[t].starts + (size_t)(r - 1) * insts[t].n : nullptr;
+            l.p0 = nullptr;
+            l.stop_after = 0;
+            l.trace_len = 0;
+            lanes.push_back(l);
+        }
+    return lanes;
+}
+
+// Restart tuner: a 32-step probe of the real batch with each candidate count of starts per
+// instance; the largest count whose step time is at most twice the single-start step time
+// is returned.  Extra starts that leave the step time nearly unchanged (the step is bound by
+// reading Q once, or by latency) improve the best objective at little cost; the tuner stops
+// short of counts that would multiply the time of every step.
+static int tune_restarts(const std::vector<InstIn>& insts, const ubqp_opts& o, bool tc, float* probe_us)
+{
+    static const int kCand[5] = {1, 8, 32, 64, 128};
+    double t1 = 0.0;
+    int best = 1;
+    for (int c = 0; c < 5; ++c) {
+        ubqp_opts po = o;
+        po.restarts = kCand[c];
+        po.stats = nullptr;
+        po.profile_kernels = 0;
+        po.stop_at_target = 0;
+        po.target_objective = INFINITY;
+        po.max_ticks_per_sync = 32;
+        Solver S(po);
+        S.probe_ticks_ = 32;
+        std::vector<LaneIn> lanes = build_lanes(insts, kCand[c]);
+        int rc = S.setup(insts, lanes, tc);
+        if (rc == UBQP_ENOMEM) break;   // this many starts do not fit: keep the best so far
+        if (rc) return rc;
+        rc = S.run();
+        if (rc) return rc;
+        ubqp_stats st;
+        rc = S.fill_stats(&st);
+        if (rc) return rc;
+        const double t = S.ms_device() / (double)std::max<int64_t>(st.ticks, 1);
+        probe_us[c] = (float)(1e3 * t);
+        if (c == 0) t1 = t;
+        if (t <= 2.0 * t1) best = kCand[c];
+    }
+    return best;
+}
+
 int ubqp_solve_batched(int32_t num, const int64_t* n, const double* const* Q, const double* const* b,
                        const ubqp_opts* o_in, uint8_t* const* x_out, double* obj_out)
 {
@@ -1112,8 +1179,6 @@ int ubqp_solve_batched(int32_t num, const int64_t* n, const double* const* Q, co
     }
     const bool tc = o.precision != UBQP_FP32;
     std::vector<InstIn> insts(num);
-    std::vector<LaneIn> lanes;
-    const int R = std::max(1, o.restarts);
     for (int32_t t = 0; t < num; ++t) {
         insts[t].n = n[t];
         insts[t].Q = Q[t];
@@ -1121,21 +1186,18 @@ int ubqp_solve_batched(int32_t num, const int64_t* n, const double* const* Q, co
         insts[t].mu = o.mu ? o.mu[t] : nullptr;
         insts[t].starts = o.x_starts ? o.x_starts[t] : nullptr;
         insts[t].reformulated = false;
-        for (int r = 0; r < R; ++r) {
-            LaneIn l;
-            l.inst = t;
-            l.restart = r;
-            l.phase = r == 0 ? PH_JACOBI : PH_EVAL;
-            l.start_kind = r == 0 ? 0 : 1;
-            l.x0 = (r > 0 && insts[t].starts) ? insts[t].starts + (size_t)(r - 1) * n[t] : nullptr;
-            l.p0 = nullptr;
-            l.stop_after = 0;
-            l.trace_len = 0;
-            lanes.push_back(l);
-        }
     }
+    int rc = check_opts(o);   // before the tuner, which builds lanes from these options
+    if (rc) return rc;
+    float probe_us[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (o.restarts == 0) {
+        rc = tune_restarts(insts, o, tc, probe_us);
+        if (rc < 0) return rc;
+        o.restarts = rc;
+    }
+    std::vector<LaneIn> lanes = build_lanes(insts, o.restarts);
     Solver S(o);
-    int rc = S.setup(insts, lanes, tc);
+    rc = S.setup(insts, lanes, tc);
     if (rc) return rc;
     rc = S.run();
     if (rc) return rc;
@@ -1145,6 +1207,8 @@ int ubqp_solve_batched(int32_t num, const int64_t* n, const double* const* Q, co
     rc = S.fill_stats(&st);
     if (rc) return rc;
     st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    st.restarts = o.restarts;
+    for (int c = 0; c < 5; ++c) st.restart_probe_us[c] = probe_us[c];
     if (o.stats) *o.stats = st;
     return st.lanes_capped > 0 ? UBQP_EMAXITER : UBQP_OK;
 }

@@ -31,56 +31,89 @@ __device__ __forceinline__ void cacc4(float2& acc, float4 q, float4 u)
 __device__ __forceinline__ float4 ldg_stream(const float4* p)
 {
     float4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0,%1,%2,%3}, [%4];"
                  : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                  : "l"(p));
     return v;
 }
 
-// two rows at once (independent load streams)
-__device__ __forceinline__ void row_dot2_f32(const float* __restrict__ ra, const float* __restrict__ rb,
-                                             const float* su, int ld, int lane, float& va, float& vb)
+// dot of NR rows (1 or 2) with u: 16-byte groups at columns c, c + 32, c + 64, c + 96 (in
+// float4 units) are loaded for every row before any is used, so each lane keeps 4 * NR
+// loads in flight.  Group j goes to accumulator j & 1 of its row, in column order; the
+// tails keep the same alternation, so the result does not depend on the unrolling or NR.
+template <int NR>
+__device__ __forceinline__ void rows_dot_f32(const float* const (&rows)[NR], const float* su, int ld, int lane,
+                                             float (&out)[NR])
 {
-    const float4* a4 = reinterpret_cast<const float4*>(ra);
-    const float4* b4 = reinterpret_cast<const float4*>(rb);
     const float4* u4 = reinterpret_cast<const float4*>(su);
     const int n4 = ld >> 2;
-    float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+    float2 acc[NR][2];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
     int c = lane;
+    for (; c + 96 < n4; c += 128) {
+        float4 q[NR][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) q[r][j] = ldg_stream(reinterpret_cast<const float4*>(rows[r]) + c + 32 * j);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float4 u = u4[c + 32 * j];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) cacc4(acc[r][j & 1], q[r][j], u);
+        }
+    }
     for (; c + 32 < n4; c += 64) {
-        const float4 qa0 = ldg_stream(a4 + c), qa1 = ldg_stream(a4 + c + 32);
-        const float4 qb0 = ldg_stream(b4 + c), qb1 = ldg_stream(b4 + c + 32);
-        const float4 u0 = u4[c], u1 = u4[c + 32];
-        cacc4(a0, qa0, u0);
-        cacc4(b0, qb0, u0);
-        cacc4(a1, qa1, u1);
-        cacc4(b1, qb1, u1);
+        float4 q[NR][2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) q[r][j] = ldg_stream(reinterpret_cast<const float4*>(rows[r]) + c + 32 * j);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float4 u = u4[c + 32 * j];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) cacc4(acc[r][j], q[r][j], u);
+        }
     }
     for (; c < n4; c += 32) {
-        const float4 u0 = u4[c];
-        cacc4(a0, ldg_stream(a4 + c), u0);
-        cacc4(b0, ldg_stream(b4 + c), u0);
+        const float4 u = u4[c];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) cacc4(acc[r][0], ldg_stream(reinterpret_cast<const float4*>(rows[r]) + c), u);
     }
-    float2 a = csum_shfl_reduce(csum_merge(a0, a1));
-    float2 b = csum_shfl_reduce(csum_merge(b0, b1));
-    va = a.x + a.y;
-    vb = b.x + b.y;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const float2 a = csum_shfl_reduce(csum_merge(acc[r][0], acc[r][1]));
+        out[r] = a.x + a.y;
+    }
 }
 
 // dot of one row of the evaluation matrix (each FP64 entry q stored as FP32 hi + lo with
 // hi + lo = q to about 2^-48) with a 0/1 vector: the products are the entries themselves,
 // so TwoSum accumulation of hi and lo gives the FP64 row sum without FP64 arithmetic
-// (exactly, for integer data)
-__device__ __forceinline__ double row_dot_eval(const float2* __restrict__ row, const float* su, int ld,
-                                               int lane)
+// (exactly, for integer data).  Four 16-byte groups (eight entries) in flight per lane.
+__device__ __forceinline__ double row_dot_eval(const float2* __restrict__ row, const float* su, int ld, int lane)
 {
     const float4* r4 = reinterpret_cast<const float4*>(row);   // two entries per 16 bytes
     const float2* u2 = reinterpret_cast<const float2*>(su);
     const int n2 = ld >> 1;
     float2 ah = make_float2(0.f, 0.f), al = ah;
-    for (int c = lane; c < n2; c += 32) {
-        float4 q = __ldg(r4 + c);
-        float2 u = u2[c];
+    int c = lane;
+    for (; c + 96 < n2; c += 128) {
+        float4 q[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q[j] = ldg_stream(r4 + c + 32 * j);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 u = u2[c + 32 * j];
+            if (u.x != 0.f) { csum_add(ah, q[j].x); csum_add(al, q[j].y); }
+            if (u.y != 0.f) { csum_add(ah, q[j].z); csum_add(al, q[j].w); }
+        }
+    }
+    for (; c < n2; c += 32) {
+        const float4 q = ldg_stream(r4 + c);
+        const float2 u = u2[c];
         if (u.x != 0.f) { csum_add(ah, q.x); csum_add(al, q.y); }
         if (u.y != 0.f) { csum_add(ah, q.z); csum_add(al, q.w); }
     }
@@ -108,13 +141,22 @@ __device__ __forceinline__ void item_rows(const LaneDev& L, int ph, int row0, in
             if (lane == 0) sv[r] = v;
         }
     } else {
+        // warp w takes rows w and w + kWarps together, then w + 2 kWarps, ...
         for (int r = warp; r < rows; r += 2 * kWarps) {
-            const int r2 = r + kWarps < rows ? r + kWarps : r;
-            float va, vb;
-            row_dot2_f32(L.Qoff + (size_t)(row0 + r) * ld, L.Qoff + (size_t)(row0 + r2) * ld, su, ld, lane, va, vb);
-            if (lane == 0) {
-                sv[r] = (double)va;
-                sv[r2] = (double)vb;
+            const float* ra = L.Qoff + (size_t)(row0 + r) * ld;
+            if (r + kWarps < rows) {
+                const float* const rp[2] = {ra, ra + (size_t)kWarps * ld};
+                float v[2];
+                rows_dot_f32<2>(rp, su, ld, lane, v);
+                if (lane == 0) {
+                    sv[r] = (double)v[0];
+                    sv[r + kWarps] = (double)v[1];
+                }
+            } else {
+                const float* const rp[1] = {ra};
+                float v[1];
+                rows_dot_f32<1>(rp, su, ld, lane, v);
+                if (lane == 0) sv[r] = (double)v[0];
             }
         }
     }

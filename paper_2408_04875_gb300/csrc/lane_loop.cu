@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
     __shared__ unsigned long long s_entry, s_base;
     __shared__ int s_last, s_npush;
     __shared__ unsigned s_pay;
+    __shared__ __align__(16) LaneDev sL;   // the popped lane's descriptor
+    static_assert(sizeof(LaneDev) % 8 == 0, "descriptor copied in 8-byte pieces");
     const unsigned long long cap = A.cap, mask = cap - 1;
 
     for (;;) {
@@ -131,8 +133,12 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
             continue;
         }
 
-        // ---- one (lane, row block) item, as in the lock-step kernel
-        const LaneDev& L = A.lanes[lane_id];
+        // ---- one (lane, row block) item, as in the lock-step kernel.  The descriptor never
+        // changes, so it comes through the read-only path (cached in L1 across steps).
+        if (threadIdx.x < (int)(sizeof(LaneDev) / 8))
+            reinterpret_cast<int2*>(&sL)[threadIdx.x] = __ldg(reinterpret_cast<const int2*>(A.lanes + lane_id) + threadIdx.x);
+        __syncthreads();
+        const LaneDev& L = sL;
         const int ph = L.st->phase;
         const int k = L.st->k;
         const int row0 = blk * A.rows_per_item;

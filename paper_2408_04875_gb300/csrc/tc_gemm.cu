@@ -330,6 +330,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
         if (A.flops && rank == 0 && threadIdx.x == 0)   // 2 n flops per (row, lane), single term
             atomicAdd(A.flops, 2ull * (unsigned long long)min(128, I.n - mt * 128) * (unsigned long long)I.n *
                                    (unsigned long long)nreal);
+        if (A.P.bytes && rank == 0 && threadIdx.x == 0) {
+            // algorithmic bytes: the M tile's rows of Q_off once per step (BF16, charged to the
+            // first N tile) and the starts' inputs once (charged to the first M tile)
+            unsigned long long by = 0;
+            if (nt == 0) by += 2ull * (unsigned long long)min(128, I.n - mt * 128) * (unsigned long long)I.n;
+            if (mt == 0) by += 2ull * (two ? 2ull : 1ull) * (unsigned long long)nreal * (unsigned long long)I.n;
+            atomicAdd(A.P.bytes, by);
+        }
         if (!A.raw)
             for (int c = c0 + (int)threadIdx.x; c < c1; c += kTcThreads) {
                 const LaneState* st = A.lanes[I.lane0 + nt * BN + c].st;

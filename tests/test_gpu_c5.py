@@ -1,0 +1,103 @@
+"""The ragged multi-instance batch (512 instances of uneven n and density, half integer Q,
+half Max-Cut) on the tensor-core path, and the restart tuner, through the C ABI.
+
+The method is a heuristic, so a batch this size has no oracle value to match element by
+element; what is unique is the objective of the returned point, which must equal the exact
+f(x) = x'Qx + b'x of the original data (integers, so FP64 evaluates it exactly), and every
+returned x must be binary.  The full-size run checks both on a sample of instances, in the
+launch configuration the benchmark times; the reduced batch checks them on every instance
+and compares batched lanes with the same instances solved one by one.
+"""
+import numpy as np
+import pytest
+
+from paper_2408_04875_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ub():
+    import paper_2408_04875_gb300 as ub
+    ub.lib()
+    return ub
+
+
+def _f(Q, b, x):
+    x = x.astype(np.float64)
+    return float(x @ Q @ x + b @ x)
+
+
+def test_c5_law_reduced_batch_exact_objectives(ub):
+    """32 instances drawn by the ragged-batch law (n in [100, 500]), 8 starts each."""
+    specs = I.c5_specs(32, seed=7, n_lo=100, n_hi=500)
+    data = [I.c5_instance(sp) for sp in specs]
+    Qs = [Q for Q, _ in data]
+    bs = [b for _, b in data]
+    xs, objs, st = ub.solve_batched(Qs, bs, None, restarts=8, precision=ub.BF16X2_TC, max_outer=6)
+    assert st["lanes"] == 32 * 8 and st["restarts"] == 8
+    for (Q, b), x, f in zip(data, xs, objs):
+        assert set(np.unique(x)) <= {0, 1}
+        assert f == _f(Q, b, x)
+
+
+def test_c5_law_batch_equals_single_instances(ub):
+    """Instances of both kinds solved in one ragged tensor-core launch give the bits they give
+    alone (same starts and perturbations passed in; one CTA per tile so that the K order does
+    not depend on the batch)."""
+    specs = I.c5_specs(6, seed=11, n_lo=100, n_hi=400)
+    data = [I.c5_instance(sp) for sp in specs]
+    R = 4
+    mus = [np.diag(np.diag(I.perturbation(Q, sp[3]))) for (Q, _), sp in zip(data, specs)]
+    starts = [I.random_starts(Q.shape[0], R - 1, sp[3]) for (Q, _), sp in zip(data, specs)]
+    kw = dict(restarts=R, precision=ub.BF16X2_TC, tc_cluster=1, max_outer=8)
+    xs, objs, _ = ub.solve_batched([Q for Q, _ in data], [b for _, b in data], mus, starts, **kw)
+    for (Q, b), mu, s0, x, f in zip(data, mus, starts, xs, objs):
+        x1, f1, _ = ub.solve(Q, b, mu=mu, starts=s0, **kw)
+        assert f1 == f and np.array_equal(x1, x)
+
+
+def test_restart_tuner_follows_its_rule(ub):
+    """restarts = 0: every candidate is probed and the largest count whose step time is at
+    most twice the single-start step time is used."""
+    specs = I.c5_specs(8, seed=13, n_lo=200, n_hi=800)
+    data = [I.c5_instance(sp) for sp in specs]
+    _, _, st = ub.solve_batched([Q for Q, _ in data], [b for _, b in data], None, restarts=0,
+                                precision=ub.BF16X2_TC, max_outer=2)
+    probe = st["restart_probe_us"]
+    cands = [1, 8, 32, 64, 128]
+    assert probe[0] > 0
+    expect = max(c for c, t in zip(cands, probe) if 0 < t <= 2 * probe[0])
+    assert st["restarts"] == expect
+    assert st["lanes"] == 8 * expect
+
+
+def test_restart_tuner_rejects_caller_starts(ub):
+    Q, b = I.c5_instance(I.c5_specs(1, seed=1, n_lo=50, n_hi=60)[0])
+    with pytest.raises(ub.UBQPError) as e:
+        ub.solve(Q, b, starts=I.random_starts(Q.shape[0], 3, 1), restarts=0)
+    assert e.value.status == -1
+
+
+def test_c5_full_batch_properties(ub):
+    """The full 512-instance batch at its real sizes (n up to 3000, density up to 1), starts
+    per instance from the tuner, one penalty update: every x binary, and the objective exact on
+    24 sampled instances of both kinds."""
+    import torch
+    specs = I.c5_specs(512)
+    rng = np.random.default_rng(0)
+    sample = set(rng.choice(512, size=24, replace=False).tolist())
+    Qd, bd, host = [], [], {}
+    for i, sp in enumerate(specs):
+        Q, b = I.c5_instance(sp)
+        Qd.append(torch.from_numpy(Q).cuda())
+        bd.append(torch.from_numpy(b).cuda())
+        if i in sample:
+            host[i] = (Q, b)
+    xs, objs, st = ub.solve_batched(Qd, bd, None, restarts=0, precision=ub.BF16X2_TC, max_outer=1)
+    assert st["restarts"] in (1, 8, 32, 64, 128)
+    assert st["lanes"] == 512 * st["restarts"]
+    for i, x in enumerate(xs):
+        assert x.shape == (specs[i][0],) and set(np.unique(x)) <= {0, 1}
+    for i, (Q, b) in host.items():
+        assert objs[i] == _f(Q, b, xs[i]), i
