@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "inner PG iters/s (batch×n) and time-to-oracle-objective vs plain FP32 path"
 UNIT = "lane-var-updates/s"
 GEMV_KERNELS = {1: "phase_a_gemv_kernel", 2: "lane_loop_kernel"}
+# DRAM bytes (read + write) per algorithmic byte of lane_loop_kernel, from the ncu capture of
+# one whole-solve launch of this workload (profiles/lane_loop_kernel_c2.md): 28.19 / 28.60 GB
+LOOP_TRAFFIC_RATIO = 28.19 / 28.60
 SIZES = (250, 500, 1000, 2500)
 SEEDS_PER_SIZE = 10
 WORKLOAD = ("plain PSDP sweep: n in {250,500,1000,2500} x 10 seeded instances, density 0.1, "
@@ -391,7 +394,9 @@ def run_gpu(args):
                        "inner_iters_per_step": stats[-1]["inner_iters"], "outer_steps_per_step": stats[-1]["outer_steps"],
                        "ticks_per_step": stats[-1]["ticks"], "best_objectives_first3": [float(v) for v in objs[:3]]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": (LOOP_TRAFFIC_RATIO * pa_bytes / max(pa_n, 1)
+                                     if stats[-1]["gemv_kernel"] == 2 and pa_n else None),
                          "kernel": GEMV_KERNELS.get(stats[-1]["gemv_kernel"], "?"), "launches": pa_n,
                          "avg_launch_us": pa_ms * 1e3 / max(pa_n, 1),
                          "algorithmic_bytes_per_launch": pa_bytes / max(pa_n, 1), "peak_kind": peak_kind},

@@ -84,6 +84,9 @@ typedef struct {
                              /* opts->restarts == 0)                                    */
     float restart_probe_us[5]; /* restart tuner: step time measured with 1, 8, 32, 64  */
                              /* and 128 starts per instance (0 when not tuned)          */
+    int32_t tc_kernel;       /* tensor-core contraction that ran: 1 split-K clusters,   */
+                             /* 2 persistent (many tiles), 0 none                       */
+    int32_t reserved_;
     int64_t inner_hist[UBQP_HIST_BINS]; /* projected steps per subproblem (Fig. 5)   */
 } ubqp_stats;
 
@@ -256,7 +259,8 @@ int64_t ubqp_profile_timeline(float* ms_out, int64_t* work_out, int64_t cap);
  * its own, D = A (B_hi + B_lo)^T with FP32 accumulation, returned raw.
  *   A n x n, B_hi and B_lo (B_lo may be NULL) R x n, all BF16 bit patterns in HOST memory,
  *   row-major; D_out R x n FP32 host memory (row r = lane r).  cluster: CTAs splitting K
- *   (1..8), 0 = picked by the library.  1 <= n <= 32768, 1 <= R <= 1024.
+ *   (1..8), 0 = picked by the library, -1 = the persistent kernel of many-tile launches
+ *   (no split-K).  1 <= n <= 32768, 1 <= R <= 1024.
  */
 int ubqp_tc_matmul_probe(const uint16_t* A, const uint16_t* B_hi, const uint16_t* B_lo, int64_t n, int64_t R,
                          int32_t cluster, float* D_out);

@@ -42,7 +42,8 @@ class Stats(C.Structure):
                 ("phase_a_ms", C.c_double), ("phase_a_launches", C.c_int64), ("phase_a_bytes", C.c_int64),
                 ("kernel_launches", C.c_int64), ("ms_to_target", C.c_double), ("phase_a_flops", C.c_int64),
                 ("cluster_size", C.c_int32), ("gemv_kernel", C.c_int32), ("restarts", C.c_int32),
-                ("restart_probe_us", C.c_float * 5), ("inner_hist", C.c_int64 * HIST_BINS)]
+                ("restart_probe_us", C.c_float * 5), ("tc_kernel", C.c_int32), ("reserved_", C.c_int32),
+                ("inner_hist", C.c_int64 * HIST_BINS)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("inner_hist", "restart_probe_us")}

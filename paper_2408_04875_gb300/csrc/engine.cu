@@ -163,6 +163,7 @@ struct InstDev {
     size_t o_Q, o_b, o_mu, o_starts;  // staging offsets (when host data)
     bool Q_host, b_host, mu_host, starts_host;
     size_t o_Qoff, o_Qbf, o_Qeval, o_d, o_bp, o_oabs, o_rabs, o_tsum, o_borig, o_qdb, o_gamma;
+    size_t ntact = 0;     // TC: index of this instance's first N tile in the active-lane counters
     size_t o_Uhi, o_Ulo;
     int bn, n_tiles, rows_b;   // tensor-core tiling of this instance's lanes
     int lane0, nl;
@@ -239,6 +240,9 @@ class Solver {
         }
         max_ld_ = max_ld;
         o_scal_ = ar_.reserve(insts.size() * 4 * sizeof(float));
+        o_row0_ = ar_.reserve((insts.size() + 1) * sizeof(int64_t));
+        o_valargs_ = ar_.reserve(insts.size() * sizeof(ValArgs));
+        o_refargs_ = ar_.reserve(insts.size() * sizeof(RefArgs));
         o_valid_ = ar_.reserve(insts.size() * 4 * sizeof(float));
         o_inexact_ = ar_.reserve(insts.size() * sizeof(int));
         o_hist_ = ar_.reserve(UBQP_HIST_BINS * sizeof(int64_t));
@@ -298,7 +302,10 @@ class Solver {
                 I.rows_b = I.n_tiles * I.bn;
                 I.o_Uhi = ar_.reserve((size_t)I.rows_b * I.ld * 2);
                 I.o_Ulo = o_.precision == UBQP_BF16X2_TC ? ar_.reserve((size_t)I.rows_b * I.ld * 2) : 0;
+                I.ntact = ntact_total_;
+                ntact_total_ += (size_t)I.n_tiles;
             }
+            o_ntact_ = ar_.reserve(ntact_total_ * sizeof(int32_t));
             o_tcinst_ = ar_.reserve(inst_.size() * sizeof(TcInst));
             o_tcerr_ = ar_.reserve(sizeof(int32_t));
         }
@@ -379,9 +386,24 @@ class Solver {
                 I.mu = ar_.at<double>(I.o_mu);
             }
         }
-        // ---- validate (Q symmetric, finite)
-        for (size_t t = 0; t < insts.size(); ++t) {
-            UBQP_CK(launch_validate(inst_[t].Q, inst_[t].b, (int)inst_[t].n, ar_.at<float>(o_valid_) + 4 * t, stream_));
+        // ---- validate (Q symmetric, finite): one launch over every row of every instance
+        const int ninst = (int)insts.size();
+        std::vector<int64_t> row0(ninst + 1, 0);
+        for (int t = 0; t < ninst; ++t) row0[t + 1] = row0[t] + inst_[t].n;
+        {
+            std::vector<ValArgs> va(ninst);
+            for (int t = 0; t < ninst; ++t) {
+                va[t].Q = inst_[t].Q;
+                va[t].b = inst_[t].b;
+                va[t].n = (int)inst_[t].n;
+                va[t].pad_ = 0;
+                va[t].out = ar_.at<float>(o_valid_) + 4 * t;
+            }
+            UBQP_CK(cudaMemcpyAsync(ar_.at<int64_t>(o_row0_), row0.data(), row0.size() * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, stream_));
+            UBQP_CK(cudaMemcpyAsync(ar_.at<ValArgs>(o_valargs_), va.data(), va.size() * sizeof(ValArgs),
+                                    cudaMemcpyHostToDevice, stream_));
+            UBQP_CK(launch_validate(ar_.at<ValArgs>(o_valargs_), ar_.at<int64_t>(o_row0_), ninst, row0[ninst], stream_));
             launches_ += 1;
         }
         std::vector<float> val(insts.size() * 4);
@@ -394,11 +416,12 @@ class Solver {
                 return UBQP_ENOTSYM;
             }
         }
-        // ---- reformulate (Sec. 3.5)
+        // ---- reformulate (Sec. 3.5): one launch over every row of every instance
+        std::vector<RefArgs> refs(insts.size());
         for (size_t t = 0; t < insts.size(); ++t) {
             const InstIn& in = insts[t];
             InstDev& I = inst_[t];
-            RefArgs a;
+            RefArgs& a = refs[t];
             memset(&a, 0, sizeof(a));
             a.n = (int)I.n;
             a.ld = I.ld;
@@ -425,14 +448,19 @@ class Solver {
             a.scal = ar_.at<float>(o_scal_) + 4 * t;
             a.inexact = ar_.at<int>(o_inexact_) + t;
             a.no_gamma = in.reformulated ? 1 : 0;  // Q', b' given: no shift
-            UBQP_CK(launch_reformulate(a, stream_));
-            launches_ += (I.ld > I.n) ? 2 : 1;
             if (tc && I.nl > 0 && a.Qbf) {
                 // zero the padded rows of the BF16 matrix (rows n..ld-1)
                 if ((size_t)I.ld > (size_t)I.n)
-                    UBQP_CK(cudaMemsetAsync(a.Qbf + (size_t)I.n * I.ld, 0, (size_t)(I.ld - I.n) * I.ld * 2, stream_));
+                    // rows n..ld-1 all lie in the last M tile: clear its tiles, the reformulation
+                    // then writes rows < n over them
+                    UBQP_CK(cudaMemsetAsync(a.Qbf + qbf_index((size_t)(I.ld - 128), 0, (size_t)I.ld), 0,
+                                            (size_t)128 * I.ld * 2, stream_));
             }
         }
+        UBQP_CK(cudaMemcpyAsync(ar_.at<RefArgs>(o_refargs_), refs.data(), refs.size() * sizeof(RefArgs),
+                                cudaMemcpyHostToDevice, stream_));
+        UBQP_CK(launch_reformulate(ar_.at<RefArgs>(o_refargs_), ar_.at<int64_t>(o_row0_), ninst, row0[ninst], stream_));
+        launches_ += 2;
         std::vector<float> scal(insts.size() * 4);
         UBQP_CK(cudaMemcpyAsync(scal.data(), ar_.at<float>(o_scal_), scal.size() * 4, cudaMemcpyDeviceToHost, stream_));
         std::vector<int> inexact(insts.size());
@@ -491,6 +519,7 @@ class Solver {
             if (tc) {
                 L.u_hi = ar_.at<__nv_bfloat16>(I.o_Uhi) + (size_t)in.restart * I.ld;
                 L.u_lo = I.o_Ulo ? ar_.at<__nv_bfloat16>(I.o_Ulo) + (size_t)in.restart * I.ld : nullptr;
+                L.nt_active = ar_.at<int32_t>(o_ntact_) + I.ntact + in.restart / I.bn;
             }
             L.trace_x = in.trace_len > 0 ? ar_.at<float>(o_trace_x_[l]) : nullptr;
             L.trace_alpha = in.trace_len > 0 ? ar_.at<float>(o_trace_a_[l]) : nullptr;
@@ -522,17 +551,25 @@ class Solver {
                 if (I.o_Ulo) UBQP_CK(cudaMemsetAsync(ar_.at<char>(I.o_Ulo), 0, (size_t)I.rows_b * I.ld * 2, stream_));
             }
             UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_tcerr_), 0, sizeof(int32_t), stream_));
-            // tile table with the TMA descriptors of every instance
+            // tile table with the TMA descriptors of every instance, largest instances first:
+            // CTAs take tiles at a fixed stride, and this order deals every CTA a similar mix of
+            // long and short tiles (the table order does not change any result)
             std::vector<TcInst> ti(inst_.size());
+            ntact_host_.assign(ntact_total_, 0);
+            std::vector<size_t> by_size(inst_.size());
+            for (size_t t = 0; t < inst_.size(); ++t) by_size[t] = t;
+            std::stable_sort(by_size.begin(), by_size.end(),
+                             [&](size_t a, size_t b) { return inst_[a].ld > inst_[b].ld; });
             int cl = 0, kb_min = 1 << 30;
             max_bn_ = 16;
-            for (size_t t = 0; t < inst_.size(); ++t) {
+            for (size_t q = 0; q < inst_.size(); ++q) {
+                const size_t t = by_size[q];
                 InstDev& I = inst_[t];
-                TcInst& h = ti[t];
+                TcInst& h = ti[q];
                 memset(&h, 0, sizeof(h));
                 const void* ub = ar_.at<char>(I.o_Uhi);
                 const void* lb = I.o_Ulo ? (const void*)ar_.at<char>(I.o_Ulo) : ub;
-                if (tc_encode_map(&h.tmA, ar_.at<char>(I.o_Qbf), I.ld, I.ld, 128) != CUDA_SUCCESS ||
+                if (tc_encode_map(&h.tmA, ar_.at<char>(I.o_Qbf), (int64_t)I.ld * I.ld / 64, 64, 128) != CUDA_SUCCESS ||
                     tc_encode_map(&h.tmBhi, ub, I.rows_b, I.ld, I.bn) != CUDA_SUCCESS ||
                     tc_encode_map(&h.tmBlo, lb, I.rows_b, I.ld, I.bn) != CUDA_SUCCESS) {
                     set_error("cuTensorMapEncodeTiled failed for instance %zu", t);
@@ -547,6 +584,8 @@ class Solver {
                 h.bn = I.bn;
                 h.two_terms = I.o_Ulo ? 1 : 0;
                 h.cluster0 = cl;
+                h.nt_active = ar_.at<int32_t>(o_ntact_) + I.ntact;
+                for (int q = 0; q < I.n_tiles; ++q) ntact_host_[I.ntact + q] = std::min(I.bn, I.nl - q * I.bn);
                 cl += h.m_tiles * h.n_tiles;
                 kb_min = std::min(kb_min, I.ld / 64);
                 max_bn_ = std::max(max_bn_, I.bn);
@@ -554,10 +593,17 @@ class Solver {
             tc_tiles_ = cl;
             UBQP_CK(cudaMemcpyAsync(ar_.at<TcInst>(o_tcinst_), ti.data(), ti.size() * sizeof(TcInst),
                                     cudaMemcpyHostToDevice, stream_));
+            UBQP_CK(cudaMemcpyAsync(ar_.at<int32_t>(o_ntact_), ntact_host_.data(), ntact_total_ * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, stream_));
             const bool two = o_.precision == UBQP_BF16X2_TC;
             tc_stages_ = tc_pick_stages(max_bn_, two);
             tc_S_ = o_.tc_cluster > 0 ? o_.tc_cluster
                                       : tc_pick_cluster(tc_tiles_, kb_min, max_bn_, two, tc_stages_, num_sms_);
+            // enough tiles for the whole GPU without splitting K: the persistent kernel, which
+            // overlaps each tile's epilogue with the next tile's contraction
+            const int tcp_stages = tcp_pick_stages(max_bn_, two);
+            tcp_ = tc_S_ == 1 && tcp_stages >= 2 && tc_tiles_ >= num_sms_;
+            if (tcp_) tc_stages_ = tcp_stages;
         }
         LaneInitArgs lia;
         lia.lanes = ar_.at<LaneDev>(o_lanes_);
@@ -602,7 +648,7 @@ class Solver {
             tca.inst = ar_.at<TcInst>(o_tcinst_);
             tca.ninst = (int)inst_.size();
             tca.stages = tc_stages_;
-            tca.tmem_cols = tc_tmem_cols(max_bn_);
+            tca.tmem_cols = tc_tmem_cols(max_bn_, o_.precision == UBQP_BF16X2_TC);
             tca.max_bn = max_bn_;
             tca.two_any = o_.precision == UBQP_BF16X2_TC ? 1 : 0;
             tca.lanes = ar_.at<LaneDev>(o_lanes_);
@@ -610,6 +656,10 @@ class Solver {
             tca.err = ar_.at<int32_t>(o_tcerr_);
             tca.flops = prof ? ar_.at<unsigned long long>(o_flops_) : nullptr;
             tca.P = ta.P;
+            if (tcp_) {
+                tca.tmem_cols = tcp_tmem_cols(o_.precision == UBQP_BF16X2_TC);
+                tcp_grid_ = tcp_grid(tca, tc_tiles_);
+            }
         }
         const bool timeline = o_.profile_kernels >= 2;
         unsigned long long* d_work_ctr = tc_ ? ar_.at<unsigned long long>(o_flops_) : ar_.at<unsigned long long>(o_bytes_);
@@ -643,7 +693,7 @@ class Solver {
                     tt.active_count = last ? d_active : nullptr;
                     e = launch_phase_a_gemv_f32(tt, stream_);
                 } else if (has_a) {
-                    e = tc_launch(tca, tc_tiles_, tc_S_, stream_);
+                    e = tcp_ ? tcp_launch(tca, tc_tiles_, tcp_grid_, stream_) : tc_launch(tca, tc_tiles_, tc_S_, stream_);
                 }
                 if (e != cudaSuccess) return e;
                 if (prof && has_a) e = cudaEventRecord(evA_[2 * t + 1], stream_);
@@ -928,6 +978,7 @@ class Solver {
         UBQP_CK(cudaStreamSynchronize(stream_));
         s->phase_a_flops = (int64_t)fl;
         s->cluster_size = tc_ ? tc_S_ : 0;
+        s->tc_kernel = tc_ ? (tcp_ ? 2 : 1) : 0;
         s->gemv_kernel = tc_ ? 0 : (loop_ ? 2 : 1);
         UBQP_CK(cudaMemcpyAsync(s->inner_hist, ar_.at<int64_t>(o_hist_), sizeof(s->inner_hist), cudaMemcpyDeviceToHost,
                                 stream_));
@@ -1025,6 +1076,10 @@ class Solver {
            o_linit_ = 0, o_items_ = 0, o_bytes_ = 0, o_counters_ = 0, o_tcinst_ = 0, o_tcerr_ = 0, o_ring_ = 0, o_ht_ = 0, o_loopctr_ = 0, o_budget_ = 0,
            o_flops_ = 0, o_queue_ = 0;
     int tc_tiles_ = 0, tc_S_ = 1, tc_stages_ = 2, max_bn_ = 16;
+    bool tcp_ = false;   // tensor-core lanes on the persistent kernel
+    size_t ntact_total_ = 0, o_ntact_ = 0, o_row0_ = 0, o_valargs_ = 0, o_refargs_ = 0;
+    std::vector<int32_t> ntact_host_;   // staged until the copy completes (the stream syncs in run)
+    int tcp_grid_ = 0;
     size_t o_final_lane0_ = 0, o_final_nl_ = 0, o_final_obj_ = 0, o_final_best_ = 0, o_final_xptr_ = 0,
            o_final_xbuf_ = 0;
 };

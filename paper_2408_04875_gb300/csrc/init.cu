@@ -82,10 +82,10 @@ __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v)
 }
 
 // out[0] = max |Q_ij - Q_ji|, out[1] = max |Q_ij| (i != j), out[2] = nonfinite flag, out[3] = max|Q|
-__global__ void validate_kernel(const double* __restrict__ Q, const double* __restrict__ b, int n, float* out)
+__device__ __forceinline__ void validate_row(const double* __restrict__ Q, const double* __restrict__ b, int n,
+                                             float* out, int i)
 {
     __shared__ float sh[8];
-    const int i = blockIdx.x;
     float asym = 0.f, offmax = 0.f, qmax = 0.f, bad = 0.f;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         double q = Q[(size_t)i * n + j];
@@ -111,11 +111,10 @@ __global__ void validate_kernel(const double* __restrict__ Q, const double* __re
 }
 
 // one CTA per row i
-__global__ void reformulate_kernel(RefArgs a)
+__device__ __forceinline__ void reformulate_row(const RefArgs& a, int i)
 {
     __shared__ double shd[8];
     __shared__ float shf[8];
-    const int i = blockIdx.x;
     const int n = a.n, ld = a.ld;
     const double* Qrow = a.Q + (size_t)i * n;
     const double bi = a.b ? a.b[i] : 0.0;
@@ -151,12 +150,12 @@ __global__ void reformulate_kernel(RefArgs a)
         if (j == i) {
             dii = qm + gam;
             if (a.Qoff) a.Qoff[(size_t)i * ld + j] = 0.f;
-            if (a.Qbf) a.Qbf[(size_t)i * ld + j] = __float2bfloat16_rn(0.f);
+            if (a.Qbf) a.Qbf[qbf_index(i, j, ld)] = __float2bfloat16_rn(0.f);
         } else {
             double stored;
             if (a.Qbf) {
                 __nv_bfloat16 h = __float2bfloat16_rn((float)qm);
-                a.Qbf[(size_t)i * ld + j] = h;
+                a.Qbf[qbf_index(i, j, ld)] = h;
                 stored = (double)__bfloat162float(h);
                 if (j < n && stored != qm) atomicOr(a.inexact, 1);
             } else {
@@ -193,10 +192,36 @@ __global__ void reformulate_kernel(RefArgs a)
     }
 }
 
-// padding rows of the per-instance vectors (i in [n, ld)) are zero
-__global__ void zero_tail_kernel(RefArgs a)
+// the instance owning global row g of a batch: row0[t] <= g < row0[t + 1]
+__device__ __forceinline__ int batch_instance(const int64_t* row0, int ninst, int64_t g)
 {
-    for (int i = a.n + blockIdx.x * blockDim.x + threadIdx.x; i < a.ld; i += gridDim.x * blockDim.x) {
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row0[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// every instance of a batch in one launch: one CTA per row of every instance
+__global__ void validate_kernel(const ValArgs* v, const int64_t* row0, int ninst)
+{
+    const int t = batch_instance(row0, ninst, blockIdx.x);
+    const ValArgs& a = v[t];
+    validate_row(a.Q, a.b, a.n, a.out, (int)(blockIdx.x - row0[t]));
+}
+
+__global__ void reformulate_kernel(const RefArgs* args, const int64_t* row0, int ninst)
+{
+    const int t = batch_instance(row0, ninst, blockIdx.x);
+    reformulate_row(args[t], (int)(blockIdx.x - row0[t]));
+}
+
+// padding rows of the per-instance vectors (i in [n, ld)) are zero; one CTA per instance
+__global__ void zero_tail_kernel(const RefArgs* args)
+{
+    const RefArgs& a = args[blockIdx.x];
+    for (int i = a.n + threadIdx.x; i < a.ld; i += blockDim.x) {
         a.d[i] = 1.f;  // keeps divisions finite; never used for i >= n
         a.bprime[i] = 0.f;
         a.tsum[i] = 0.f;
@@ -294,18 +319,18 @@ __global__ void trace_to_f64_kernel(const float* in, double* out, int64_t count)
 }
 
 // ---------------------------------------------------------------------------------
-cudaError_t launch_validate(const double* Q, const double* b, int n, float* out, cudaStream_t s)
+cudaError_t launch_validate(const ValArgs* v, const int64_t* row0, int ninst, int64_t rows, cudaStream_t s)
 {
-    validate_kernel<<<n, 256, 0, s>>>(Q, b, n, out);
+    validate_kernel<<<(unsigned)rows, 256, 0, s>>>(v, row0, ninst);
     return cudaGetLastError();
 }
 
-cudaError_t launch_reformulate(const RefArgs& a, cudaStream_t s)
+cudaError_t launch_reformulate(const RefArgs* args, const int64_t* row0, int ninst, int64_t rows, cudaStream_t s)
 {
-    reformulate_kernel<<<a.n, 256, 0, s>>>(a);
+    reformulate_kernel<<<(unsigned)rows, 256, 0, s>>>(args, row0, ninst);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (a.ld > a.n) zero_tail_kernel<<<1, 256, 0, s>>>(a);
+    zero_tail_kernel<<<ninst, 256, 0, s>>>(args);
     return cudaGetLastError();
 }
 

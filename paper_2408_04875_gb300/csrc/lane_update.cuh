@@ -327,8 +327,10 @@ static __device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, 
     }
 }
 
-// The update of one lane by one CTA of kBThreads threads (phase B).  Called by the
-// stand-alone phase-B kernel and by the last phase-A CTA of a lane in the fused GEMV tick.
+// The update of one lane by one CTA of 32..kBThreads threads (a multiple of 32).  Called by
+// the stand-alone update kernel and by the CTA that completes a GEMV lane's step.  With at
+// most blockDim.x partials every thread merges at most one, so the reduction order (and the
+// result) does not depend on the CTA size.
 static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& P, int32_t* active_count)
 {
     __shared__ LaneState S;
@@ -350,7 +352,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
         Acc a;
         a.zero();
         const int ns = phase_nsum(ph), nm = phase_nmax(ph);
-        for (int b = threadIdx.x; b < L.nblk; b += kBThreads) {
+        for (int b = threadIdx.x; b < L.nblk; b += blockDim.x) {
             const Partial& p = L.part[b];
 #pragma unroll
             for (int t = 0; t < 12; ++t)
@@ -383,7 +385,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
             for (int t = 0; t < 12; ++t) R.s[t] = make_float2(0.f, 0.f);
             for (int t = 0; t < 6; ++t) R.m[t] = 0.f;
             R.f = 0.0;
-            for (int w = 0; w < kBWarps; ++w) {
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
                 for (int t = 0; t < 12; ++t) R.s[t] = csum_merge(R.s[t], sh_s[w][t]);
                 for (int t = 0; t < 6; ++t) R.m[t] = fmaxf(R.m[t], sh_m[w][t]);
                 if (ph == PH_EVAL) R.f += sh_f[w];
@@ -404,7 +406,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
         float4* XP4 = reinterpret_cast<float4*>(vec + (size_t)V_XPREV * ld);
         const float4* G4 = reinterpret_cast<const float4*>(vec + (size_t)V_G * ld);
         float4* U4 = reinterpret_cast<float4*>(vec + (size_t)V_U * ld);
-        for (int q = threadIdx.x; q < (ld >> 2); q += kBThreads) {
+        for (int q = threadIdx.x; q < (ld >> 2); q += blockDim.x) {
             const float4 x = X4[q], g = G4[q];
             XP4[q] = x;
             float4 y;
@@ -428,7 +430,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
             }
         }
     }
-    for (int i = threadIdx.x; i < n && !(act == A_STEP_PABB && usrc == U_X); i += kBThreads) {
+    for (int i = threadIdx.x; i < n && !(act == A_STEP_PABB && usrc == U_X); i += blockDim.x) {
         float x = vec[V_X * ld + i];
         if (act & A_TRACE) L.trace_x[(size_t)D.trace_k * n + i] = x;
         if (act & A_COPY_W_X) {
@@ -509,6 +511,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
     if (threadIdx.x == 0) {
         if ((act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
         S.updates += 1;
+        if (S.phase == PH_DONE && L.nt_active) atomicSub(L.nt_active, 1);   // phase0 != PH_DONE here
         *L.st = S;
         if (S.phase != PH_DONE && active_count) atomicAdd(active_count, 1);
     }

@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <vector>
 #include <cstring>
 
 #include "../../include/ubqp.h"
@@ -129,23 +130,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar)
                  : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v)
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // 16 consecutive FP32 columns of this thread's TMEM lane
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
 {
@@ -158,6 +142,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Accumulator layout.  The hi and lo rows of the inputs sit back to back in shared memory,
+// so one MMA with N = 2 bn covers both terms: columns [0, bn) of its accumulator collect the
+// hi products, [bn, 2 bn) the lo products.  Each MMA instruction costs a similar time
+// whatever its N up to 256 (measured: ~155 cycles for N = 16 and ~170 for N = 128), so fewer,
+// wider instructions are what raises throughput.  The k-steps of a tile are also dealt
+// round-robin to tc_chains_k(bn) accumulators (chain c at column offset c * w, w = 2 bn or bn)
+// so that consecutive MMAs do not all accumulate into one place.  The drain adds, for each
+// column, the hi parts of the chains in ascending order, then the lo parts; both kernels use
+// this layout, so a tile's sums do not depend on which kernel computed it.
+__host__ __device__ constexpr int tc_chains_k(int bn) { return bn <= 32 ? 4 : (bn <= 64 ? 2 : 1); }
+
+// 16 consecutive output columns of this thread's TMEM lane, summed over terms and chains
+__device__ __forceinline__ void tmem_ld16_sum(uint32_t taddr, int bn, bool two, float* v)
+{
+    const int nk = tc_chains_k(bn), w = two ? 2 * bn : bn;
+    tmem_ld16(taddr, v);
+    for (int t = 0; t < (two ? 2 : 1); ++t)
+        for (int c = (t == 0 ? 1 : 0); c < nk; ++c) {
+            float u[16];
+            tmem_ld16(taddr + (uint32_t)(c * w + t * bn), u);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] += u[i];
+        }
 }
 
 // warp-level reduction of one lane's accumulator into its partial record (lane 0 writes)
@@ -183,6 +192,59 @@ __device__ __forceinline__ void warp_reduce_write(Acc& a, int ph, Partial* out, 
 }
 
 }  // namespace
+
+// Per-row epilogue of one lane of an M tile (rows mt*128 + lane + 32 j, j < 4, values vv
+// from the contraction) and its partial record L.part[mt], by one warp.
+__device__ __forceinline__ void tc_lane_epilogue(const TcArgs& A, const TcInst& I, int mt, int r, int ph, int k,
+                                                 const float (&vv)[4], int lane)
+{
+    const LaneDev& L = A.lanes[I.lane0 + r];
+    Acc a;
+    a.zero();
+    if (ph == PH_INNER) {
+        // Alg. 2 gradient for four rows: all operands loaded before any result is stored
+        float* vec = L.vec;
+        const int ld = L.ld;
+        float x[4], dmp[4], ts[4], xp[4], go[4], oa[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = min(mt * 128 + lane + 32 * j, I.n - 1);
+            x[j] = vec[V_X * ld + i];
+            dmp[j] = vec[V_DMP * ld + i];
+            ts[j] = L.tsum[i];
+            xp[j] = vec[V_XPREV * ld + i];
+            go[j] = vec[V_G * ld + i];
+            oa[j] = L.oabs[i];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = mt * 128 + lane + 32 * j;
+            if (i >= I.n) continue;
+            const float g = fmaf(dmp[j], 2.f * x[j] - 1.f, fmaf(2.f, vv[j], ts[j]));
+            if (k >= 1) {
+                const float sj = x[j] - xp[j], yj = g - go[j];
+                csum_add(a.s[0], sj * sj);
+                csum_add(a.s[1], sj * yj);
+                csum_add(a.s[2], yj * yj);
+            } else {
+                a.m[1] = fmaxf(a.m[1], fabsf(dmp[j]));
+                a.m[2] = fmaxf(a.m[2], fabsf(vec[V_BBAR * ld + i]));
+                a.m[3] = fmaxf(a.m[3], oa[j] + fabsf(dmp[j]));
+            }
+            vec[V_G * ld + i] = g;
+            const float viol = (x[j] > 0.f && x[j] < 1.f) ? fabsf(g)
+                               : (x[j] <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
+            a.m[0] = fmaxf(a.m[0], viol);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = mt * 128 + lane + 32 * j;
+            if (i < I.n) row_epilogue(L, ph, k, i, (double)vv[j], a, A.P.tau_z);
+        }
+    }
+    warp_reduce_write(a, ph, L.part + mt, ph == PH_EVAL);
+}
 
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
@@ -216,7 +278,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
         s_fail = 0;
         // a tile whose lanes are all finished is skipped by every CTA of the cluster
         int alive = A.raw ? 1 : 0;
-        if (!A.raw) {
+        if (!A.raw && I.nt_active) {
+            alive = I.nt_active[s_nt] > 0;
+        } else if (!A.raw) {
             const int r0 = s_nt * I.bn, r1 = min(I.R, r0 + I.bn);
             for (int r = r0; r < r1 && !alive; ++r) alive = A.lanes[I.lane0 + r].st->phase != PH_DONE;
         }
@@ -261,7 +325,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
                 unsigned char* st = ring + (size_t)s * stage_bytes;
                 mbar_expect_tx(&full_bar[s], stage_bytes);
                 const int kx = (kb0 + kb) * 64;
-                tma_load_2d(st, &I.tmA, &full_bar[s], kx, mt * 128);
+                tma_load_2d(st, &I.tmA, &full_bar[s], 0, (mt * kb_total + kb0 + kb) * 128);
                 tma_load_2d(st + a_bytes, &I.tmBhi, &full_bar[s], kx, nt * BN);
                 if (two) tma_load_2d(st + a_bytes + b_bytes, &I.tmBlo, &full_bar[s], kx, nt * BN);
             }
@@ -271,8 +335,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
                     mbar_wait(&full_bar[kb % NS], (uint32_t)((kb / NS) & 1));
             }
         } else if (warp == 1 && lane == 0) {
-            // MMA issuer: 4 K-steps of 16 per 64-wide k-block, hi then lo term
-            const uint32_t idesc = idesc_bf16(128, BN);
+            // MMA issuer: 4 K-steps of 16 per 64-wide k-block, both terms in one MMA of N = 2 BN
+            const uint32_t idesc = idesc_bf16(128, two ? 2 * BN : BN);
+            const int NK = tc_chains_k(BN), W = two ? 2 * BN : BN;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % NS;
                 if (!mbar_wait(&full_bar[s], (uint32_t)((kb / NS) & 1))) { s_fail = 1; break; }
@@ -281,9 +346,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
                 const uint32_t sb = sa + a_bytes;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const uint64_t ad = sdesc_sw128(sa + k * 32);
-                    umma_bf16(tmem, ad, sdesc_sw128(sb + k * 32), idesc, (kb > 0 || k > 0) ? 1u : 0u);
-                    if (two) umma_bf16(tmem, ad, sdesc_sw128(sb + b_bytes + k * 32), idesc, 1u);
+                    const int ks = kb * 4 + k, ck = ks % NK;
+                    umma_bf16(tmem + (uint32_t)(ck * W), sdesc_sw128(sa + k * 32), sdesc_sw128(sb + k * 32), idesc,
+                              ks >= NK ? 1u : 0u);
                 }
                 umma_commit(&empty_bar[s]);
             }
@@ -306,7 +371,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
         for (int q = warp >> 2; q < BN / 16; q += 2) {   // 16-column chunks split over the two warpgroups
             float v[16];
             if (have) {
-                tmem_ld16(tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q * 16), v);
+                tmem_ld16_sum(tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(q * 16), BN, two, v);
             } else {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] = 0.f;
@@ -367,53 +432,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
             }
             const int ph = s_ph[c - c0];
             if (ph == PH_DONE) continue;
-            const int k = s_k[c - c0];
-            const LaneDev& L = A.lanes[I.lane0 + r];
-            Acc a;
-            a.zero();
-            if (ph == PH_INNER) {
-                // Alg. 2 gradient for four rows: all operands loaded before any result is stored
-                float* vec = L.vec;
-                const int ld = L.ld;
-                float x[4], dmp[4], ts[4], xp[4], go[4], oa[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int i = min(mt * 128 + lane + 32 * j, I.n - 1);
-                    x[j] = vec[V_X * ld + i];
-                    dmp[j] = vec[V_DMP * ld + i];
-                    ts[j] = L.tsum[i];
-                    xp[j] = vec[V_XPREV * ld + i];
-                    go[j] = vec[V_G * ld + i];
-                    oa[j] = L.oabs[i];
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int i = mt * 128 + lane + 32 * j;
-                    if (i >= I.n) continue;
-                    const float g = fmaf(dmp[j], 2.f * x[j] - 1.f, fmaf(2.f, vv[j], ts[j]));
-                    if (k >= 1) {
-                        const float sj = x[j] - xp[j], yj = g - go[j];
-                        csum_add(a.s[0], sj * sj);
-                        csum_add(a.s[1], sj * yj);
-                        csum_add(a.s[2], yj * yj);
-                    } else {
-                        a.m[1] = fmaxf(a.m[1], fabsf(dmp[j]));
-                        a.m[2] = fmaxf(a.m[2], fabsf(vec[V_BBAR * ld + i]));
-                        a.m[3] = fmaxf(a.m[3], oa[j] + fabsf(dmp[j]));
-                    }
-                    vec[V_G * ld + i] = g;
-                    const float viol = (x[j] > 0.f && x[j] < 1.f) ? fabsf(g)
-                                       : (x[j] <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
-                    a.m[0] = fmaxf(a.m[0], viol);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int i = mt * 128 + lane + 32 * j;
-                    if (i < I.n) row_epilogue(L, ph, k, i, (double)vv[j], a, A.P.tau_z);
-                }
-            }
-            warp_reduce_write(a, ph, L.part + mt, ph == PH_EVAL);
+            tc_lane_epilogue(A, I, mt, r, ph, s_k[c - c0], vv, lane);
         }
     }
     cluster.sync();  // peers' shared memory stays alive until every CTA has read it
@@ -424,6 +443,253 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
             tc_fence_after();
             tmem_dealloc(tmem_base, (uint32_t)A.tmem_cols);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Persistent form for launches with many tiles (the ragged batch): no split-K, one CTA per
+// SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... and overlaps the epilogue of
+// one tile with the contraction of the next.
+//
+// Roles: warp 0 (one thread) keeps the TMA ring full across tile boundaries; warp 1 (one
+// thread) issues the MMAs of each tile into one of two TMEM accumulators (columns
+// buf * max_bn), waiting until the epilogue has drained that buffer; warps 4..7 drain the
+// finished accumulator into shared memory (each warp reaches TMEM lanes 32 (w mod 4) ..)
+// and release it; warps 2..7 then run the per-row epilogue of the tile's lanes.  All roles
+// walk the same tile list and skip the same finished tiles (lane states do not change
+// during the launch).  Waits are bounded; after a failure every role stops working but the
+// epilogue warps keep their named barriers matched, and the CTA lets issued copies and
+// MMAs complete before it frees shared memory and TMEM.
+struct TcTile {
+    int inst, mt, nt, kb;
+    bool alive;
+};
+
+__device__ __forceinline__ TcTile tcp_tile(const TcArgs& A, int t)
+{
+    int lo = 0, hi = A.ninst - 1;   // last instance whose first tile index <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (A.inst[mid].cluster0 <= t) lo = mid; else hi = mid - 1;
+    }
+    const TcInst& I = A.inst[lo];
+    const int local = t - I.cluster0;
+    TcTile T;
+    T.inst = lo;
+    T.mt = local / I.n_tiles;
+    T.nt = local % I.n_tiles;
+    T.kb = I.ld / 64;
+    T.alive = A.raw != nullptr;
+    if (!T.alive && I.nt_active) {
+        T.alive = I.nt_active[T.nt] > 0;
+    } else if (!T.alive) {
+        const int r0 = T.nt * I.bn, r1 = min(I.R, r0 + I.bn);
+        for (int r = r0; r < r1 && !T.alive; ++r) T.alive = A.lanes[I.lane0 + r].st->phase != PH_DONE;
+    }
+    return T;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void epi_bar_sync() { asm volatile("bar.sync 1, 192;" ::: "memory"); }
+
+__device__ __forceinline__ int vload(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+__global__ void __launch_bounds__(kTcThreads, 1) phase_a_tcp_kernel(TcArgs A, int ntiles)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* ring = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int NS = A.stages;
+    const uint32_t stage_max = 128u * 128u + (uint32_t)A.max_bn * 128u * (A.two_any ? 2u : 1u);
+    float* P = reinterpret_cast<float*>(ring + (size_t)NS * stage_max);
+    __shared__ uint64_t full_bar[kTcpMaxStages], empty_bar[kTcpMaxStages], accf_bar[2], acce_bar[2], fin_bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    __shared__ long long s_issued;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t col_stride = A.two_any ? 256u : 128u;   // one accumulator buffer: terms x chains x bn <= this
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf_bar[b], 1);
+            mbar_init(&acce_bar[b], 4);   // one arrival per draining warp
+        }
+        mbar_init(&fin_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+        s_issued = 0;
+    }
+    if (warp == 1) tmem_alloc(&tmem_base, (uint32_t)A.tmem_cols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {   // ---- TMA producer
+            long long pos = 0;
+            for (int t = blockIdx.x; t < ntiles && !vload(&s_fail); t += gridDim.x) {
+                const TcTile T = tcp_tile(A, t);
+                if (!T.alive) continue;
+                const TcInst& I = A.inst[T.inst];
+                const bool two = I.two_terms != 0;
+                const uint32_t a_bytes = 128u * 128u, b_bytes = (uint32_t)I.bn * 128u;
+                const uint32_t sb = a_bytes + b_bytes * (two ? 2u : 1u);
+                for (int kb = 0; kb < T.kb; ++kb, ++pos) {
+                    const int s = (int)(pos % NS);
+                    const long long use = pos / NS;
+                    if (use > 0 && !mbar_wait(&empty_bar[s], (uint32_t)((use - 1) & 1))) {
+                        s_fail = 1;
+                        break;
+                    }
+                    unsigned char* st = ring + (size_t)s * stage_max;
+                    mbar_expect_tx(&full_bar[s], sb);
+                    tma_load_2d(st, &I.tmA, &full_bar[s], 0, (T.mt * T.kb + kb) * 128);
+                    tma_load_2d(st + a_bytes, &I.tmBhi, &full_bar[s], kb * 64, T.nt * I.bn);
+                    if (two) tma_load_2d(st + a_bytes + b_bytes, &I.tmBlo, &full_bar[s], kb * 64, T.nt * I.bn);
+                    s_issued = pos + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ---- MMA issuer
+            long long pos = 0;
+            int j = 0;
+            for (int t = blockIdx.x; t < ntiles && !vload(&s_fail); t += gridDim.x) {
+                const TcTile T = tcp_tile(A, t);
+                if (!T.alive) continue;
+                const TcInst& I = A.inst[T.inst];
+                const bool two = I.two_terms != 0;
+                const uint32_t a_bytes = 128u * 128u;
+                const int buf = j & 1, use_b = j >> 1;
+                if (use_b > 0 && !mbar_wait(&acce_bar[buf], (uint32_t)((use_b - 1) & 1))) {
+                    s_fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)buf * col_stride;
+                const uint32_t idesc = idesc_bf16(128, two ? 2 * I.bn : I.bn);
+                const int NK = tc_chains_k(I.bn), W = two ? 2 * I.bn : I.bn;
+                bool ok = true;
+                for (int kb = 0; kb < T.kb; ++kb, ++pos) {
+                    const int s = (int)(pos % NS);
+                    if (!mbar_wait(&full_bar[s], (uint32_t)((pos / NS) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(ring + (size_t)s * stage_max);
+                    const uint32_t sbh = sa + a_bytes;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int ks = kb * 4 + k, ck = ks % NK;
+                        umma_bf16(d + (uint32_t)(ck * W), sdesc_sw128(sa + k * 32), sdesc_sw128(sbh + k * 32), idesc,
+                                  ks >= NK ? 1u : 0u);
+                    }
+                    umma_commit(&empty_bar[s]);
+                }
+                if (!ok) {
+                    s_fail = 1;
+                    break;
+                }
+                umma_commit(&accf_bar[buf]);
+                ++j;
+            }
+            // every MMA issued has completed before TMEM is released
+            if (pos > 0) {
+                umma_commit(&fin_bar);
+                mbar_wait(&fin_bar, 0u);
+            }
+        }
+    } else {
+        // ---- warps 2..7: epilogue; warps 4..7 first drain TMEM into P[col][row]
+        const bool drain = warp >= 4;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const TcTile T = tcp_tile(A, t);
+            if (!T.alive) continue;
+            const TcInst& I = A.inst[T.inst];
+            const int buf = j & 1, use_b = j >> 1;
+            if (drain) {
+                int ok = 0;
+                if (lane == 0) ok = !vload(&s_fail) && mbar_wait(&accf_bar[buf], (uint32_t)(use_b & 1));
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok && lane == 0) s_fail = 1;
+                tc_fence_after();
+                const int row = (warp & 3) * 32 + lane;
+                for (int q = 0; q < I.bn / 16; ++q) {
+                    float v[16];
+                    if (ok) {
+                        tmem_ld16_sum(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)buf * col_stride +
+                                          (uint32_t)(q * 16),
+                                      I.bn, I.two_terms != 0, v);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) P[(q * 16 + i) * 128 + row] = v[i];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0 && ok) mbar_arrive(&acce_bar[buf]);
+            }
+            epi_bar_sync();   // P holds this tile's products
+            if (!vload(&s_fail)) {
+                const int nreal = min(I.bn, I.R - T.nt * I.bn);
+                if (warp == 2 && lane == 0) {
+                    const unsigned long long rows = (unsigned long long)min(128, I.n - T.mt * 128);
+                    if (A.flops) atomicAdd(A.flops, 2ull * rows * (unsigned long long)I.n * (unsigned long long)nreal);
+                    if (A.P.bytes) {
+                        unsigned long long by = 0;
+                        if (T.nt == 0) by += 2ull * rows * (unsigned long long)I.n;
+                        if (T.mt == 0)
+                            by += 2ull * (I.two_terms ? 2ull : 1ull) * (unsigned long long)nreal * (unsigned long long)I.n;
+                        atomicAdd(A.P.bytes, by);
+                    }
+                }
+                for (int c = warp - 2; c < nreal; c += 6) {
+                    const int r = T.nt * I.bn + c;
+                    float vv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) vv[q] = P[c * 128 + lane + 32 * q];
+                    if (A.raw) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int i = T.mt * 128 + lane + 32 * q;
+                            if (i < I.n) A.raw[(size_t)r * I.ld + i] = vv[q];
+                        }
+                        continue;
+                    }
+                    const LaneState* st = A.lanes[I.lane0 + r].st;
+                    const int ph = st->phase;
+                    if (ph == PH_DONE) continue;
+                    tc_lane_epilogue(A, I, T.mt, r, ph, st->k, vv, lane);
+                }
+            }
+            epi_bar_sync();   // P may be overwritten
+            ++j;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_fail) {
+        if (A.err) atomicExch(A.err, 1);
+        // copies already issued land before the ring's shared memory goes away
+        const long long iss = s_issued;
+        for (long long q = (iss > NS ? iss - NS : 0); q < iss; ++q)
+            mbar_wait(&full_bar[q % NS], (uint32_t)((q / NS) & 1));
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, (uint32_t)A.tmem_cols);
     }
 }
 
@@ -449,6 +715,51 @@ int tc_pick_stages(int bn, bool two)
     if (s > kTcMaxStages) s = kTcMaxStages;
     if (s < 2) s = 2;
     return s;
+}
+
+// persistent kernel: ring of `stages` slots of the largest stage, then P (max_bn x 128 FP32)
+size_t tcp_smem_bytes(int bn, bool two, int stages)
+{
+    const size_t stage = 128 * 128 + (size_t)bn * 128 * (two ? 2 : 1);
+    return stage * stages + (size_t)bn * 128 * 4 + 1024;
+}
+
+int tcp_pick_stages(int bn, bool two)
+{
+    const size_t stage = 128 * 128 + (size_t)bn * 128 * (two ? 2 : 1);
+    const size_t room = 210 * 1024 - (size_t)bn * 128 * 4 - 1024;
+    int s = (int)(room / stage);
+    if (s > kTcpMaxStages) s = kTcpMaxStages;
+    return s;   // < 2: the persistent kernel does not fit this tile width
+}
+
+// two accumulator buffers of terms x chains x bn <= 128 per term columns each
+int tcp_tmem_cols(bool two) { return two ? 512 : 256; }
+
+// one CTA per SM (as many as fit), never more than the tiles
+int tcp_grid(const TcArgs& a, int ntiles)
+{
+    const size_t smem = tcp_smem_bytes(a.max_bn, a.two_any != 0, a.stages);
+    int dev = 0, sms = 148, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(phase_a_tcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, phase_a_tcp_kernel, kTcThreads, smem) != cudaSuccess ||
+        per < 1) {
+        cudaGetLastError();
+        per = 1;
+    }
+    const int g = sms * per;
+    return ntiles < g ? ntiles : g;
+}
+
+cudaError_t tcp_launch(const TcArgs& a, int ntiles, int grid, cudaStream_t st)
+{
+    const size_t smem = tcp_smem_bytes(a.max_bn, a.two_any != 0, a.stages);
+    cudaError_t e = cudaFuncSetAttribute(phase_a_tcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    phase_a_tcp_kernel<<<grid, kTcThreads, smem, st>>>(a, ntiles);
+    return cudaGetLastError();
 }
 
 cudaError_t tc_launch(const TcArgs& a, int total_clusters, int S, cudaStream_t st)
@@ -495,7 +806,7 @@ int tc_max_active_clusters(int bn, bool two, int stages, int S)
     return n;
 }
 
-int tc_tmem_cols(int bn) { return pow2_at_least(bn); }
+int tc_tmem_cols(int bn, bool two) { return pow2_at_least((two ? 2 : 1) * tc_chains_k(bn) * bn); }
 
 int tc_pick_cluster(int tiles, int kb_min, int bn, bool two, int stages, int num_sms)
 {
@@ -548,7 +859,7 @@ using namespace ubqp;
 extern "C" int ubqp_tc_matmul_probe(const uint16_t* A, const uint16_t* Bhi, const uint16_t* Blo, int64_t n,
                                     int64_t R, int32_t cluster, float* D_out)
 {
-    if (!A || !Bhi || !D_out || n < 1 || n > 32768 || R < 1 || R > 1024 || cluster < 0 || cluster > 8)
+    if (!A || !Bhi || !D_out || n < 1 || n > 32768 || R < 1 || R > 1024 || cluster < -1 || cluster > 8)
         return UBQP_EINVAL;
     const int ld = (int)((n + 127) / 128 * 128);
     const int rpad = (int)((R + 15) / 16 * 16);
@@ -570,8 +881,10 @@ extern "C" int ubqp_tc_matmul_probe(const uint16_t* A, const uint16_t* Bhi, cons
     int rc = UBQP_OK;
     do {
         if (cudaMemset(buf, 0, off_err + 256) != cudaSuccess) { rc = UBQP_ECUDA; break; }
-        if (cudaMemcpy2D(buf, (size_t)ld * 2, A, (size_t)n * 2, (size_t)n * 2, (size_t)n, cudaMemcpyHostToDevice) !=
-                cudaSuccess ||
+        std::vector<uint16_t> At((size_t)ld * ld, 0);   // A in the tiled layout of the solver
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = 0; j < n; ++j) At[qbf_index((size_t)i, (size_t)j, (size_t)ld)] = A[i * n + j];
+        if (cudaMemcpy(buf, At.data(), At.size() * 2, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy2D(buf + off_bhi, (size_t)ld * 2, Bhi, (size_t)n * 2, (size_t)n * 2, (size_t)R,
                          cudaMemcpyHostToDevice) != cudaSuccess ||
             (two && cudaMemcpy2D(buf + off_blo, (size_t)ld * 2, Blo, (size_t)n * 2, (size_t)n * 2, (size_t)R,
@@ -581,7 +894,7 @@ extern "C" int ubqp_tc_matmul_probe(const uint16_t* A, const uint16_t* Bhi, cons
         }
         TcInst h;
         memset(&h, 0, sizeof(h));
-        if (tc_encode_map(&h.tmA, buf, ld, ld, 128) != CUDA_SUCCESS ||
+        if (tc_encode_map(&h.tmA, buf, (int64_t)ld * ld / 64, 64, 128) != CUDA_SUCCESS ||
             tc_encode_map(&h.tmBhi, buf + off_bhi, rows_b, ld, bn) != CUDA_SUCCESS ||
             tc_encode_map(&h.tmBlo, buf + off_blo, rows_b, ld, bn) != CUDA_SUCCESS) {
             rc = UBQP_ECUDA;
@@ -601,15 +914,23 @@ extern "C" int ubqp_tc_matmul_probe(const uint16_t* A, const uint16_t* Bhi, cons
         memset(&a, 0, sizeof(a));
         a.inst = reinterpret_cast<const TcInst*>(buf + off_inst);
         a.ninst = 1;
-        a.stages = tc_pick_stages(bn, two);
-        a.tmem_cols = tc_tmem_cols(bn);
+        const bool persistent = cluster == -1;
+        if (persistent && tcp_pick_stages(bn, two) < 2) { rc = UBQP_ENOTSUP; break; }
+        a.stages = persistent ? tcp_pick_stages(bn, two) : tc_pick_stages(bn, two);
+        a.tmem_cols = persistent ? tcp_tmem_cols(two) : tc_tmem_cols(bn, two);
         a.max_bn = bn;
         a.two_any = two ? 1 : 0;
         a.raw = reinterpret_cast<float*>(buf + off_d);
         a.err = reinterpret_cast<int32_t*>(buf + off_err);
         const int tiles = h.m_tiles * h.n_tiles;
-        const int S = cluster > 0 ? cluster : tc_pick_cluster(tiles, ld / 64, bn, two, a.stages, nsm);
-        if (tc_launch(a, tiles, S, nullptr) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaError_t le;
+        if (persistent) {
+            le = tcp_launch(a, tiles, tcp_grid(a, tiles), nullptr);
+        } else {
+            const int S = cluster > 0 ? cluster : tc_pick_cluster(tiles, ld / 64, bn, two, a.stages, nsm);
+            le = tc_launch(a, tiles, S, nullptr);
+        }
+        if (le != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
             rc = UBQP_ECUDA;
             break;
         }

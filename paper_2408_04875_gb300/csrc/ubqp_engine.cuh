@@ -5,6 +5,14 @@
 
 namespace ubqp {
 
+// Layout of the BF16 matrix of the tensor-core path: tiles of 128 rows x 64 columns (one
+// k-block of one M tile), stored contiguously in the order [M tile][k-block], rows of 64
+// entries inside a tile.  One TMA box is then one contiguous 16 KB run of memory.
+__host__ __device__ __forceinline__ size_t qbf_index(size_t i, size_t j, size_t ld)
+{
+    return (((i >> 7) * (ld >> 6) + (j >> 6)) * 128 + (i & 127)) * 64 + (j & 63);
+}
+
 struct RefArgs {
     int32_t n, ld, inst, diag_only_mu;
     int32_t no_gamma;       // Q, b are already Q', b' (test entries): gamma = 0
@@ -16,12 +24,21 @@ struct RefArgs {
     double margin;
     uint64_t seed;
     float* Qoff;            // GEMV: n x ld FP32 (or null)
-    __nv_bfloat16* Qbf;     // TC: ld x ld BF16 (or null)
+    __nv_bfloat16* Qbf;     // TC: ld x ld BF16 in the tiled layout of qbf_index (or null)
     float2* Qeval;          // GEMV: n x ld original as (hi, lo) FP32 pairs (or null)
     float *d, *bprime, *oabs, *rabs, *tsum;   // tsum = d + b' formed in FP64
     double *borig, *qdb, *gamma;
     float* scal;            // [0] max_{i!=j} |Q'_ij| stored, [1] max rabs
     int* inexact;           // TC: set when BF16 changed an off-diagonal entry
+};
+
+// validation of one instance: out[0] = max |Q_ij - Q_ji|, out[1] = max off-diagonal |Q_ij|,
+// out[2] = non-finite flag, out[3] = max |Q_ij|
+struct ValArgs {
+    const double* Q;
+    const double* b;
+    float* out;
+    int32_t n, pad_;
 };
 
 struct LaneInit {
@@ -47,8 +64,9 @@ struct FinalArgs {
     uint8_t* const* x_out;  // device pointers, one per instance
 };
 
-cudaError_t launch_validate(const double* Q, const double* b, int n, float* out, cudaStream_t s);
-cudaError_t launch_reformulate(const RefArgs& a, cudaStream_t s);
+// one launch for every instance of a batch; row0[t] = first global row of instance t
+cudaError_t launch_validate(const ValArgs* v, const int64_t* row0, int ninst, int64_t rows, cudaStream_t s);
+cudaError_t launch_reformulate(const RefArgs* args, const int64_t* row0, int ninst, int64_t rows, cudaStream_t s);
 cudaError_t launch_lane_init(const LaneInitArgs& a, int nlanes, cudaStream_t s);
 cudaError_t launch_finalize(const FinalArgs& a, int ninst, cudaStream_t s);
 cudaError_t launch_lane_vec_to_f64(const LaneDev* lanes, int lane, int v, int n, double* out, cudaStream_t s);

@@ -128,6 +128,8 @@ struct LaneDev {
     void* gg;
     int32_t gld;
     int32_t pad_;
+    int32_t* nt_active;    // TC lanes: unfinished lanes of this lane's N tile (decremented
+                           // by the update that finishes the lane), else null
 };
 
 // solver constants (kernel parameter)

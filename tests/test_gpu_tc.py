@@ -33,7 +33,10 @@ def _probe(A, Bhi, Blo, cluster=0):
 
 @pytest.mark.parametrize("n,R,cluster,two", [
     (128, 16, 1, True), (200, 37, 0, True), (1000, 64, 2, True), (1000, 256, 0, True),
-    (2500, 256, 0, True), (640, 300, 0, True), (384, 48, 3, False), (2560, 256, 4, True)])
+    (2500, 256, 0, True), (640, 300, 0, True), (384, 48, 3, False), (2560, 256, 4, True),
+    # cluster -1: the persistent kernel (tiles strided over CTAs, two TMEM accumulators)
+    (128, 16, -1, True), (1000, 64, -1, True), (3000, 8, -1, True), (640, 300, -1, True),
+    (2500, 256, -1, True), (384, 48, -1, False), (40000 // 13, 1, -1, True)])
 def test_tc_contraction_matches_exact_product(n, R, cluster, two):
     rng = np.random.default_rng(n + R)
     A = rng.integers(-100, 101, (n, n)).astype(np.float32)
