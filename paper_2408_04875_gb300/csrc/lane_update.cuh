@@ -406,8 +406,23 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
         float4* XP4 = reinterpret_cast<float4*>(vec + (size_t)V_XPREV * ld);
         const float4* G4 = reinterpret_cast<const float4*>(vec + (size_t)V_G * ld);
         float4* U4 = reinterpret_cast<float4*>(vec + (size_t)V_U * ld);
-        for (int q = threadIdx.x; q < (ld >> 2); q += blockDim.x) {
-            const float4 x = X4[q], g = G4[q];
+        // two groups per thread per pass, both loaded before either is stored
+        const int n4 = ld >> 2, nt = blockDim.x;
+        for (int q0 = threadIdx.x; q0 < n4; q0 += 2 * nt) {
+            float4 xs[2], gs[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = q0 + h * nt;
+                if (q < n4) {
+                    xs[h] = X4[q];
+                    gs[h] = G4[q];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+            const int q = q0 + h * nt;
+            if (q >= n4) break;
+            const float4 x = xs[h], g = gs[h];
             XP4[q] = x;
             float4 y;
             y.x = fminf(fmaxf(fmaf(-al, g.x, x.x), 0.f), 1.f);
@@ -427,6 +442,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
                 }
             } else {
                 U4[q] = y;
+            }
             }
         }
     }

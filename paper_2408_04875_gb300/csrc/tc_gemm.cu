@@ -194,54 +194,81 @@ __device__ __forceinline__ void warp_reduce_write(Acc& a, int ph, Partial* out, 
 }  // namespace
 
 // Per-row epilogue of one lane of an M tile (rows mt*128 + lane + 32 j, j < 4, values vv
-// from the contraction) and its partial record L.part[mt], by one warp.
-__device__ __forceinline__ void tc_lane_epilogue(const TcArgs& A, const TcInst& I, int mt, int r, int ph, int k,
-                                                 const float (&vv)[4], int lane)
+// from the contraction) and its partial record L.part[mt], by one warp.  The gradient step
+// (the common case) is split into loading its operands and finishing, so that the lane
+// loops can load the next lane's operands while they finish the current one.
+struct InnerOps {
+    float x[4], dmp[4], ts[4], xp[4], go[4], oa[4];
+};
+
+__device__ __forceinline__ void tc_inner_load(const LaneDev& L, int n, int mt, int lane, InnerOps& o)
 {
-    const LaneDev& L = A.lanes[I.lane0 + r];
+    const float* vec = L.vec;
+    const int ld = L.ld;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = min(mt * 128 + lane + 32 * j, n - 1);
+        o.x[j] = vec[V_X * ld + i];
+        o.dmp[j] = vec[V_DMP * ld + i];
+        o.ts[j] = L.tsum[i];
+        o.xp[j] = vec[V_XPREV * ld + i];
+        o.go[j] = vec[V_G * ld + i];
+        o.oa[j] = L.oabs[i];
+    }
+}
+
+// Alg. 2 gradient for four rows from operands loaded beforehand
+__device__ __forceinline__ void tc_inner_finish(const LaneDev& L, int n, int mt, int k, const float (&vv)[4],
+                                                int lane, const InnerOps& o)
+{
+    float* vec = L.vec;
+    const int ld = L.ld;
     Acc a;
     a.zero();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = mt * 128 + lane + 32 * j;
+        if (i >= n) continue;
+        const float g = fmaf(o.dmp[j], 2.f * o.x[j] - 1.f, fmaf(2.f, vv[j], o.ts[j]));
+        if (k >= 1) {
+            const float sj = o.x[j] - o.xp[j], yj = g - o.go[j];
+            csum_add(a.s[0], sj * sj);
+            csum_add(a.s[1], sj * yj);
+            csum_add(a.s[2], yj * yj);
+        } else {
+            a.m[1] = fmaxf(a.m[1], fabsf(o.dmp[j]));
+            a.m[2] = fmaxf(a.m[2], fabsf(vec[V_BBAR * ld + i]));
+            a.m[3] = fmaxf(a.m[3], o.oa[j] + fabsf(o.dmp[j]));
+        }
+        vec[V_G * ld + i] = g;
+        const float viol = (o.x[j] > 0.f && o.x[j] < 1.f) ? fabsf(g)
+                           : (o.x[j] <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
+        a.m[0] = fmaxf(a.m[0], viol);
+    }
+    warp_reduce_write(a, PH_INNER, L.part + mt, false);
+}
+
+// any phase; `pre` holds the gradient operands when the caller already loaded them
+__device__ __forceinline__ void tc_lane_epilogue(const TcArgs& A, const TcInst& I, int mt, int r, int ph, int k,
+                                                 const float (&vv)[4], int lane, const InnerOps* pre)
+{
+    const LaneDev& L = A.lanes[I.lane0 + r];
     if (ph == PH_INNER) {
-        // Alg. 2 gradient for four rows: all operands loaded before any result is stored
-        float* vec = L.vec;
-        const int ld = L.ld;
-        float x[4], dmp[4], ts[4], xp[4], go[4], oa[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = min(mt * 128 + lane + 32 * j, I.n - 1);
-            x[j] = vec[V_X * ld + i];
-            dmp[j] = vec[V_DMP * ld + i];
-            ts[j] = L.tsum[i];
-            xp[j] = vec[V_XPREV * ld + i];
-            go[j] = vec[V_G * ld + i];
-            oa[j] = L.oabs[i];
+        if (pre) {
+            tc_inner_finish(L, I.n, mt, k, vv, lane, *pre);
+        } else {
+            InnerOps o;
+            tc_inner_load(L, I.n, mt, lane, o);
+            tc_inner_finish(L, I.n, mt, k, vv, lane, o);
         }
+        return;
+    }
+    Acc a;
+    a.zero();
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = mt * 128 + lane + 32 * j;
-            if (i >= I.n) continue;
-            const float g = fmaf(dmp[j], 2.f * x[j] - 1.f, fmaf(2.f, vv[j], ts[j]));
-            if (k >= 1) {
-                const float sj = x[j] - xp[j], yj = g - go[j];
-                csum_add(a.s[0], sj * sj);
-                csum_add(a.s[1], sj * yj);
-                csum_add(a.s[2], yj * yj);
-            } else {
-                a.m[1] = fmaxf(a.m[1], fabsf(dmp[j]));
-                a.m[2] = fmaxf(a.m[2], fabsf(vec[V_BBAR * ld + i]));
-                a.m[3] = fmaxf(a.m[3], oa[j] + fabsf(dmp[j]));
-            }
-            vec[V_G * ld + i] = g;
-            const float viol = (x[j] > 0.f && x[j] < 1.f) ? fabsf(g)
-                               : (x[j] <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
-            a.m[0] = fmaxf(a.m[0], viol);
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = mt * 128 + lane + 32 * j;
-            if (i < I.n) row_epilogue(L, ph, k, i, (double)vv[j], a, A.P.tau_z);
-        }
+    for (int j = 0; j < 4; ++j) {
+        const int i = mt * 128 + lane + 32 * j;
+        if (i < I.n) row_epilogue(L, ph, k, i, (double)vv[j], a, A.P.tau_z);
     }
     warp_reduce_write(a, ph, L.part + mt, ph == PH_EVAL);
 }
@@ -412,8 +439,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
         __syncthreads();
         float* peers[8];
         for (int q = 0; q < S; ++q) peers[q] = cluster.map_shared_rank(P, q);
+        // lanes c0 + warp, + 8, ...: the next lane's gradient operands load while this one finishes
+        InnerOps cur, nxt;
+        bool cur_ok = false;
+        if (!A.raw && c0 + warp < c1 && s_ph[c0 + warp - c0] == PH_INNER) {
+            tc_inner_load(A.lanes[I.lane0 + nt * BN + c0 + warp], I.n, mt, lane, cur);
+            cur_ok = true;
+        }
         for (int c = c0 + warp; c < c1; c += kTcThreads / 32) {
             const int r = nt * BN + c;  // restart index within the instance
+            const int cn = c + kTcThreads / 32;
+            bool nxt_ok = false;
+            if (!A.raw && cn < c1 && s_ph[cn - c0] == PH_INNER) {
+                tc_inner_load(A.lanes[I.lane0 + nt * BN + cn], I.n, mt, lane, nxt);
+                nxt_ok = true;
+            }
             float vv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -428,11 +468,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
                     const int i = mt * 128 + lane + 32 * j;
                     if (i < I.n) A.raw[(size_t)r * I.ld + i] = vv[j];
                 }
-                continue;
+            } else {
+                const int ph = s_ph[c - c0];
+                if (ph != PH_DONE) tc_lane_epilogue(A, I, mt, r, ph, s_k[c - c0], vv, lane, cur_ok ? &cur : nullptr);
             }
-            const int ph = s_ph[c - c0];
-            if (ph == PH_DONE) continue;
-            tc_lane_epilogue(A, I, mt, r, ph, s_k[c - c0], vv, lane);
+            cur = nxt;
+            cur_ok = nxt_ok;
         }
     }
     cluster.sync();  // peers' shared memory stays alive until every CTA has read it
@@ -655,8 +696,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tcp_kernel(TcArgs A, in
                         atomicAdd(A.P.bytes, by);
                     }
                 }
+                // lanes warp - 2, + 6, ...: the next lane's gradient operands load while this one finishes
+                InnerOps cur, nxt;
+                int cur_ph = PH_DONE, cur_k = 0;
+                auto lane_at = [&](int c, InnerOps& o, int& ph, int& k) {
+                    ph = PH_DONE;
+                    if (A.raw || c >= nreal) return;
+                    const LaneState* st = A.lanes[I.lane0 + T.nt * I.bn + c].st;
+                    ph = st->phase;
+                    k = st->k;
+                    if (ph == PH_INNER) tc_inner_load(A.lanes[I.lane0 + T.nt * I.bn + c], I.n, T.mt, lane, o);
+                };
+                lane_at(warp - 2, cur, cur_ph, cur_k);
                 for (int c = warp - 2; c < nreal; c += 6) {
                     const int r = T.nt * I.bn + c;
+                    int nxt_ph, nxt_k = 0;
+                    lane_at(c + 6, nxt, nxt_ph, nxt_k);
                     float vv[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) vv[q] = P[c * 128 + lane + 32 * q];
@@ -666,12 +721,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tcp_kernel(TcArgs A, in
                             const int i = T.mt * 128 + lane + 32 * q;
                             if (i < I.n) A.raw[(size_t)r * I.ld + i] = vv[q];
                         }
-                        continue;
+                    } else if (cur_ph != PH_DONE) {
+                        tc_lane_epilogue(A, I, T.mt, r, cur_ph, cur_k, vv, lane, cur_ph == PH_INNER ? &cur : nullptr);
                     }
-                    const LaneState* st = A.lanes[I.lane0 + r].st;
-                    const int ph = st->phase;
-                    if (ph == PH_DONE) continue;
-                    tc_lane_epilogue(A, I, T.mt, r, ph, st->k, vv, lane);
+                    cur = nxt;
+                    cur_ph = nxt_ph;
+                    cur_k = nxt_k;
                 }
             }
             epi_bar_sync();   // P may be overwritten
