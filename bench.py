@@ -338,7 +338,7 @@ def run_gpu(args):
     Md = [torch.from_numpy(m).cuda() for m in mus]
     torch.cuda.synchronize()
     kw = dict(profile_kernels=0 if args.no_profile else 1, gemv_kernel=args.gemv_kernel,
-              lane_budget=args.lane_budget)
+              lane_budget=args.lane_budget, rows_per_item=args.rows_per_item)
     if args.max_outer is not None:
         kw["max_outer"] = args.max_outer
     for _ in range(args.warmup):
@@ -434,6 +434,8 @@ def main():
     ap.add_argument("--restarts", type=int, default=256)
     ap.add_argument("--gemv-kernel", type=int, default=0, choices=[0, 1, 2],
                     help="scheduler of the FP32 lanes: 0 library's choice, 1 lock-step, 2 lane loop")
+    ap.add_argument("--rows-per-item", type=int, default=0,
+                    help="FP32 lanes: matrix rows per work item (0 = library default)")
     ap.add_argument("--lane-budget", type=int, default=0,
                     help="lane loop: steps per lane per launch (0 = library default)")
     args = ap.parse_args()

@@ -128,6 +128,8 @@ typedef struct {
                              /* advance independently inside one launch); 0 = 2 for 4  */
                              /* or more lanes, else 1 (and 1 when profile_kernels == 2) */
     int lane_budget;         /* lane loop: steps per lane between host checks; 0 = 1024 */
+    int rows_per_item;       /* FP32 lanes: matrix rows per work item, 8..256 (a multiple */
+                             /* of 8); 0 = chosen from the batch size                  */
     double target_objective; /* objective to time against (used when finite)           */
     void* stream;            /* cudaStream_t, NULL = default stream                    */
     const double* const* mu; /* optional perturbations, one n x n matrix per instance   */
