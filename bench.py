@@ -32,8 +32,8 @@ METRIC = "inner PG iters/s (batch×n) and time-to-oracle-objective vs plain FP32
 UNIT = "lane-var-updates/s"
 GEMV_KERNELS = {1: "phase_a_gemv_kernel", 2: "lane_loop_kernel"}
 # DRAM bytes (read + write) per algorithmic byte of lane_loop_kernel, from the ncu capture of
-# one whole-solve launch of this workload (profiles/lane_loop_kernel_c2.md): 28.19 / 28.60 GB
-LOOP_TRAFFIC_RATIO = 28.19 / 28.60
+# one whole-solve launch of this workload (profiles/lane_loop_kernel_c2.md): 28.12 / 28.60 GB
+LOOP_TRAFFIC_RATIO = 28.12 / 28.60
 SIZES = (250, 500, 1000, 2500)
 SEEDS_PER_SIZE = 10
 WORKLOAD = ("plain PSDP sweep: n in {250,500,1000,2500} x 10 seeded instances, density 0.1, "
