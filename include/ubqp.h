@@ -86,7 +86,7 @@ typedef struct {
                              /* and 128 starts per instance (0 when not tuned)          */
     int32_t tc_kernel;       /* tensor-core contraction that ran: 1 split-K clusters,   */
                              /* 2 persistent (many tiles), 0 none                       */
-    int32_t reserved_;
+    int32_t sym_storage;     /* 1 when the FP32 lanes ran on the symmetric tiles        */
     int64_t inner_hist[UBQP_HIST_BINS]; /* projected steps per subproblem (Fig. 5)   */
 } ubqp_stats;
 
@@ -130,6 +130,9 @@ typedef struct {
     int lane_budget;         /* lane loop: steps per lane between host checks; 0 = 1024 */
     int rows_per_item;       /* FP32 lanes: matrix rows per work item, 8..256 (a multiple */
                              /* of 8); 0 = chosen from the batch size                  */
+    int sym_storage;         /* FP32 lanes on the lane loop: 1 = store only the upper   */
+                             /* triangle of Q'_off (128 x 128 tiles; each step reads    */
+                             /* about half the bytes), 0 = dense rows: 1                */
     double target_objective; /* objective to time against (used when finite)           */
     void* stream;            /* cudaStream_t, NULL = default stream                    */
     const double* const* mu; /* optional perturbations, one n x n matrix per instance   */

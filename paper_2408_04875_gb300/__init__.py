@@ -42,7 +42,7 @@ class Stats(C.Structure):
                 ("phase_a_ms", C.c_double), ("phase_a_launches", C.c_int64), ("phase_a_bytes", C.c_int64),
                 ("kernel_launches", C.c_int64), ("ms_to_target", C.c_double), ("phase_a_flops", C.c_int64),
                 ("cluster_size", C.c_int32), ("gemv_kernel", C.c_int32), ("restarts", C.c_int32),
-                ("restart_probe_us", C.c_float * 5), ("tc_kernel", C.c_int32), ("reserved_", C.c_int32),
+                ("restart_probe_us", C.c_float * 5), ("tc_kernel", C.c_int32), ("sym_storage", C.c_int32),
                 ("inner_hist", C.c_int64 * HIST_BINS)]
 
     def as_dict(self):
@@ -60,7 +60,7 @@ class Opts(C.Structure):
                 ("sigma_rel", C.c_double), ("seed", C.c_uint64), ("restarts", C.c_int),
                 ("precision", C.c_int), ("lobpcg_max_iter", C.c_int), ("lobpcg_tol", C.c_double),
                 ("jacobi_max_iter", C.c_int), ("max_ticks_per_sync", C.c_int), ("profile_kernels", C.c_int),
-                ("stop_at_target", C.c_int), ("tc_cluster", C.c_int), ("gemv_kernel", C.c_int), ("lane_budget", C.c_int), ("rows_per_item", C.c_int), ("target_objective", C.c_double),
+                ("stop_at_target", C.c_int), ("tc_cluster", C.c_int), ("gemv_kernel", C.c_int), ("lane_budget", C.c_int), ("rows_per_item", C.c_int), ("sym_storage", C.c_int), ("target_objective", C.c_double),
                 ("stream", C.c_void_p),
                 ("mu", C.c_void_p), ("x_starts", C.c_void_p), ("stats", C.POINTER(Stats))]
 

@@ -168,6 +168,8 @@ struct InstDev {
     bool Q_host, b_host, mu_host, starts_host;
     size_t o_Qoff, o_Qbf, o_Qeval, o_d, o_bp, o_oabs, o_rabs, o_tsum, o_borig, o_qdb, o_gamma;
     size_t ntact = 0;     // TC: index of this instance's first N tile in the active-lane counters
+    int nb = 0;           // row blocks of kSymT rows (symmetric storage)
+    size_t o_Qsym = 0;    // symmetric storage tiles
     size_t o_Uhi, o_Ulo;
     int bn, n_tiles, rows_b;   // tensor-core tiling of this instance's lanes
     int lane0, nl;
@@ -210,6 +212,18 @@ class Solver {
         UBQP_CK(cudaGetDevice(&dev));
         UBQP_CK(cudaDeviceGetAttribute(&num_sms_, cudaDevAttrMultiProcessorCount, dev));
 
+        // ---- symmetric storage: only with the lane loop (decided here because it fixes the
+        // row padding and the row blocks); tiles are indexed in 15 bits per lane
+        {
+            const bool loop_likely =
+                !tc && lanes.size() < 0xFFFEu &&
+                (o_.gemv_kernel == 2 || (o_.gemv_kernel == 0 && o_.profile_kernels < 2 && lanes.size() >= 4));
+            sym_ = loop_likely && o_.sym_storage != 0;
+            for (const InstIn& in : insts) {
+                const int64_t nb = (in.n + kSymT - 1) / kSymT;
+                if (nb * (nb + 1) / 2 >= 0x8000) sym_ = false;
+            }
+        }
         // ---- layout
         inst_.resize(insts.size());
         int max_ld = 32;
@@ -217,7 +231,7 @@ class Solver {
             const InstIn& in = insts[t];
             InstDev& I = inst_[t];
             I.n = in.n;
-            I.ld = (int)round_up((size_t)in.n, tc ? 128 : 32);
+            I.ld = (int)round_up((size_t)in.n, sym_ ? kSymT : (tc ? 128 : 32));
             max_ld = std::max(max_ld, I.ld);
             const size_t n = (size_t)in.n, ld = (size_t)I.ld;
             I.Q_host = !is_device_ptr(in.Q);
@@ -231,6 +245,8 @@ class Solver {
             I.o_Qoff = tc ? 0 : ar_.reserve(n * ld * 4);
             I.o_Qbf = tc ? ar_.reserve(ld * ld * 2) : 0;
             I.o_Qeval = tc ? 0 : ar_.reserve(n * ld * 8);
+            I.nb = (int)(ld / kSymT);
+            I.o_Qsym = sym_ ? ar_.reserve((size_t)I.nb * (I.nb + 1) / 2 * kSymT * kSymT * 4) : 0;
             I.o_d = ar_.reserve(ld * 4);
             I.o_bp = ar_.reserve(ld * 4);
             I.o_oabs = ar_.reserve(ld * 4);
@@ -264,6 +280,7 @@ class Solver {
         int rb = 8;
         while (rb < 32 && total_rows / rb > target_items) rb *= 2;
         if (o_.rows_per_item > 0) rb = o_.rows_per_item;
+        if (sym_) rb = kSymT;   // the second stage works on whole tile rows
         rows_per_item_ = rb;
 
         lanes_.assign(lanes.size(), LaneDev());
@@ -275,6 +292,8 @@ class Solver {
         o_trace_a_.assign(lanes.size(), 0);
         o_x0_.assign(lanes.size(), SIZE_MAX);
         o_p0_.assign(lanes.size(), SIZE_MAX);
+        sym_host_.assign(sym_ ? lanes.size() : 0, SymLane());
+        o_pbuf_.assign(lanes.size(), 0);
         int64_t nitems = 0;
         for (size_t l = 0; l < lanes.size(); ++l) {
             const LaneIn& in = lanes[l];
@@ -290,7 +309,12 @@ class Solver {
             L.stop_after = in.stop_after;
             L.restart = in.restart;
             L.trace_len = in.trace_len;
-            if (!tc) nitems += L.nblk;
+            if (!tc) nitems += sym_ ? (int64_t)I.nb * (I.nb + 1) / 2 : L.nblk;
+            if (sym_) {
+                sym_host_[l].nb = I.nb;
+                sym_host_[l].ntiles = I.nb * (I.nb + 1) / 2;
+                o_pbuf_[l] = ar_.reserve((size_t)I.nb * I.ld * 4);
+            }
             o_vec_[l] = ar_.reserve((size_t)NVEC * I.ld * 4);
             o_bx_[l] = ar_.reserve((size_t)I.ld);
             o_part_[l] = ar_.reserve((size_t)L.nblk * sizeof(Partial));
@@ -319,6 +343,8 @@ class Solver {
         o_flops_ = ar_.reserve(sizeof(unsigned long long));
         o_states_ = ar_.reserve(lanes.size() * sizeof(LaneState));
         o_counters_ = ar_.reserve(lanes.size() * sizeof(unsigned int));
+        o_symctr_ = sym_ ? ar_.reserve(lanes.size() * sizeof(unsigned int)) : 0;
+        o_symlanes_ = sym_ ? ar_.reserve(lanes.size() * sizeof(SymLane)) : 0;
         o_queue_ = ar_.reserve(2 * sizeof(int32_t));
         o_lanes_ = ar_.reserve(lanes.size() * sizeof(LaneDev));
         o_linit_ = ar_.reserve(lanes.size() * sizeof(LaneInit));
@@ -346,8 +372,8 @@ class Solver {
             }
             // automatic choice: the loop pays off once several lanes can overlap one another's
             // update latency; one to three lanes step faster in lock-step
-            loop_ = fits && (o_.gemv_kernel == 2 ||
-                             (o_.gemv_kernel == 0 && o_.profile_kernels < 2 && lanes.size() >= 4));
+            loop_ = sym_ || (fits && (o_.gemv_kernel == 2 ||
+                                      (o_.gemv_kernel == 0 && o_.profile_kernels < 2 && lanes.size() >= 4)));
             if (loop_) {
                 UBQP_CK(prepare_lane_loop(max_ld));
                 loop_grid_ = lane_loop_grid(max_ld);
@@ -366,6 +392,7 @@ class Solver {
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_bytes_), 0, sizeof(unsigned long long), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_flops_), 0, sizeof(unsigned long long), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_counters_), 0, lanes.size() * sizeof(unsigned int), stream_));
+        if (sym_) UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_symctr_), 0, lanes.size() * sizeof(unsigned int), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_queue_), 0, 2 * sizeof(int32_t), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_valid_), 0, insts.size() * 4 * sizeof(float), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_scal_), 0, insts.size() * 4 * sizeof(float), stream_));
@@ -468,6 +495,12 @@ class Solver {
                                 cudaMemcpyHostToDevice, stream_));
         UBQP_CK(launch_reformulate(ar_.at<RefArgs>(o_refargs_), ar_.at<int64_t>(o_row0_), ninst, row0[ninst], stream_));
         launches_ += 2;
+        if (sym_)
+            for (InstDev& I : inst_) {
+                if (I.nl == 0) continue;
+                UBQP_CK(launch_pack_sym(ar_.at<float>(I.o_Qoff), (int)I.n, I.ld, ar_.at<float>(I.o_Qsym), stream_));
+                launches_ += 1;
+            }
         std::vector<float> scal(insts.size() * 4);
         UBQP_CK(cudaMemcpyAsync(scal.data(), ar_.at<float>(o_scal_), scal.size() * 4, cudaMemcpyDeviceToHost, stream_));
         std::vector<int> inexact(insts.size());
@@ -523,6 +556,12 @@ class Solver {
             L.part = ar_.at<Partial>(o_part_[l]);
             L.st = ar_.at<LaneState>(o_states_) + l;
             L.counter = ar_.at<unsigned int>(o_counters_) + l;
+            if (sym_) {
+                SymLane& S = sym_host_[l];
+                S.Qsym = ar_.at<float>(I.o_Qsym);
+                S.pbuf = ar_.at<float>(o_pbuf_[l]);
+                S.counter = ar_.at<unsigned int>(o_symctr_) + l;
+            }
             if (tc) {
                 L.u_hi = ar_.at<__nv_bfloat16>(I.o_Uhi) + (size_t)in.restart * I.ld;
                 L.u_lo = I.o_Ulo ? ar_.at<__nv_bfloat16>(I.o_Ulo) + (size_t)in.restart * I.ld : nullptr;
@@ -538,8 +577,11 @@ class Solver {
             for (size_t l = 0; l < lanes.size(); ++l) order[l] = (int)l;
             std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lanes_[a].n > lanes_[b].n; });
             for (int l : order)
-                for (int b = 0; b < lanes_[l].nblk; ++b) items.push_back(make_int2(l, b));
+                for (int b = 0; b < (sym_ ? sym_host_[l].ntiles : lanes_[l].nblk); ++b) items.push_back(make_int2(l, b));
         }
+        if (sym_)
+            UBQP_CK(cudaMemcpyAsync(ar_.at<SymLane>(o_symlanes_), sym_host_.data(), sym_host_.size() * sizeof(SymLane),
+                                    cudaMemcpyHostToDevice, stream_));
         UBQP_CK(cudaMemcpyAsync(ar_.at<LaneDev>(o_lanes_), lanes_.data(), lanes_.size() * sizeof(LaneDev),
                                 cudaMemcpyHostToDevice, stream_));
         UBQP_CK(cudaMemcpyAsync(ar_.at<LaneInit>(o_linit_), lane_init_.data(), lane_init_.size() * sizeof(LaneInit),
@@ -831,6 +873,7 @@ class Solver {
         la.active_after = ctr + 1;
         la.err = ctr + 2;
         la.budget_left = ar_.at<int32_t>(o_budget_);
+        la.sym = sym_ ? ar_.at<SymLane>(o_symlanes_) : nullptr;
         la.P = make_params(o_, ar_.at<int64_t>(o_hist_));
         const bool prof = o_.profile_kernels != 0;
         if (prof) la.P.bytes = ar_.at<unsigned long long>(o_bytes_);
@@ -986,6 +1029,7 @@ class Solver {
         s->phase_a_flops = (int64_t)fl;
         s->cluster_size = tc_ ? tc_S_ : 0;
         s->tc_kernel = tc_ ? (tcp_ ? 2 : 1) : 0;
+        s->sym_storage = sym_ ? 1 : 0;
         s->gemv_kernel = tc_ ? 0 : (loop_ ? 2 : 1);
         UBQP_CK(cudaMemcpyAsync(s->inner_hist, ar_.at<int64_t>(o_hist_), sizeof(s->inner_hist), cudaMemcpyDeviceToHost,
                                 stream_));
@@ -1084,6 +1128,10 @@ class Solver {
            o_flops_ = 0, o_queue_ = 0;
     int tc_tiles_ = 0, tc_S_ = 1, tc_stages_ = 2, max_bn_ = 16;
     bool tcp_ = false;   // tensor-core lanes on the persistent kernel
+    bool sym_ = false;   // FP32 lanes on the symmetric storage (lane loop only)
+    std::vector<SymLane> sym_host_;
+    std::vector<size_t> o_pbuf_;
+    size_t o_symctr_ = 0, o_symlanes_ = 0;
     size_t ntact_total_ = 0, o_ntact_ = 0, o_row0_ = 0, o_valargs_ = 0, o_refargs_ = 0;
     std::vector<int32_t> ntact_host_;   // staged until the copy completes (the stream syncs in run)
     int tcp_grid_ = 0;
@@ -1129,6 +1177,7 @@ void ubqp_opts_default(ubqp_opts* o)
     o->gemv_kernel = 0;
     o->lane_budget = 0;
     o->rows_per_item = 0;
+    o->sym_storage = 1;
     o->target_objective = INFINITY;
     o->stream = nullptr;
     o->mu = nullptr;

@@ -166,17 +166,147 @@ __device__ __forceinline__ void item_rows(const LaneDev& L, int ph, int row0, in
 // algorithmic bytes of the item when P.bytes is set: the stored entries of these rows once
 // (FP32, or 8 bytes per entry of the evaluation matrix), the input vector once per lane
 // (charged to block 0), and the per-row vectors the epilogue touches
+// (sym_parts > 0: the rows' products came from the symmetric tiles, and the item read
+// sym_parts partial values per row instead of matrix rows)
 __device__ __forceinline__ void item_finish(const LaneDev& L, int ph, int k, int blk, int row0, int rows,
-                                            const double* sv, const Params& P)
+                                            const double* sv, const Params& P, int sym_parts = 0)
 {
     Acc a;
     a.zero();
     if ((int)threadIdx.x < rows) row_epilogue(L, ph, k, row0 + threadIdx.x, sv[threadIdx.x], a, P.tau_z);
     block_reduce_write<kWarps>(a, ph, L.part + blk, ph == PH_EVAL);
     if (P.bytes && threadIdx.x == 0) {
-        unsigned long long by = (unsigned long long)rows * L.n * (ph == PH_EVAL ? 8ull : 4ull) +
-                                (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
+        unsigned long long by = sym_parts > 0
+                                    ? (unsigned long long)rows * (unsigned long long)sym_parts * 4ull + 16ull * rows
+                                    : (unsigned long long)rows * L.n * (ph == PH_EVAL ? 8ull : 4ull) +
+                                          (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
         atomicAdd(P.bytes, by);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Symmetric storage (persistent lane loop).  Q_off is symmetric, so only its upper
+// triangle is stored, as kSymT x kSymT FP32 tiles (I <= J, row-major inside a tile) packed
+// row by row: tile t of the sequence (0,0), (0,1), .., (0,nb-1), (1,1), ...  One read of a
+// tile gives two products: its rows times u_J (for the rows of block I) and its columns
+// times u_I (for the rows of block J); a diagonal tile is stored whole and gives its row
+// products only.  Each product is a partial vector of kSymT values, written to
+// pbuf[K * ld + row] with K the other block index, so that a row of block b finds its nb
+// partials at pbuf[K * ld + row], K = 0 .. nb-1, from the tiles (b, K) or (K, b).  A second
+// stage sums them in that order for each row block and runs the usual epilogue.
+// tile t -> (I, J), I <= J, in the row-by-row packing of an nb x nb upper triangle
+__device__ __forceinline__ void sym_tile_ij(int t, int nb, int& I, int& J)
+{
+    // first tile of row i: f(i) = i nb - i (i - 1) / 2; take the largest i with f(i) <= t
+    const float b2 = 2.f * nb + 1.f;
+    int i = (int)floorf((b2 - sqrtf(fmaxf(b2 * b2 - 8.f * (float)t, 0.f))) * 0.5f);
+    i = max(0, min(i, nb - 1));
+    while (i > 0 && i * nb - i * (i - 1) / 2 > t) --i;
+    while (i + 1 < nb && (i + 1) * nb - (i + 1) * i / 2 <= t) ++i;
+    I = i;
+    J = i + (t - (i * nb - i * (i - 1) / 2));
+}
+
+// one tile of one lane: the row products go to pbuf[J][rows of I] and (off the diagonal) the
+// column products to pbuf[I][rows of J].  Warp w takes tile rows 16 w .. 16 w + 15 in two
+// passes of 8, lane l columns 4 l .. 4 l + 3.  Row products: the four products of a lane
+// summed with FMAs, then the 8 rows of a pass reduced over the 32 lanes by a butterfly that
+// halves the values each lane holds at every stage (9 shuffles for 8 rows; afterwards lane l
+// holds row (l >> 2) & 7).  Column products: FMAs over the warp's 16 rows, then the 8 warps
+// merged in order with TwoSum.  The sum over tiles (the second stage) is TwoSum-compensated.
+// (Measured on the 40-lane sweep: 128 x 128 tiles 18.98 s per step; 256 x 256 tiles 21.8 s,
+// too few work items once the small lanes are one tile each.)
+__device__ __forceinline__ void sym_tile_item(const SymLane& S, const LaneDev& L, int t, float* s_u,
+                                              float (*s_col)[kSymT], const Params& P)
+{
+    static_assert(kSymT == 128 && kThreads == 256, "the mapping below is written for 128 x 128 tiles");
+    int I, J;
+    sym_tile_ij(t, S.nb, I, J);
+    const int ld = L.ld;
+    const float* u = L.vec + (size_t)V_U * ld;
+    if (threadIdx.x < kSymT) s_u[threadIdx.x] = u[I * kSymT + threadIdx.x];
+    else s_u[threadIdx.x] = u[J * kSymT + threadIdx.x - kSymT];
+    __syncthreads();
+    const float* s_uI = s_u;
+    const float4 uj = reinterpret_cast<const float4*>(s_u + kSymT)[threadIdx.x & 31];
+    const float4* tile = reinterpret_cast<const float4*>(S.Qsym + (size_t)t * kSymT * kSymT);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+    float* rowdst = S.pbuf + (size_t)J * ld + I * kSymT;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int r0 = warp * 16 + h * 8;
+        float4 q[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) q[r] = ldg_stream(tile + (size_t)(r0 + r) * (kSymT / 4) + lane);
+        float v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            float a = __fmul_rn(q[r].x, uj.x);
+            a = fmaf(q[r].y, uj.y, a);
+            a = fmaf(q[r].z, uj.z, a);
+            v[r] = fmaf(q[r].w, uj.w, a);
+            const float ui = s_uI[r0 + r];
+            c0 = fmaf(q[r].x, ui, c0);
+            c1 = fmaf(q[r].y, ui, c1);
+            c2 = fmaf(q[r].z, ui, c2);
+            c3 = fmaf(q[r].w, ui, c3);
+        }
+        // butterfly: lanes with the stage's bit set keep the upper half of their rows
+        {
+            const bool up = lane & 16;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float keep = up ? v[j + 4] : v[j], send = up ? v[j] : v[j + 4];
+                v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+            }
+        }
+        {
+            const bool up = lane & 8;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const float keep = up ? v[j + 2] : v[j], send = up ? v[j] : v[j + 2];
+                v[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+            }
+        }
+        {
+            const bool up = lane & 4;
+            const float keep = up ? v[1] : v[0], send = up ? v[0] : v[1];
+            v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+        if ((lane & 3) == 0) rowdst[r0 + ((lane >> 2) & 7)] = v[0];
+    }
+    if (I != J) {
+        s_col[warp][4 * lane + 0] = c0;
+        s_col[warp][4 * lane + 1] = c1;
+        s_col[warp][4 * lane + 2] = c2;
+        s_col[warp][4 * lane + 3] = c3;
+        __syncthreads();
+        if (threadIdx.x < kSymT) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) csum_add(acc, s_col[w][threadIdx.x]);
+            S.pbuf[(size_t)I * ld + J * kSymT + threadIdx.x] = acc.x + acc.y;
+        }
+    }
+    if (P.bytes && threadIdx.x == 0) {
+        // the tile's entries inside the matrix once, u_I and u_J, the partial vectors written
+        const unsigned long long ri = (unsigned long long)min(kSymT, L.n - I * kSymT);
+        const unsigned long long cj = (unsigned long long)min(kSymT, L.n - J * kSymT);
+        atomicAdd(P.bytes, ri * cj * 4ull + 2ull * kSymT * 4ull + (I != J ? 2ull : 1ull) * kSymT * 4ull);
+    }
+}
+
+// row products of block b from its nb partial vectors, summed in K order with TwoSum
+__device__ __forceinline__ void sym_block_sums(const SymLane& S, const LaneDev& L, int b, int rows, double* sv)
+{
+    if ((int)threadIdx.x < rows) {
+        const float* p = S.pbuf + b * kSymT + threadIdx.x;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int K = 0; K < S.nb; ++K) csum_add(acc, p[(size_t)K * L.ld]);
+        sv[threadIdx.x] = (double)(acc.x + acc.y);
     }
 }
 

@@ -319,6 +319,32 @@ __global__ void trace_to_f64_kernel(const float* in, double* out, int64_t count)
 }
 
 // ---------------------------------------------------------------------------------
+// Packs Q'_off (n x ld FP32 rows, zero diagonal) into the upper-triangle tiles of the
+// symmetric storage: kSymT x kSymT tiles (I, J), I <= J, row-major inside a tile, in the
+// order (0,0), (0,1), .., (0,nb-1), (1,1), ...  One CTA per tile; rows beyond n are zero.
+__global__ void pack_sym_kernel(const float* __restrict__ Qoff, int n, int ld, float* __restrict__ Qsym, int nb)
+{
+    int I = 0, rem = (int)blockIdx.x, rowlen = nb;
+    while (rem >= rowlen) {
+        rem -= rowlen;
+        ++I;
+        --rowlen;
+    }
+    const int J = I + rem;
+    float* dst = Qsym + (size_t)blockIdx.x * kSymT * kSymT;
+    for (int e = threadIdx.x; e < kSymT * kSymT; e += blockDim.x) {
+        const int row = I * kSymT + e / kSymT, col = J * kSymT + e % kSymT;
+        dst[e] = row < n ? Qoff[(size_t)row * ld + col] : 0.f;
+    }
+}
+
+cudaError_t launch_pack_sym(const float* Qoff, int n, int ld, float* Qsym, cudaStream_t s)
+{
+    const int nb = ld / kSymT;
+    pack_sym_kernel<<<nb * (nb + 1) / 2, 256, 0, s>>>(Qoff, n, ld, Qsym, nb);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_validate(const ValArgs* v, const int64_t* row0, int ninst, int64_t rows, cudaStream_t s)
 {
     validate_kernel<<<(unsigned)rows, 256, 0, s>>>(v, row0, ninst);

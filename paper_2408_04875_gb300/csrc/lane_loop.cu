@@ -15,6 +15,12 @@
 // 32 bits, so a consumer that popped position q waits until the slot holds position q's
 // entry; every wait gives up after kLoopWaitNs, sets the error flag and ends the CTA.
 //
+// With symmetric storage (A.sym set) a step that multiplies by Q_off has two stages: one
+// entry per stored tile (entry block < kBlockFlag), whose products go to the lane's partial
+// vectors, and then, pushed by the CTA that finished the lane's last tile, one entry per row
+// block (kBlockFlag | b) that sums the block's partials and runs the epilogue.  Evaluation
+// steps read the dense evaluation matrix and have row-block entries only.
+//
 // Lanes written by one CTA are read by CTAs on other SMs within the same launch, so this
 // file is compiled with plain loads cached in L2 only (-dlcm=cg): no SM may serve a lane
 // vector from a stale L1 line.  Q itself never changes and keeps its non-coherent
@@ -26,6 +32,7 @@ namespace ubqp {
 constexpr uint64_t kLoopWaitNs = 5000000000ull;   // 5 s
 constexpr uint32_t kLaneSkip = 0xFFFEu;            // seeded block of a finished lane
 constexpr uint32_t kLanePoison = 0xFFFFu;          // ends the CTA that pops it
+constexpr uint32_t kBlockFlag = 0x8000u;           // symmetric storage: a row-block entry
 
 __device__ __forceinline__ unsigned long long ring_seq(unsigned long long pos, unsigned long long cap)
 {
@@ -76,9 +83,15 @@ __global__ void __launch_bounds__(1024) lane_loop_seed_kernel(LoopArgs A)
     const unsigned long long base = s_base, cap = A.cap;
     for (int e = threadIdx.x; e < A.nitems; e += blockDim.x) {
         const int2 it = A.items[e];
-        const bool act = A.lanes[it.x].st->phase != PH_DONE;
+        const int ph = A.lanes[it.x].st->phase;
+        bool act = ph != PH_DONE;
+        unsigned blk = (unsigned)it.y;
+        if (A.sym && ph == PH_EVAL) {   // an evaluation step: row blocks only
+            act = it.y < A.sym[it.x].nb;
+            blk |= kBlockFlag;
+        }
         const unsigned long long pos = base + (unsigned long long)e;
-        const unsigned long long pay = act ? ((unsigned long long)it.x << 16) | (unsigned)it.y
+        const unsigned long long pay = act ? ((unsigned long long)it.x << 16) | blk
                                            : ((unsigned long long)kLaneSkip << 16);
         A.ring[pos & (cap - 1)] = ring_seq(pos, cap) | pay;
     }
@@ -102,6 +115,8 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
     __shared__ int s_last, s_npush;
     __shared__ unsigned s_pay;
     __shared__ __align__(16) LaneDev sL;   // the popped lane's descriptor
+    __shared__ __align__(16) float s_uIJ[2 * kSymT];   // u_I, u_J of a tile
+    __shared__ float s_col[kWarps][kSymT];
     static_assert(sizeof(LaneDev) % 8 == 0, "descriptor copied in 8-byte pieces");
     const unsigned long long cap = A.cap, mask = cap - 1;
 
@@ -126,7 +141,8 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
         }
         __syncthreads();
         const unsigned pay = (unsigned)(s_entry & 0xFFFFFFFFull);
-        const int lane_id = (int)(pay >> 16), blk = (int)(pay & 0xFFFFu);
+        const int lane_id = (int)(pay >> 16);
+        int blk = (int)(pay & 0xFFFFu);
         if ((unsigned)lane_id == kLanePoison) break;
         if ((unsigned)lane_id == kLaneSkip) {
             __syncthreads();
@@ -139,15 +155,50 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
             reinterpret_cast<int2*>(&sL)[threadIdx.x] = __ldg(reinterpret_cast<const int2*>(A.lanes + lane_id) + threadIdx.x);
         __syncthreads();
         const LaneDev& L = sL;
+        if (A.sym && !(blk & kBlockFlag)) {
+            // ---- symmetric storage, stage 1: one tile's row and column products
+            const SymLane S = A.sym[lane_id];
+            sym_tile_item(S, L, blk, s_uIJ, s_col, A.P);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_npush = 0;
+                if (atomicAdd(S.counter, 1u) == (unsigned)(S.ntiles - 1)) {
+                    // the lane's last tile: its row blocks come next
+                    *S.counter = 0u;
+                    s_npush = S.nb;
+                    s_pay = ((unsigned)lane_id << 16) | kBlockFlag;
+                    s_base = atomicAdd(A.tail, (unsigned long long)S.nb);
+                    __threadfence();
+                }
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < s_npush; t += kThreads) {
+                const unsigned long long pos = s_base + (unsigned long long)t;
+                st_release(A.ring + (pos & mask), ring_seq(pos, cap) | s_pay | (unsigned)t);
+            }
+            __syncthreads();
+            continue;
+        }
+        blk &= ~(int)kBlockFlag;
         const int ph = L.st->phase;
         const int k = L.st->k;
         const int row0 = blk * A.rows_per_item;
         const int rows = min(A.rows_per_item, L.n - row0);
-        item_load_u(L, su);
-        __syncthreads();
-        item_rows(L, ph, row0, rows, su, sv);
-        __syncthreads();
-        item_finish(L, ph, k, blk, row0, rows, sv, A.P);
+        int sym_parts = 0;
+        if (A.sym && ph != PH_EVAL) {
+            // ---- symmetric storage, stage 2: the block's products from its partial vectors
+            const SymLane S = A.sym[lane_id];
+            sym_block_sums(S, L, blk, rows, sv);
+            sym_parts = S.nb;
+            __syncthreads();
+        } else {
+            item_load_u(L, su);
+            __syncthreads();
+            item_rows(L, ph, row0, rows, su, sv);
+            __syncthreads();
+        }
+        item_finish(L, ph, k, blk, row0, rows, sv, A.P, sym_parts);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) s_last = (atomicAdd(L.counter, 1u) == (unsigned)(L.nblk - 1));
@@ -164,9 +215,13 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
                 A.budget_left[lane_id] = left;
                 const bool done = L.st->phase == PH_DONE;
                 if (!done && left > 0) {
-                    s_npush = L.nblk;
-                    s_pay = (unsigned)lane_id << 16;
-                    s_base = atomicAdd(A.tail, (unsigned long long)L.nblk);
+                    // next step: dense row blocks, or with symmetric storage the tiles (the
+                    // row blocks alone for an evaluation step)
+                    const bool tiles = A.sym && L.st->phase != PH_EVAL;
+                    const int cnt = tiles ? A.sym[lane_id].ntiles : L.nblk;
+                    s_npush = cnt;
+                    s_pay = ((unsigned)lane_id << 16) | (A.sym && !tiles ? kBlockFlag : 0u);
+                    s_base = atomicAdd(A.tail, (unsigned long long)cnt);
                 } else {
                     if (!done) atomicAdd(A.active_after, 1);
                     const bool last_lane = atomicSub(A.running, 1) == 1;

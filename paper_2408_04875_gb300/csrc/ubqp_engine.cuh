@@ -64,6 +64,9 @@ struct FinalArgs {
     uint8_t* const* x_out;  // device pointers, one per instance
 };
 
+// Q'_off rows -> symmetric storage tiles (ld a multiple of 128)
+cudaError_t launch_pack_sym(const float* Qoff, int n, int ld, float* Qsym, cudaStream_t s);
+
 // one launch for every instance of a batch; row0[t] = first global row of instance t
 cudaError_t launch_validate(const ValArgs* v, const int64_t* row0, int ninst, int64_t rows, cudaStream_t s);
 cudaError_t launch_reformulate(const RefArgs* args, const int64_t* row0, int ninst, int64_t rows, cudaStream_t s);

@@ -385,6 +385,18 @@ cudaError_t prepare_phase_a_gemv(int max_ld);
 int gemv_grid(int max_ld, int nitems);
 cudaError_t launch_phase_a_gemv_f32(const TickArgs& a, cudaStream_t s);
 cudaError_t launch_phase_a_grad(const TickArgs& a, int dtype, int64_t n, cudaStream_t s);
+constexpr int kSymT = 128;   // tile edge of the symmetric storage
+
+// one lane's symmetric storage (persistent lane loop): the packed upper-triangle tiles of
+// its instance, its partial vectors (nb x ld floats) and the counter of its tiles this step
+struct SymLane {
+    const float* Qsym;
+    float* pbuf;
+    unsigned int* counter;
+    int32_t nb;                 // row blocks of kSymT rows
+    int32_t ntiles;             // nb (nb + 1) / 2
+};
+
 // persistent lane loop (GEMV lanes): a ring of (lane, row block) entries shared by all CTAs
 struct LoopArgs {
     const LaneDev* lanes;
@@ -403,6 +415,7 @@ struct LoopArgs {
     int32_t* active_after;      // lanes unfinished when the launch ends
     int32_t* err;               // set when a bounded wait runs out
     int32_t* budget_left;       // per lane
+    const SymLane* sym;         // per lane, or null: dense rows
     Params P;
 };
 

@@ -63,8 +63,13 @@ def _trajectory_sensitivity(Qp, bp, p, x0, ref, K):
     return float(np.max(np.max(np.abs(Y - X), axis=1) / np.max(np.abs(X), axis=1)))
 
 
+# dense rows (one lane steps in lock-step), or the lane loop on the symmetric tiles
+SCHEDULES = {"dense": {}, "sym": dict(gemv_kernel=2, sym_storage=1)}
+
+
+@pytest.mark.parametrize("sched", ["dense", "sym"])
 @pytest.mark.parametrize("n,seed", [(50, 0), (50, 1), (50, 2), (100, 0), (250, 0), (250, 1), (700, 2)])
-def test_pabb_first_50_iterates_within_1e5(ub, n, seed):
+def test_pabb_first_50_iterates_within_1e5(ub, n, seed, sched):
     """Both sides run Alg. 2 from the same FP32-representable state (Q', b', p, x^0 as
     the GPU holds them).  Bar: relative deviation <= 1e-5 over the first 50 iterates.
     A BB trajectory can amplify rounding by orders of magnitude (a long BB1 step after a
@@ -75,7 +80,7 @@ def test_pabb_first_50_iterates_within_1e5(ub, n, seed):
     Q, b = I.random_ubqp(n, 0.1, seed)
     Qp, bp, p, x0 = (_r32(a) for a in _state_after_first_penalty(Q, b, I.perturbation(Q, seed)))
     ref = O.inner(Qp, bp, p, x0, trace_len=51)
-    got = ub.inner_run(Qp, bp, p, x0, trace_len=51)
+    got = ub.inner_run(Qp, bp, p, x0, trace_len=51, **SCHEDULES[sched])
     K = min(50, ref["steps"], got["steps"])
     X, Y = ref["trace_x"][: K + 1], got["trace_x"][: K + 1]
     rel = np.max(np.abs(Y - X), axis=1) / np.maximum(np.max(np.abs(X), axis=1), 1e-30)
@@ -168,10 +173,11 @@ def test_ragged_batch_matches_single_solves(ub):
     specs = [(37, 1), (120, 2), (64, 3), (250, 4)]
     Qs = [I.random_ubqp(n, 0.15, s)[0] for n, s in specs]
     mus = [I.perturbation(Q, s) for Q, (n, s) in zip(Qs, specs)]
-    xs, obj, _ = ub.solve_batched(Qs, None, mus)
-    for Q, mu, x, f in zip(Qs, mus, xs, obj):
-        x1, f1, _ = ub.solve(Q, None, mu=mu)
-        assert f1 == f and np.array_equal(x1, x)
+    for kw in (dict(gemv_kernel=2, sym_storage=1), dict(gemv_kernel=2, sym_storage=0), dict(gemv_kernel=1)):
+        xs, obj, _ = ub.solve_batched(Qs, None, mus, **kw)
+        for Q, mu, x, f in zip(Qs, mus, xs, obj):
+            x1, f1, _ = ub.solve(Q, None, mu=mu, **kw)
+            assert f1 == f and np.array_equal(x1, x), kw
 
 
 @pytest.mark.parametrize("specs", [[(37, 1)], [(1000, 2)], [(2500, 3)], [(250, 4), (1000, 5), (61, 6)],
@@ -183,15 +189,16 @@ def test_schedulers_agree_bitwise(ub, specs):
     157 row blocks and ragged batches of three and five sizes."""
     Qs = [I.random_ubqp(n, 0.1, s)[0] for n, s in specs]
     mus = [I.perturbation(Q, s) for Q, (n, s) in zip(Qs, specs)]
-    kw = dict(max_outer=4)
+    kw = dict(max_outer=4, sym_storage=0)   # dense rows in both
     x1, f1, s1 = ub.solve_batched(Qs, None, mus, gemv_kernel=1, **kw)
     x2, f2, s2 = ub.solve_batched(Qs, None, mus, gemv_kernel=2, **kw)
     assert s1["gemv_kernel"] == 1 and s2["gemv_kernel"] == 2
     assert np.array_equal(f1, f2) and all(np.array_equal(a, b) for a, b in zip(x1, x2))
     for key in ("inner_iters", "outer_steps", "lobpcg_iters", "jacobi_iters", "var_updates"):
         assert s1[key] == s2[key], key
-    _, _, s0 = ub.solve_batched(Qs, None, mus, **kw)
+    _, _, s0 = ub.solve_batched(Qs, None, mus, max_outer=4)
     assert s0["gemv_kernel"] == (2 if len(specs) >= 4 else 1)   # the default: the loop from 4 lanes
+    assert s0["sym_storage"] == (1 if len(specs) >= 4 else 0)   # ... on the symmetric tiles
 
 
 def test_lane_loop_small_budget_relaunches(ub):
@@ -213,8 +220,8 @@ def test_restarts_keep_best_and_are_exact(ub):
     Q, b = I.random_ubqp(80, 0.2, 9, b_range=(-20, 20))
     mu = I.perturbation(Q, 9)
     starts = I.random_starts(80, 7, 9)
-    x1, f1, _ = ub.solve(Q, b, mu=mu)
-    x8, f8, st = ub.solve(Q, b, mu=mu, starts=starts, restarts=8)
+    x1, f1, _ = ub.solve(Q, b, mu=mu, gemv_kernel=2)   # start 0 alone, in the batch's mode
+    x8, f8, st = ub.solve(Q, b, mu=mu, starts=starts, restarts=8, gemv_kernel=2)
     assert st["lanes"] == 8
     assert f8 <= f1 and f8 == O.objective(Q, b, x8)
     for r in range(7):   # each start alone, through the oracle, is never better than the batch
@@ -222,25 +229,28 @@ def test_restarts_keep_best_and_are_exact(ub):
         assert f8 <= fr + 1e-3 * abs(fr)
 
 
+@pytest.mark.parametrize("sched", ["dense", "sym"])
 @pytest.mark.parametrize("n", [250])
-def test_c2_sizes_within_tenth_percent(ub, n):
+def test_c2_sizes_within_tenth_percent(ub, n, sched):
     Qs, mus = [], []
     for seed in range(3):
         Q, _ = I.c2_instance(n, seed)
         Qs.append(Q)
         mus.append(I.perturbation(Q, seed))
-    xs, obj, _ = ub.solve_batched(Qs, None, mus)
+    xs, obj, st = ub.solve_batched(Qs, None, mus, **SCHEDULES[sched])
+    assert st["sym_storage"] == (1 if sched == "sym" else 0)
     for Q, mu, x, f in zip(Qs, mus, xs, obj):
         assert f == O.objective(Q, None, x)
         _, f_orc, _ = O.solve(Q, None, mu)
         assert f - f_orc <= 1e-3 * abs(f_orc), (f, f_orc)
 
 
-def test_full_size_c2_instance_properties(ub):
-    """n = 2500 (largest single-instance size): exact objective of the returned point,
-    binary output and a finished run."""
+@pytest.mark.parametrize("sched", ["dense", "sym"])
+def test_full_size_c2_instance_properties(ub, sched):
+    """n = 2500 (largest single-instance size; 210 symmetric tiles): exact objective of the
+    returned point, binary output and a finished run."""
     Q, _ = I.c2_instance(2500, 0)
-    x, f, st = ub.solve(Q, None, mu=I.perturbation(Q, 0))
+    x, f, st = ub.solve(Q, None, mu=I.perturbation(Q, 0), **SCHEDULES[sched])
     assert set(np.unique(x)) <= {0, 1}
     assert f == O.objective(Q, None, x)
     assert st["status"] == 0 and st["lanes_capped"] == 0
