@@ -34,7 +34,7 @@ GEMV_KERNELS = {1: "phase_a_gemv_kernel", 2: "lane_loop_kernel"}
 # DRAM bytes (read + write) per algorithmic byte of lane_loop_kernel, from the ncu capture of
 # one whole-solve launch of this workload (profiles/lane_loop_kernel_c2.md); the symmetric
 # storage is the default, the dense rows the alternative (sym_storage = 0)
-LOOP_TRAFFIC_RATIO = {1: 15.59 / 16.90, 0: 28.12 / 28.60}
+LOOP_TRAFFIC_RATIO = {1: 15.70 / 16.90, 0: 28.12 / 28.60}
 SIZES = (250, 500, 1000, 2500)
 SEEDS_PER_SIZE = 10
 WORKLOAD = ("plain PSDP sweep: n in {250,500,1000,2500} x 10 seeded instances, density 0.1, "

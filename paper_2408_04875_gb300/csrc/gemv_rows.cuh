@@ -207,28 +207,25 @@ __device__ __forceinline__ void sym_tile_ij(int t, int nb, int& I, int& J)
     J = i + (t - (i * nb - i * (i - 1) / 2));
 }
 
-// one tile of one lane: the row products go to pbuf[J][rows of I] and (off the diagonal) the
-// column products to pbuf[I][rows of J].  Warp w takes tile rows 16 w .. 16 w + 15 in two
-// passes of 8, lane l columns 4 l .. 4 l + 3.  Row products: the four products of a lane
-// summed with FMAs, then the 8 rows of a pass reduced over the 32 lanes by a butterfly that
-// halves the values each lane holds at every stage (9 shuffles for 8 rows; afterwards lane l
-// holds row (l >> 2) & 7).  Column products: FMAs over the warp's 16 rows, then the 8 warps
-// merged in order with TwoSum.  The sum over tiles (the second stage) is TwoSum-compensated.
+// one tile of one lane: the row products go to pbuf[J][rows of I] and the column products of
+// this thread's warp to s_colw (8 warps x kSymT, merged by the caller).  Warp w takes tile
+// rows 16 w .. 16 w + 15 in two passes of 8, lane l columns 4 l .. 4 l + 3.  Row products: the
+// four products of a lane summed with FMAs, then the 8 rows of a pass reduced over the 32
+// lanes by a butterfly that halves the values each lane holds at every stage (9 shuffles for
+// 8 rows; afterwards lane l holds row (l >> 2) & 7).  Column products: FMAs over the warp's
+// 16 rows.  u_J (this lane's four columns) and u_I (each pass's rows) are read straight from
+// the lane's input vector with the tile's loads.
 // (Measured on the 40-lane sweep: 128 x 128 tiles 18.98 s per step; 256 x 256 tiles 21.8 s,
 // too few work items once the small lanes are one tile each.)
-__device__ __forceinline__ void sym_tile_item(const SymLane& S, const LaneDev& L, int t, float* s_u,
-                                              float (*s_col)[kSymT], const Params& P)
+__device__ __forceinline__ void sym_tile_part(const SymLane& S, const LaneDev& L, int t, float (*s_colw)[kSymT],
+                                              const Params& P)
 {
     static_assert(kSymT == 128 && kThreads == 256, "the mapping below is written for 128 x 128 tiles");
     int I, J;
     sym_tile_ij(t, S.nb, I, J);
     const int ld = L.ld;
     const float* u = L.vec + (size_t)V_U * ld;
-    if (threadIdx.x < kSymT) s_u[threadIdx.x] = u[I * kSymT + threadIdx.x];
-    else s_u[threadIdx.x] = u[J * kSymT + threadIdx.x - kSymT];
-    __syncthreads();
-    const float* s_uI = s_u;
-    const float4 uj = reinterpret_cast<const float4*>(s_u + kSymT)[threadIdx.x & 31];
+    const float4 uj = reinterpret_cast<const float4*>(u + J * kSymT)[threadIdx.x & 31];
     const float4* tile = reinterpret_cast<const float4*>(S.Qsym + (size_t)t * kSymT * kSymT);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
@@ -239,6 +236,9 @@ __device__ __forceinline__ void sym_tile_item(const SymLane& S, const LaneDev& L
         float4 q[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) q[r] = ldg_stream(tile + (size_t)(r0 + r) * (kSymT / 4) + lane);
+        const float4 ui0 = reinterpret_cast<const float4*>(u + I * kSymT + r0)[0];
+        const float4 ui1 = reinterpret_cast<const float4*>(u + I * kSymT + r0)[1];
+        const float uis[8] = {ui0.x, ui0.y, ui0.z, ui0.w, ui1.x, ui1.y, ui1.z, ui1.w};
         float v[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
@@ -246,7 +246,7 @@ __device__ __forceinline__ void sym_tile_item(const SymLane& S, const LaneDev& L
             a = fmaf(q[r].y, uj.y, a);
             a = fmaf(q[r].z, uj.z, a);
             v[r] = fmaf(q[r].w, uj.w, a);
-            const float ui = s_uI[r0 + r];
+            const float ui = uis[r];
             c0 = fmaf(q[r].x, ui, c0);
             c1 = fmaf(q[r].y, ui, c1);
             c2 = fmaf(q[r].z, ui, c2);
@@ -278,24 +278,39 @@ __device__ __forceinline__ void sym_tile_item(const SymLane& S, const LaneDev& L
         v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
         if ((lane & 3) == 0) rowdst[r0 + ((lane >> 2) & 7)] = v[0];
     }
-    if (I != J) {
-        s_col[warp][4 * lane + 0] = c0;
-        s_col[warp][4 * lane + 1] = c1;
-        s_col[warp][4 * lane + 2] = c2;
-        s_col[warp][4 * lane + 3] = c3;
-        __syncthreads();
-        if (threadIdx.x < kSymT) {
-            float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) csum_add(acc, s_col[w][threadIdx.x]);
-            S.pbuf[(size_t)I * ld + J * kSymT + threadIdx.x] = acc.x + acc.y;
-        }
-    }
+    s_colw[warp][4 * lane + 0] = c0;
+    s_colw[warp][4 * lane + 1] = c1;
+    s_colw[warp][4 * lane + 2] = c2;
+    s_colw[warp][4 * lane + 3] = c3;
     if (P.bytes && threadIdx.x == 0) {
         // the tile's entries inside the matrix once, u_I and u_J, the partial vectors written
         const unsigned long long ri = (unsigned long long)min(kSymT, L.n - I * kSymT);
         const unsigned long long cj = (unsigned long long)min(kSymT, L.n - J * kSymT);
         atomicAdd(P.bytes, ri * cj * 4ull + 2ull * kSymT * 4ull + (I != J ? 2ull : 1ull) * kSymT * 4ull);
+    }
+}
+
+// one ring entry of the first stage: tiles kSymGroup g .. kSymGroup g + kSymGroup - 1 of a lane
+// (fewer at the end).  The column products of every tile off the diagonal are merged over the
+// 8 warps in order with TwoSum, after one barrier, by one 128-thread half of the CTA per tile.
+__device__ __forceinline__ void sym_group_item(const SymLane& S, const LaneDev& L, int g,
+                                               float (*s_col)[kWarps][kSymT], const Params& P)
+{
+    static_assert(kSymGroup * kSymT == kThreads, "one half of the CTA merges each tile's columns");
+    const int t0 = g * kSymGroup;
+#pragma unroll 1
+    for (int k = 0; k < kSymGroup && t0 + k < S.ntiles; ++k) sym_tile_part(S, L, t0 + k, s_col[k], P);
+    __syncthreads();
+    const int k = threadIdx.x / kSymT, c = threadIdx.x % kSymT;
+    if (t0 + k < S.ntiles) {
+        int I, J;
+        sym_tile_ij(t0 + k, S.nb, I, J);
+        if (I != J) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) csum_add(acc, s_col[k][w][c]);
+            S.pbuf[(size_t)I * L.ld + J * kSymT + c] = acc.x + acc.y;
+        }
     }
 }
 

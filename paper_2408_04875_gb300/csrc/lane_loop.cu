@@ -16,7 +16,7 @@
 // entry; every wait gives up after kLoopWaitNs, sets the error flag and ends the CTA.
 //
 // With symmetric storage (A.sym set) a step that multiplies by Q_off has two stages: one
-// entry per stored tile (entry block < kBlockFlag), whose products go to the lane's partial
+// entry per kSymGroup stored tiles (entry block < kBlockFlag), whose products go to the lane's partial
 // vectors, and then, pushed by the CTA that finished the lane's last tile, one entry per row
 // block (kBlockFlag | b) that sums the block's partials and runs the epilogue.  Evaluation
 // steps read the dense evaluation matrix and have row-block entries only.
@@ -115,8 +115,7 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
     __shared__ int s_last, s_npush;
     __shared__ unsigned s_pay;
     __shared__ __align__(16) LaneDev sL;   // the popped lane's descriptor
-    __shared__ __align__(16) float s_uIJ[2 * kSymT];   // u_I, u_J of a tile
-    __shared__ float s_col[kWarps][kSymT];
+    __shared__ float s_col[kSymGroup][kWarps][kSymT];
     static_assert(sizeof(LaneDev) % 8 == 0, "descriptor copied in 8-byte pieces");
     const unsigned long long cap = A.cap, mask = cap - 1;
 
@@ -158,12 +157,12 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
         if (A.sym && !(blk & kBlockFlag)) {
             // ---- symmetric storage, stage 1: one tile's row and column products
             const SymLane S = A.sym[lane_id];
-            sym_tile_item(S, L, blk, s_uIJ, s_col, A.P);
+            sym_group_item(S, L, blk, s_col, A.P);
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) {
                 s_npush = 0;
-                if (atomicAdd(S.counter, 1u) == (unsigned)(S.ntiles - 1)) {
+                if (atomicAdd(S.counter, 1u) == (unsigned)(S.ngroups - 1)) {
                     // the lane's last tile: its row blocks come next
                     *S.counter = 0u;
                     s_npush = S.nb;
@@ -218,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
                     // next step: dense row blocks, or with symmetric storage the tiles (the
                     // row blocks alone for an evaluation step)
                     const bool tiles = A.sym && L.st->phase != PH_EVAL;
-                    const int cnt = tiles ? A.sym[lane_id].ntiles : L.nblk;
+                    const int cnt = tiles ? A.sym[lane_id].ngroups : L.nblk;
                     s_npush = cnt;
                     s_pay = ((unsigned)lane_id << 16) | (A.sym && !tiles ? kBlockFlag : 0u);
                     s_base = atomicAdd(A.tail, (unsigned long long)cnt);

@@ -386,6 +386,7 @@ int gemv_grid(int max_ld, int nitems);
 cudaError_t launch_phase_a_gemv_f32(const TickArgs& a, cudaStream_t s);
 cudaError_t launch_phase_a_grad(const TickArgs& a, int dtype, int64_t n, cudaStream_t s);
 constexpr int kSymT = 128;   // tile edge of the symmetric storage
+constexpr int kSymGroup = 2; // tiles per first-stage ring entry
 
 // one lane's symmetric storage (persistent lane loop): the packed upper-triangle tiles of
 // its instance, its partial vectors (nb x ld floats) and the counter of its tiles this step
@@ -395,6 +396,7 @@ struct SymLane {
     unsigned int* counter;
     int32_t nb;                 // row blocks of kSymT rows
     int32_t ntiles;             // nb (nb + 1) / 2
+    int32_t ngroups;            // first-stage entries: ceil(ntiles / kSymGroup)
 };
 
 // persistent lane loop (GEMV lanes): a ring of (lane, row block) entries shared by all CTAs
