@@ -67,6 +67,19 @@ def _instances(rank: int, sizes=SIZES, seeds=SEEDS_PER_SIZE):
     return Qs, mus
 
 
+def aggregate_ranks(ms: float, work: float, dist, device: str):
+    """Whole-job figures of a multi-rank run: the slowest rank's time (the job ends with it)
+    and the work of all ranks.  `dist` is torch.distributed (or None for one rank); the
+    tensors live on `device` ("cuda" under NCCL, "cpu" under gloo)."""
+    import torch
+    ms_t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    work_t = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(work_t, op=dist.ReduceOp.SUM)
+    return float(ms_t.item()), float(work_t.item())
+
+
 class ClockSampler:
     """nvidia-smi samples during the timed region (clocks, power, throttle reasons)."""
 
@@ -358,15 +371,8 @@ def run_gpu(args):
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    work = sum(s["var_updates"] for s in stats)
-    work_t = torch.tensor([float(work)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(work_t)
-    value = float(work_t.item()) / (ms_max * 1e-3)
+    ms_max, work_all = aggregate_ranks(ms, sum(s["var_updates"] for s in stats), dist, "cuda")
+    value = work_all / (ms_max * 1e-3)
 
     # end to end through the public API with host buffers (H2D of Q and mu, D2H of x, f)
     st_e2e, e2e_s = None, None
