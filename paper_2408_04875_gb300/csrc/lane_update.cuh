@@ -257,7 +257,10 @@ static __device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, 
             D.usrc = U_DLW;
             break;
         }
-        // Sec. 3.4: alpha = eta * lambda_min, or the resolution floor (see the design doc reading)
+        // Sec. 3.4: alpha = eta * lambda_min.  The paper does not say what to do when
+        // lambda_min is not positive or is tiny; below the resolution floor F = c * delta * rho
+        // (the smallest curvature change the KKT test of Eq. (cret) can resolve) the step is
+        // eta * F * 2^m, m = consecutive steps taken at the floor
         float lam = lam_new;
         float F = P.lambda_floor_rel * P.tol_inner * S.rho;
         float alpha;
