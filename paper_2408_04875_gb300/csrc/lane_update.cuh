@@ -260,7 +260,7 @@ static __device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, 
         // Sec. 3.4: alpha = eta * lambda_min.  The paper does not say what to do when
         // lambda_min is not positive or is tiny; below the resolution floor F = c * delta * rho
         // (the smallest curvature change the KKT test of Eq. (cret) can resolve) the step is
-        // eta * F * 2^m, m = consecutive steps taken at the floor
+        // eta * F * 2^m, m = the floor steps taken in a row just before this one (at most 60)
         float lam = lam_new;
         float F = P.lambda_floor_rel * P.tol_inner * S.rho;
         float alpha;
