@@ -309,13 +309,13 @@ class Solver {
             L.stop_after = in.stop_after;
             L.restart = in.restart;
             L.trace_len = in.trace_len;
-            if (!tc) nitems += sym_ ? ((int64_t)I.nb * (I.nb + 1) / 2 + kSymGroup - 1) / kSymGroup : L.nblk;
             if (sym_) {
                 sym_host_[l].nb = I.nb;
                 sym_host_[l].ntiles = I.nb * (I.nb + 1) / 2;
                 sym_host_[l].ngroups = (sym_host_[l].ntiles + kSymGroup - 1) / kSymGroup;
                 o_pbuf_[l] = ar_.reserve((size_t)I.nb * I.ld * 4);
             }
+            if (!tc) nitems += sym_ ? sym_slots(sym_host_[l]) : L.nblk;
             o_vec_[l] = ar_.reserve((size_t)NVEC * I.ld * 4);
             o_bx_[l] = ar_.reserve((size_t)I.ld);
             o_part_[l] = ar_.reserve((size_t)L.nblk * sizeof(Partial));
@@ -578,7 +578,7 @@ class Solver {
             for (size_t l = 0; l < lanes.size(); ++l) order[l] = (int)l;
             std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lanes_[a].n > lanes_[b].n; });
             for (int l : order)
-                for (int b = 0; b < (sym_ ? sym_host_[l].ngroups : lanes_[l].nblk); ++b) items.push_back(make_int2(l, b));
+                for (int b = 0; b < (sym_ ? sym_slots(sym_host_[l]) : lanes_[l].nblk); ++b) items.push_back(make_int2(l, b));
         }
         if (sym_)
             UBQP_CK(cudaMemcpyAsync(ar_.at<SymLane>(o_symlanes_), sym_host_.data(), sym_host_.size() * sizeof(SymLane),

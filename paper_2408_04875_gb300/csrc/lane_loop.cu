@@ -60,8 +60,9 @@ __device__ __forceinline__ uint64_t loop_clock()
 
 // Seeds one launch (one CTA): budgets, the count of lanes with work, and the ring entries
 // of every lane's current step in the static item order (largest lanes first); finished
-// lanes keep their places as skip entries.  When no lane has work, one poison entry per
-// CTA follows so that the loop kernel ends at once.
+// lanes, and slots that a lane's current step does not use, keep their places as skip
+// entries.  When no lane has work, one poison entry per CTA follows so that the loop kernel
+// ends at once.
 __global__ void __launch_bounds__(1024) lane_loop_seed_kernel(LoopArgs A)
 {
     __shared__ int s_active;
@@ -86,9 +87,10 @@ __global__ void __launch_bounds__(1024) lane_loop_seed_kernel(LoopArgs A)
         const int ph = A.lanes[it.x].st->phase;
         bool act = ph != PH_DONE;
         unsigned blk = (unsigned)it.y;
-        if (A.sym && ph == PH_EVAL) {   // an evaluation step: row blocks only
-            act = it.y < A.sym[it.x].nb;
-            blk |= kBlockFlag;
+        if (A.sym && act) {   // a tile step, or an evaluation step (row blocks only)
+            const SymLane& S = A.sym[it.x];
+            act = it.y < (ph == PH_EVAL ? S.nb : S.ngroups);
+            if (ph == PH_EVAL) blk |= kBlockFlag;
         }
         const unsigned long long pos = base + (unsigned long long)e;
         const unsigned long long pay = act ? ((unsigned long long)it.x << 16) | blk

@@ -399,6 +399,11 @@ struct SymLane {
     int32_t ngroups;            // first-stage entries: ceil(ntiles / kSymGroup)
 };
 
+// seeded ring slots of one lane: its current step is either a tile step (ngroups entries) or
+// an evaluation step (nb row-block entries), so it gets the larger count and the seed skips
+// the slots its step does not use
+inline int sym_slots(const SymLane& S) { return S.ngroups > S.nb ? S.ngroups : S.nb; }
+
 // persistent lane loop (GEMV lanes): a ring of (lane, row block) entries shared by all CTAs
 struct LoopArgs {
     const LaneDev* lanes;
