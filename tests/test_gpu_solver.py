@@ -216,6 +216,23 @@ def test_lane_loop_small_budget_relaunches(ub):
     assert s3["gemv_kernel"] == 1                       # the per-step timeline runs lock-step
 
 
+def test_sym_lanes_of_every_block_count_reseeded(ub):
+    """Symmetric storage, lanes of 1 to 9 row blocks: relaunching the loop every 3 steps seeds
+    lanes in tile steps and in evaluation steps (row blocks only) again and again.  Same bits
+    as one long launch and as a lane solved alone."""
+    ns = [100, 200, 300, 450, 600, 700, 850, 1000, 1100]
+    Qs = [I.random_ubqp(n, 0.1, 20 + i)[0] for i, n in enumerate(ns)]
+    mus = [I.perturbation(Q, 20 + i) for i, Q in enumerate(Qs)]
+    kw = dict(gemv_kernel=2, sym_storage=1, max_outer=4)
+    x1, f1, s1 = ub.solve_batched(Qs, None, mus, **kw)
+    x2, f2, s2 = ub.solve_batched(Qs, None, mus, lane_budget=3, **kw)
+    assert s1["sym_storage"] == 1 and s2["sym_storage"] == 1
+    assert np.array_equal(f1, f2) and all(np.array_equal(a, b) for a, b in zip(x1, x2))
+    assert s1["ticks"] == s2["ticks"] and s2["kernel_launches"] > s1["kernel_launches"] + 100
+    x3, f3, _ = ub.solve(Qs[4], None, mu=mus[4], **kw)   # the 5-block lane alone
+    assert f3 == f1[4] and np.array_equal(x3, x1[4])
+
+
 def test_restarts_keep_best_and_are_exact(ub):
     Q, b = I.random_ubqp(80, 0.2, 9, b_range=(-20, 20))
     mu = I.perturbation(Q, 9)
