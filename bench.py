@@ -314,14 +314,17 @@ def run_reference(args):
     rank, world, _ = _env_rank()
     if rank != 0:
         return 0
-    steps = []
+    steps, ms = [], []
     for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
         b = cpu_baseline(budget_s=10.0)
         if i >= args.warmup:
             steps.append(b)
+            ms.append((time.perf_counter() - t0) * 1e3)
     value = statistics.mean(s["value"] for s in steps)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "impl": "reference", "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "impl": "reference",
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "reference_sample": steps[-1]["sample"]},
             "cpu_baseline": {"kind": "oracle", "cores": steps[-1]["cores"], "sample": steps[-1]["sample"],

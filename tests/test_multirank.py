@@ -58,3 +58,26 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = type("A", (), dict(gpus=2, steps=1, warmup=0))()
     assert bench.run_reference(args) == 0
     assert capsys.readouterr().out == ""      # no line, no work on rank 1
+
+
+def test_reference_arm_line_has_the_contract_keys(monkeypatch, capsys):
+    """Rank 0 prints one JSON line with the keys of the benchmark contract (a short oracle
+    sample per step here)."""
+    import json
+    import bench
+    orig = bench.cpu_baseline
+    monkeypatch.setattr(bench, "cpu_baseline", lambda budget_s=0.0, threads=None: orig(budget_s=0.2, threads=2))
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    args = type("A", (), dict(gpus=1, steps=1, warmup=1))()
+    assert bench.run_reference(args) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["ms_per_step"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 2
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert "workload" in line["config"]
