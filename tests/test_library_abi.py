@@ -83,3 +83,20 @@ def test_product_package_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "ubqp_oracle" not in txt, f
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library every entry point raises before computing anything: there
+    is no CPU fallback in the product path."""
+    import numpy as np
+    import paper_2408_04875_gb300 as ub
+    monkeypatch.setattr(ub, "LIB_PATH", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(ub, "_lib", None)
+    Q = np.eye(4)
+    x = np.full(4, 0.5)
+    calls = [lambda: ub.solve(Q), lambda: ub.solve_batched([Q]), lambda: ub.initial_point(Q),
+             lambda: ub.inner_run(Q, np.zeros(4), 1.0, x), lambda: ub.penalty_probe(Q, np.zeros(4), 1.0, x),
+             lambda: ub.opts()]
+    for call in calls:
+        with pytest.raises(RuntimeError, match="missing"):
+            call()
