@@ -65,33 +65,38 @@ def build(force: bool = False) -> str:
 def lib():
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(_SO)
-        L.orc_opts_default.argtypes = [C.POINTER(Opts)]
-        L.orc_objective.restype = C.c_double
-        L.orc_objective.argtypes = [C.c_int, _dp, C.c_void_p, _u8]
-        L.orc_reformulate.argtypes = [C.c_int, _dp, C.c_void_p, C.c_void_p, C.c_double, _dp, _dp, _dp]
-        L.orc_initial_point.restype = C.c_int
-        L.orc_initial_point.argtypes = [C.c_int, _dp, _dp, _dp]
-        L.orc_penalized.restype = C.c_double
-        L.orc_penalized.argtypes = [C.c_int, _dp, C.c_void_p, C.c_void_p, _dp, C.c_void_p]
-        L.orc_kkt_residual.restype = C.c_double
-        L.orc_kkt_residual.argtypes = [C.c_int, _dp, _dp]
-        L.orc_rho.restype = C.c_double
-        L.orc_rho.argtypes = [C.c_int, _dp, C.c_void_p, C.c_void_p]
-        L.orc_lambda_min.restype = C.c_double
-        L.orc_lambda_min.argtypes = [C.c_int, _dp]
-        L.orc_penalty_step.restype = C.c_double
-        L.orc_penalty_step.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.POINTER(Opts), C.c_int,
-                                       C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int)]
-        L.orc_inner.restype = C.c_int
-        L.orc_inner.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.POINTER(Opts), C.c_int,
-                                C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
-        L.orc_solve.restype = C.c_int
-        L.orc_solve.argtypes = [C.c_int, _dp, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
-                                _u8, C.POINTER(C.c_double), C.POINTER(Stats), C.c_void_p]
-        _lib = L
+        _lib = load(build())
     return _lib
+
+
+def load(path: str):
+    """Open a compiled oracle at ``path`` and declare its entry points (the tests also
+    load copies of the oracle with planted mistakes this way)."""
+    L = C.CDLL(path)
+    L.orc_opts_default.argtypes = [C.POINTER(Opts)]
+    L.orc_objective.restype = C.c_double
+    L.orc_objective.argtypes = [C.c_int, _dp, C.c_void_p, _u8]
+    L.orc_reformulate.argtypes = [C.c_int, _dp, C.c_void_p, C.c_void_p, C.c_double, _dp, _dp, _dp]
+    L.orc_initial_point.restype = C.c_int
+    L.orc_initial_point.argtypes = [C.c_int, _dp, _dp, _dp]
+    L.orc_penalized.restype = C.c_double
+    L.orc_penalized.argtypes = [C.c_int, _dp, C.c_void_p, C.c_void_p, _dp, C.c_void_p]
+    L.orc_kkt_residual.restype = C.c_double
+    L.orc_kkt_residual.argtypes = [C.c_int, _dp, _dp]
+    L.orc_rho.restype = C.c_double
+    L.orc_rho.argtypes = [C.c_int, _dp, C.c_void_p, C.c_void_p]
+    L.orc_lambda_min.restype = C.c_double
+    L.orc_lambda_min.argtypes = [C.c_int, _dp]
+    L.orc_penalty_step.restype = C.c_double
+    L.orc_penalty_step.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.POINTER(Opts), C.c_int,
+                                   C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.orc_inner.restype = C.c_int
+    L.orc_inner.argtypes = [C.c_int, _dp, _dp, _dp, _dp, C.POINTER(Opts), C.c_int,
+                            C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int)]
+    L.orc_solve.restype = C.c_int
+    L.orc_solve.argtypes = [C.c_int, _dp, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Opts),
+                            _u8, C.POINTER(C.c_double), C.POINTER(Stats), C.c_void_p, _dp]
+    return L
 
 
 def _c(a, dtype=np.float64):
@@ -194,7 +199,8 @@ def inner(Qp, bp, p, x0, o: Opts | None = None, trace_len: int = 0):
 
 
 def solve(Q, b=None, mu=None, x_start=None, o: Opts | None = None):
-    """Alg. 3 in FP64.  Returns (x_best uint8, f_best, stats dict)."""
+    """Alg. 3 in FP64.  Returns (x_best uint8, f_best, stats dict); the stats hold the
+    inner step counts (``inner_hist``) and the last penalty vector (``p``)."""
     o = o or opts()
     Q = _c(Q)
     n = Q.shape[0]
@@ -205,8 +211,10 @@ def solve(Q, b=None, mu=None, x_start=None, o: Opts | None = None):
     f = C.c_double(0.0)
     st = Stats()
     hist = np.zeros(max(o.max_outer, 1) + 1, np.int32)
+    p = np.zeros(n)
     lib().orc_solve(n, Q, _ptr(b), _ptr(mu), _ptr(xs), C.byref(o), xb, C.byref(f), C.byref(st),
-                    _ptr(hist))
+                    _ptr(hist), p)
     stats = {k: getattr(st, k) for k, _ in Stats._fields_}
     stats["inner_hist"] = hist[: st.outer].copy()
+    stats["p"] = p
     return xb, f.value, stats

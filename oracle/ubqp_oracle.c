@@ -359,7 +359,8 @@ static double binarity(int n, const double* x)
  * followed by a subproblem solve, until x is binary; the best rounded point is kept
  * (Sec. 3.4: "the best value of x"). */
 int orc_solve(int n, const double* Q, const double* b, const double* mu, const double* x_start,
-              const orc_opts* o, uint8_t* x_best, double* f_best, orc_stats* st, int* inner_hist)
+              const orc_opts* o, uint8_t* x_best, double* f_best, orc_stats* st, int* inner_hist,
+              double* p_out)
 {
     memset(st, 0, sizeof(*st));
     if (n <= 0) { st->status = -1; return -1; }
@@ -407,6 +408,7 @@ int orc_solve(int n, const double* Q, const double* b, const double* mu, const d
     st->outer = s;
     st->final_binarity = binarity(n, x);
     *f_best = best;
+    if (p_out) memcpy(p_out, p, (size_t)n * sizeof(double));
     free(Qp); free(bp); free(gam); free(x); free(p); free(xr);
     return st->status;
 }

@@ -106,9 +106,11 @@ int orc_inner(int n, const double* Qp, const double* bp, const double* p, double
  * symmetric perturbation (may be NULL).  x_start (may be NULL) replaces the x^0 of
  * Eq. (gamma) as the first iterate.  Writes the best rounded point and its exact
  * objective.  inner_hist (may be NULL, length >= max_outer) receives the inner step
- * count of every subproblem. */
+ * count of every subproblem; p_out (may be NULL, length n) the penalty vector p of the
+ * last subproblem. */
 int orc_solve(int n, const double* Q, const double* b, const double* mu, const double* x_start,
-              const orc_opts* o, uint8_t* x_best, double* f_best, orc_stats* st, int* inner_hist);
+              const orc_opts* o, uint8_t* x_best, double* f_best, orc_stats* st, int* inner_hist,
+              double* p_out);
 
 #ifdef __cplusplus
 }

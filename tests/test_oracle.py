@@ -53,6 +53,19 @@ def test_reformulation_leaves_binary_objective_unchanged():
     assert f1 == f2 and np.array_equal(x1, x2)
 
 
+def test_reformulation_with_perturbation_is_the_perturbed_objective():
+    """Sec. 3.5: the shift Diag(gamma) cancels against b' = b - gamma on binary points while
+    the perturbation stays: x'Q'x + b''x = f(x) + x'mu x for every binary x."""
+    Q, b = _small(16, 3)
+    mu = I.perturbation(Q, 3)
+    Qp, bp, _ = O.reformulate(Q, b, mu)
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        x = rng.integers(0, 2, 16).astype(np.uint8)
+        xf = x.astype(np.float64)
+        assert O.objective(Qp, bp, x) == pytest.approx(O.objective(Q, b, x) + xf @ mu @ xf, abs=1e-9)
+
+
 # ---- h and its gradient ----------------------------------------------------------
 
 def test_gradient_matches_central_differences():
@@ -98,6 +111,7 @@ def test_rho_hand_example():
     assert O.rho(Q, np.array([0.0, 0.0]), np.array([0.0, 0.0])) == 14.0
     assert O.rho(Q, np.array([30.0, 0.0]), np.array([0.0, 0.0])) == 30.0
     assert O.rho(Q, np.array([0.0, 0.0]), np.array([-20.0, 0.0])) == 44.0   # |2(2+20)|
+    assert O.rho(Q, np.array([30.0, 0.0]), np.array([25.0, 0.0])) == 55.0   # |30+25| > |2(2-25)|
     assert O.rho(np.zeros((1, 1)), np.zeros(1), np.zeros(1)) == 1.0
 
 
@@ -150,7 +164,93 @@ def test_penalty_step_first_outer_step_positive():
     assert lam == pytest.approx(ref, rel=1e-10) and a == pytest.approx(0.9 * ref, rel=1e-10)
 
 
+def test_penalty_step_with_penalty_and_boundary_coordinates():
+    """Eq. (eq:alpha): lambda_min of Z^-1/2 (Q' - P*)_II Z^-1/2 over the interior set I only;
+    coordinates at 0 or 1 drop out, and the current penalty enters the matrix."""
+    Q, b = I.random_ubqp(40, 0.2, 3)
+    Qp, bp, _ = O.reformulate(Q, b, I.perturbation(Q, 3))
+    x = O.initial_point(Qp, bp)
+    x[0], x[1] = 0.0, 1.0
+    p = 0.2 * np.diag(Qp)
+    a, m, lam, fb = O.penalty_step(Qp, bp, p, x)
+    z = (x - x ** 2)[2:]
+    Qb = (Qp - np.diag(p))[2:, 2:]
+    ref = np.linalg.eigvalsh(Qb / np.sqrt(np.outer(z, z)))[0]
+    assert m == 38 and not fb
+    assert lam == pytest.approx(ref, rel=1e-10) and a == pytest.approx(0.9 * ref, rel=1e-10)
+
+
+def test_penalty_floor_doubles_per_consecutive_step():
+    """The floor reading: with no usable curvature (lambda_min < 0 here, checked against the
+    library) the step is positive, doubles for every consecutive floor step, and stops
+    doubling after 60."""
+    Q, b = I.random_ubqp(30, 0.3, 5)
+    Qp, bp, _ = O.reformulate(Q, b, None)
+    x = O.initial_point(Qp, bp)
+    p = 3.0 * np.diag(Qp)
+    z = x - x ** 2
+    ref = np.linalg.eigvalsh((Qp - np.diag(p)) / np.sqrt(np.outer(z, z)))[0]
+    a0, _, lam, fb = O.penalty_step(Qp, bp, p, x)
+    assert ref < 0 and lam == pytest.approx(ref, rel=1e-10) and fb and a0 > 0
+    for c in range(1, 6):
+        a, _, _, fbc = O.penalty_step(Qp, bp, p, x, consecutive=c)
+        assert fbc and a == a0 * 2 ** c
+    assert O.penalty_step(Qp, bp, p, x, consecutive=61)[0] == O.penalty_step(Qp, bp, p, x, consecutive=60)[0]
+
+
+def test_penalty_update_shrinks_scaled_curvature_by_one_minus_eta():
+    """Lemma 3.1 with Eq. (pp1): after p <- p + alpha z with alpha = eta lambda_min, the
+    matrix Z^-1/2 (Q' - P*) Z^-1/2 is the old one shifted by -alpha I, so its smallest
+    eigenvalue is (1 - eta) times the old one (library eigenvalues, one outer step)."""
+    Q, b = I.random_ubqp(40, 0.2, 6)
+    mu = I.perturbation(Q, 6)
+    Qp, bp, _ = O.reformulate(Q, b, mu)
+    x0 = O.initial_point(Qp, bp)
+    _, _, st = O.solve(Q, b, mu, o=O.opts(max_outer=1))
+    assert st["outer"] == 1
+    p = st["p"]
+    S = 1.0 / np.sqrt(np.outer(x0 - x0 ** 2, x0 - x0 ** 2))
+    lam0 = np.linalg.eigvalsh(Qp * S)[0]
+    lam1 = np.linalg.eigvalsh((Qp - np.diag(p)) * S)[0]
+    assert lam0 > 0 and lam1 == pytest.approx(0.1 * lam0, rel=1e-9)
+
+
 # ---- Alg. 2 / Alg. 1 ---------------------------------------------------------------
+
+def _equal_curvature_case(n=6, c=3.0, seed=12):
+    """Q' = Diag(d), p = d - c: every coordinate has curvature c; the box minimiser of
+    h(., p) is clip(t) with t drawn first and b' chosen to make it so."""
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(5, 10, n)
+    p = d - c
+    t = rng.uniform(-0.4, 1.4, n)
+    bp = -2 * c * t - p
+    return np.diag(d), bp, p, np.clip(t, 0, 1), rng.uniform(0.2, 0.8, n)
+
+
+def test_pabb_first_step_is_the_newton_step_at_equal_curvature():
+    """Alg. 2: alpha_0 = 1 / (2 ||Q' - P*||_inf); when every coordinate has the same
+    curvature c that is 1 / (2c), the Newton step, so the first projected step lands on
+    the box minimiser and the KKT test stops the loop."""
+    Qp, bp, p, xs, x0 = _equal_curvature_case()
+    r = O.inner(Qp, bp, p, x0, trace_len=3)
+    assert r["steps"] == 1 and r["exit"] == 0
+    assert np.max(np.abs(r["x"] - xs)) <= 1e-13
+
+
+def test_ppa_step_is_exact_on_a_diagonal_problem():
+    """Alg. 1 with h_p of Sec. 3.1: for diagonal Q' > P* the proximal weight h_p = Q'_ii - p_i
+    equals the curvature, so one step reaches the box minimiser."""
+    rng = np.random.default_rng(13)
+    n = 8
+    d = rng.uniform(2, 9, n)
+    p = rng.uniform(0, 0.5, n) * d
+    t = rng.uniform(-0.5, 1.5, n)
+    bp = -2 * (d - p) * t - p
+    r = O.inner(np.diag(d), bp, p, rng.uniform(0.2, 0.8, n), O.opts(method=1))
+    assert r["steps"] == 1 and r["exit"] == 0
+    assert np.max(np.abs(r["x"] - np.clip(t, 0, 1))) <= 1e-13
+
 
 def test_pabb_separable_case_reaches_closed_form():
     """Q_off = 0: h is separable and strictly convex on the box when Q_ii - p_i > 0;
