@@ -1,0 +1,78 @@
+"""The tile-index arithmetic of the symmetric storage on the CPU.
+
+``sym_tile_ij`` maps a packed tile number t to its block pair (I, J), I <= J, in the
+row-by-row packing of an nb x nb upper triangle; the lane loop uses it for every tile it
+reads.  The test takes the function's text from the kernel source as it stands, compiles it
+with g++ (the CUDA qualifiers defined away), and checks every t of every nb the symmetric
+storage accepts (nb (nb + 1) / 2 < 2^15, so nb <= 255) against the enumeration of the
+packing.  The device may contract b2 * b2 - 8 t into one fused multiply-add, so a second
+build spells that contraction out; the function's correction loops must make both exact.
+"""
+import pathlib
+import re
+import subprocess
+
+import pytest
+
+SRC = pathlib.Path(__file__).resolve().parent.parent / "paper_2408_04875_gb300" / "csrc" / "gemv_rows.cuh"
+
+HARNESS = r"""
+#include <cmath>
+#include <cstdio>
+#include <algorithm>
+using std::max;
+using std::min;
+#define __device__
+#define __forceinline__ inline
+%s
+int main()
+{
+    long bad = 0, checked = 0;
+    for (int nb = 1; nb <= 255; ++nb) {
+        int t = 0;
+        for (int i = 0; i < nb; ++i)
+            for (int j = i; j < nb; ++j, ++t) {
+                int I = -1, J = -1;
+                sym_tile_ij(t, nb, I, J);
+                ++checked;
+                if (I != i || J != j) {
+                    if (bad < 5) std::printf("nb=%%d t=%%d -> (%%d,%%d), want (%%d,%%d)\n", nb, t, I, J, i, j);
+                    ++bad;
+                }
+            }
+    }
+    std::printf("checked %%ld bad %%ld\n", checked, bad);
+    return bad != 0;
+}
+"""
+
+
+def _function_text() -> str:
+    text = SRC.read_text()
+    m = re.search(r"__device__ __forceinline__ void sym_tile_ij\(.*?\n}\n", text, re.S)
+    assert m, "sym_tile_ij not found in the kernel source"
+    return m.group(0)
+
+
+@pytest.mark.parametrize("fused", [False, True], ids=["plain", "fma"])
+def test_sym_tile_ij_matches_the_packing(tmp_path, fused):
+    fn = _function_text()
+    if fused:
+        expr = "b2 * b2 - 8.f * (float)t"
+        assert fn.count(expr) == 1
+        fn = fn.replace(expr, "std::fma(b2, b2, -8.f * (float)t)")
+    src = tmp_path / "tile_ij.cpp"
+    src.write_text(HARNESS % fn)
+    exe = tmp_path / "tile_ij"
+    subprocess.run(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-o", str(exe), str(src)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout
+    assert "checked 2796160 bad 0" in r.stdout, r.stdout
+
+
+def test_engine_limits_symmetric_storage_to_the_checked_range():
+    """The engine turns symmetric storage off once nb (nb + 1) / 2 reaches 2^15 (the ring
+    entry's block field), so nb = 1 .. 255 above covers every instance that uses it."""
+    engine = (SRC.parent / "engine.cu").read_text()
+    assert "if (nb * (nb + 1) / 2 >= 0x8000) sym_ = false;" in engine
+    assert 255 * 256 // 2 < 0x8000 <= 256 * 257 // 2
