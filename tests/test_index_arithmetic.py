@@ -1,5 +1,6 @@
-"""The tile-index arithmetic of the symmetric storage on the CPU.
+"""Index arithmetic of the kernels, checked on the CPU from the kernel source as it stands.
 
+Symmetric storage.
 ``sym_tile_ij`` maps a packed tile number t to its block pair (I, J), I <= J, in the
 row-by-row packing of an nb x nb upper triangle; the lane loop uses it for every tile it
 reads.  The test takes the function's text from the kernel source as it stands, compiles it
@@ -7,11 +8,17 @@ with g++ (the CUDA qualifiers defined away), and checks every t of every nb the 
 storage accepts (nb (nb + 1) / 2 < 2^15, so nb <= 255) against the enumeration of the
 packing.  The device may contract b2 * b2 - 8 t into one fused multiply-add, so a second
 build spells that contraction out; the function's correction loops must make both exact.
+
+Tensor-core layout.  ``qbf_index`` places the BF16 matrix in 128 x 64 tiles; it must be a
+bijection onto [0, ld^2) in which tile (M tile, k-block) is one contiguous run of 8192
+elements at position M tile * (ld / 64) + k-block, so that one TMA box of the
+(ld^2 / 64) x 64 view is one contiguous 16 KB copy.
 """
 import pathlib
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 SRC = pathlib.Path(__file__).resolve().parent.parent / "paper_2408_04875_gb300" / "csrc" / "gemv_rows.cuh"
@@ -76,3 +83,26 @@ def test_engine_limits_symmetric_storage_to_the_checked_range():
     engine = (SRC.parent / "engine.cu").read_text()
     assert "if (nb * (nb + 1) / 2 >= 0x8000) sym_ = false;" in engine
     assert 255 * 256 // 2 < 0x8000 <= 256 * 257 // 2
+
+
+def _qbf_index_py():
+    """qbf_index's body, taken from the source and evaluated with numpy integer arrays."""
+    text = (SRC.parent / "ubqp_engine.cuh").read_text()
+    m = re.search(r"size_t qbf_index\(size_t i, size_t j, size_t ld\)\s*\{\s*return (.*?);\s*\}", text, re.S)
+    assert m, "qbf_index not found"
+    expr = m.group(1)
+    return lambda i, j, ld: eval(expr, {}, {"i": i, "j": j, "ld": ld})
+
+
+@pytest.mark.parametrize("ld", [128, 256, 640, 2560])
+def test_qbf_index_is_a_tiled_bijection(ld):
+    f = _qbf_index_py()
+    i, j = np.meshgrid(np.arange(ld, dtype=np.uint64), np.arange(ld, dtype=np.uint64), indexing="ij")
+    idx = f(i, j, np.uint64(ld))
+    assert np.array_equal(np.sort(idx.ravel()), np.arange(ld * ld, dtype=np.uint64))
+    for M in range(ld // 128):
+        for K in range(ld // 64):
+            tile = idx[M * 128:(M + 1) * 128, K * 64:(K + 1) * 64]
+            base = (M * (ld // 64) + K) * 8192
+            # rows of 64 entries, one after the other, from the tile's base
+            assert np.array_equal(tile, base + np.arange(8192, dtype=np.uint64).reshape(128, 64))
