@@ -100,3 +100,35 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     for call in calls:
         with pytest.raises(RuntimeError, match="missing"):
             call()
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(method=7), "method"), (dict(max_outer=-1), "max_outer"), (dict(max_inner=-1), "max_inner"),
+    (dict(eta=0.0), "eta"), (dict(eta=1.0), "eta"), (dict(eta=float("nan")), "eta"),
+    (dict(tol_inner=0.0), "tolerances"), (dict(tol_outer=-1.0), "tolerances"),
+    (dict(alpha_min=0.0), "clamp"), (dict(alpha_min=2.0, alpha_max=1.0), "clamp"),
+    (dict(restarts=-1), "restarts"), (dict(restarts=4097), "restarts"),
+    (dict(precision=9), "precision"), (dict(lobpcg_max_iter=0), "iteration caps"),
+    (dict(jacobi_max_iter=0), "iteration caps"), (dict(max_ticks_per_sync=0), "max_ticks_per_sync"),
+    (dict(max_ticks_per_sync=4097), "max_ticks_per_sync"), (dict(sigma_rel=-1.0), "sigma_rel"),
+    (dict(gamma_margin=0.0), "gamma_margin"), (dict(tc_cluster=9), "tc_cluster"),
+    (dict(gemv_kernel=3), "gemv_kernel"), (dict(lane_budget=-1), "lane_budget"),
+    (dict(rows_per_item=12), "rows_per_item"), (dict(rows_per_item=4), "rows_per_item"),
+    (dict(rows_per_item=264), "rows_per_item"),
+])
+def test_invalid_options_are_rejected_before_any_cuda_call(built, kw, msg):
+    """Every option outside its documented range returns UBQP_EINVAL with a message naming
+    it, before the library touches the device (so this runs without a GPU)."""
+    import numpy as np
+    import paper_2408_04875_gb300 as ub
+    with pytest.raises(ub.UBQPError) as e:
+        ub.solve(np.eye(3), **kw)
+    assert e.value.status == -1 and msg in str(e.value)
+
+
+def test_restart_tuner_with_caller_starts_is_rejected_without_gpu(built):
+    import numpy as np
+    import paper_2408_04875_gb300 as ub
+    with pytest.raises(ub.UBQPError) as e:
+        ub.solve(np.eye(3), starts=np.full((2, 3), 0.5), restarts=0)
+    assert e.value.status == -1 and "tuner" in str(e.value)
