@@ -132,3 +132,31 @@ def test_restart_tuner_with_caller_starts_is_rejected_without_gpu(built):
     with pytest.raises(ub.UBQPError) as e:
         ub.solve(np.eye(3), starts=np.full((2, 3), 0.5), restarts=0)
     assert e.value.status == -1 and "tuner" in str(e.value)
+
+
+def _solve_batched_raw(L, num, ns, q_null=False, x_null=False, obj_null=False):
+    import numpy as np
+    n = np.array(ns if ns else [1], np.int64)
+    qs = [np.zeros(max(k, 1) ** 2) for k in n]
+    xs = [np.zeros(max(k, 1), np.uint8) for k in n]
+    qp = (C.c_void_p * len(n))(*[None if q_null else q.ctypes.data for q in qs])
+    xp = (C.c_void_p * len(n))(*[x.ctypes.data for x in xs])
+    obj = np.zeros(len(n))
+    return L.ubqp_solve_batched(num, n.ctypes.data, C.cast(qp, C.c_void_p), None, None,
+                                None if x_null else C.cast(xp, C.c_void_p), None if obj_null else obj.ctypes.data)
+
+
+@pytest.mark.parametrize("case,msg", [
+    (dict(num=0, ns=[]), b"num >= 1"),
+    (dict(num=1, ns=[65537]), b"n = 65537 out of [1, 65536]"),
+    (dict(num=1, ns=[-3]), b"n = -3 out of"),
+    (dict(num=2, ns=[4, 0]), b"instance 1: n = 0 out of"),
+    (dict(num=1, ns=[4], q_null=True), b"null Q or x_out"),
+    (dict(num=1, ns=[4], x_null=True), b"non-null n, Q, x_out, obj_out"),
+    (dict(num=1, ns=[4], obj_null=True), b"non-null n, Q, x_out, obj_out"),
+])
+def test_sizes_and_null_pointers_rejected_without_gpu(built, case, msg):
+    import paper_2408_04875_gb300 as ub
+    L = ub.lib()
+    assert _solve_batched_raw(L, **case) == -1
+    assert msg in L.ubqp_last_error()
