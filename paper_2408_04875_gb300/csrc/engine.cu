@@ -58,6 +58,26 @@ static bool is_device_ptr(const void* p)
 
 static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// a stream-ordered temporary that is freed on every early return; the success path frees
+// it itself and then calls release()
+struct AsyncTemp {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    AsyncTemp() = default;
+    AsyncTemp(const AsyncTemp&) = delete;
+    AsyncTemp& operator=(const AsyncTemp&) = delete;
+    ~AsyncTemp()
+    {
+        if (p) cudaFreeAsync(p, s);
+    }
+    void hold(void* ptr, cudaStream_t stream)
+    {
+        p = ptr;
+        s = stream;
+    }
+    void release() { p = nullptr; }
+};
+
 // one device allocation carved into 256-byte aligned pieces
 class Arena {
   public:
@@ -714,6 +734,7 @@ class Solver {
         const bool timeline = o_.profile_kernels >= 2;
         unsigned long long* d_work_ctr = tc_ ? ar_.at<unsigned long long>(o_flops_) : ar_.at<unsigned long long>(o_bytes_);
         unsigned long long* d_snap = nullptr;
+        AsyncTemp snap_guard;
         if (prof && has_a) {
             evA_.resize(2 * T);
             for (auto& e : evA_) UBQP_CK(cudaEventCreate(&e));
@@ -721,6 +742,7 @@ class Solver {
                 g_tl_ms.clear();
                 g_tl_work.clear();
                 UBQP_CK(cudaMallocAsync((void**)&d_snap, (size_t)T * sizeof(unsigned long long), stream_));
+                snap_guard.hold(d_snap, stream_);
             }
         }
 
@@ -820,7 +842,10 @@ class Solver {
             }
         }
         UBQP_CK(cudaEventRecord(ev1_, stream_));
-        if (d_snap) UBQP_CK(cudaFreeAsync(d_snap, stream_));
+        if (d_snap) {
+            snap_guard.release();
+            UBQP_CK(cudaFreeAsync(d_snap, stream_));
+        }
         UBQP_CK(cudaStreamSynchronize(stream_));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0_, ev1_);
@@ -1044,11 +1069,16 @@ class Solver {
         bool host = !is_device_ptr(out_dev_or_host);
         double* dst = out_dev_or_host;
         double* tmp = nullptr;
-        if (host) UBQP_CK(cudaMallocAsync((void**)&tmp, (size_t)n * 8, stream_));
-        if (host) dst = tmp;
+        AsyncTemp guard;
+        if (host) {
+            UBQP_CK(cudaMallocAsync((void**)&tmp, (size_t)n * 8, stream_));
+            guard.hold(tmp, stream_);
+            dst = tmp;
+        }
         UBQP_CK(launch_lane_vec_to_f64(ar_.at<LaneDev>(o_lanes_), lane, v, n, dst, stream_));
         if (host) {
             UBQP_CK(cudaMemcpyAsync(out_dev_or_host, tmp, (size_t)n * 8, cudaMemcpyDeviceToHost, stream_));
+            guard.release();
             UBQP_CK(cudaFreeAsync(tmp, stream_));
         }
         UBQP_CK(cudaStreamSynchronize(stream_));
@@ -1063,13 +1093,16 @@ class Solver {
             bool host = !is_device_ptr(dst);
             double* d = dst;
             double* tmp = nullptr;
+            AsyncTemp guard;
             if (host) {
                 UBQP_CK(cudaMallocAsync((void**)&tmp, (size_t)cnt * 8, stream_));
+                guard.hold(tmp, stream_);
                 d = tmp;
             }
             UBQP_CK(launch_trace_to_f64(src, d, cnt, stream_));
             if (host) {
                 UBQP_CK(cudaMemcpyAsync(dst, tmp, (size_t)cnt * 8, cudaMemcpyDeviceToHost, stream_));
+                guard.release();
                 UBQP_CK(cudaFreeAsync(tmp, stream_));
             }
             UBQP_CK(cudaStreamSynchronize(stream_));
