@@ -58,8 +58,11 @@ class Deadlock(Exception):
 
 
 class Loop:
-    def __init__(self, lanes, grid, budget, old_rule, rng, cap_factor=2):
+    def __init__(self, lanes, grid, budget, old_rule, rng, cap_factor=2, pop_ahead=False,
+                 ahead_on_poison=False):
         self.lanes, self.G, self.B, self.rng = lanes, grid, budget, rng
+        self.pop_ahead = pop_ahead     # reserve the next position before processing an entry
+        self.ahead_on_poison = ahead_on_poison
         self.items = [(l, b) for l, L in enumerate(lanes) for b in range(L.slots(old_rule))]
         cap = 1
         while cap < cap_factor * (len(self.items) + grid):
@@ -107,6 +110,7 @@ class Loop:
         while True:
             live = [c for c in ctas if c["state"] != "exit"]
             if not live:
+                assert self.head == self.tail, "a launch ended with reserved but unwritten positions"
                 return
             ready = [c for c in live if c["out"] or c["state"] == "pop" or self.readable(c["pos"])]
             if not ready:
@@ -132,7 +136,13 @@ class Loop:
         c["state"] = "pop"
         if lane == POISON:
             c["state"] = "exit"
-        elif lane != SKIP:
+            if self.pop_ahead and self.ahead_on_poison:
+                self.head += 1                         # a reservation nobody will read
+            return
+        if self.pop_ahead:                             # the next position, before the work
+            c["pos"], self.head = self.head, self.head + 1
+            c["state"] = "wait"
+        if lane != SKIP:
             c["out"] = self.process(lane, blk)
 
     def process(self, l, blk):
@@ -179,12 +189,16 @@ def _random_lanes(rng, sym, group):
     return lanes
 
 
+@pytest.mark.parametrize("pop_ahead", [False, True], ids=["pop", "pop_ahead"])
 @pytest.mark.parametrize("sym,group", [(False, 2), (True, 2), (True, 4), (True, 1)])
-def test_random_lane_mixes_never_deadlock_or_overrun(sym, group):
-    rng = random.Random(1000 * group + sym)
+def test_random_lane_mixes_never_deadlock_or_overrun(sym, group, pop_ahead):
+    """pop_ahead: a CTA reserves its next position right after reading a (non-poison) entry
+    and before processing it, so that the reservation's latency overlaps the work."""
+    rng = random.Random(1000 * group + sym + 7 * pop_ahead)
     for trial in range(150):
         lanes = _random_lanes(rng, sym, group)
-        loop = Loop(lanes, grid=rng.randint(1, 8), budget=rng.choice([1, 2, 3, 5, 1024]), old_rule=False, rng=rng)
+        loop = Loop(lanes, grid=rng.randint(1, 8), budget=rng.choice([1, 2, 3, 5, 1024]), old_rule=False, rng=rng,
+                    pop_ahead=pop_ahead)
         loop.run()
         assert all(L.step == len(L.kinds) for L in lanes)
         assert all(L.c1 == 0 and L.c2 == 0 for L in lanes)
@@ -209,3 +223,12 @@ def test_a_ring_below_the_bound_is_caught_overrunning():
     lanes = [Lane(rng.randint(3, 9), ["T", "E"] * 4, True, 2) for _ in range(6)]
     with pytest.raises(AssertionError, match="overwritten"):
         Loop(lanes, grid=4, budget=3, old_rule=False, rng=rng, cap_factor=0.5).run()
+
+
+def test_pop_ahead_must_not_reserve_past_its_poison():
+    """A CTA that also reserved ahead on its poison entry would leave a reserved position
+    with no reader, and the next launch's entry there would never be popped."""
+    rng = random.Random(9)
+    lanes = [Lane(3, ["T", "E", "T", "T"], True, 2), Lane(5, ["E", "T"], True, 2)]
+    with pytest.raises(AssertionError, match="reserved but unwritten"):
+        Loop(lanes, grid=3, budget=2, old_rule=False, rng=rng, pop_ahead=True, ahead_on_poison=True).run()
