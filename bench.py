@@ -269,6 +269,20 @@ def run_c5(args):
     return 0
 
 
+def _cpu_model() -> str:
+    """The host CPU's model name as lscpu prints it (the machine architecture if lscpu is
+    missing or says nothing)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def cpu_baseline(budget_s: float = 12.0, threads: int | None = None):
     """The FP64 oracle as it stands, on a bounded sample of the same workload: whole solves of
     the n = 250 instances of the sweep (taken in turn, again from the first when all ten have
@@ -305,7 +319,7 @@ def cpu_baseline(budget_s: float = 12.0, threads: int | None = None):
         for f in [ex.submit(worker) for _ in range(threads)]:
             f.result()
     dt = time.perf_counter() - t0
-    return {"value": state["work"] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    return {"value": state["work"] / dt, "unit": UNIT, "cores": threads, "cpu_model": _cpu_model(), "kind": "oracle",
             "sample": f"{state['done']} whole solves of the 10 n=250 instances of the sweep (in turn), "
                       f"{threads} threads, {dt:.1f} s"}
 
@@ -327,8 +341,8 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "reference_sample": steps[-1]["sample"]},
-            "cpu_baseline": {"kind": "oracle", "cores": steps[-1]["cores"], "sample": steps[-1]["sample"],
-                             "value": value, "unit": UNIT},
+            "cpu_baseline": {"kind": "oracle", "cores": steps[-1]["cores"], "cpu_model": steps[-1]["cpu_model"],
+                             "sample": steps[-1]["sample"], "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0

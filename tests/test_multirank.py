@@ -79,5 +79,6 @@ def test_reference_arm_line_has_the_contract_keys(monkeypatch, capsys):
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0 and line["ms_per_step"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 2
+    assert isinstance(line["cpu_baseline"]["cpu_model"], str) and line["cpu_baseline"]["cpu_model"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert "workload" in line["config"]
