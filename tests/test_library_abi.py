@@ -160,3 +160,30 @@ def test_sizes_and_null_pointers_rejected_without_gpu(built, case, msg):
     L = ub.lib()
     assert _solve_batched_raw(L, **case) == -1
     assert msg in L.ubqp_last_error()
+
+
+def test_last_error_is_per_thread(built):
+    """ubqp_last_error is thread-local: an error on one thread is not seen on another."""
+    import threading
+    import numpy as np
+    import paper_2408_04875_gb300 as ub
+    L = ub.lib()
+    seen = {}
+
+    def fail():
+        try:
+            ub.solve(np.eye(3), eta=2.0)
+        except ub.UBQPError:
+            pass
+        seen["a"] = L.ubqp_last_error()
+
+    def fresh():
+        seen["b"] = L.ubqp_last_error()
+
+    ta = threading.Thread(target=fail)
+    ta.start()
+    ta.join()
+    tb = threading.Thread(target=fresh)
+    tb.start()
+    tb.join()
+    assert b"eta" in seen["a"] and seen["b"] == b""
