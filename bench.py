@@ -186,7 +186,8 @@ def run_c4(args):
                                                      if stats[-1]["ms_to_target"] > 0 else None),
                        "ticks_per_step": stats[-1]["ticks"], "l2": "Q_off BF16 13 MB is L2-resident"},
             "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                         "frac": ach / peak if ach else None, "traffic": None, "kernel": "phase_a_tc_kernel",
+                         "frac": ach / peak if ach else None, "traffic": None,
+                         "kernel": "phase_a_tcp_kernel" if stats[-1].get("tc_kernel") == 2 else "phase_a_tc_kernel",
                          "launches": pa_n, "avg_launch_us": pa_ms * 1e3 / max(pa_n, 1),
                          "algorithmic_flops_per_launch": flops / max(pa_n, 1)},
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": clocks}
@@ -260,7 +261,8 @@ def run_c5(args):
                        "objectives_exact_on_sample": exact,
                        "l2": "BF16 Q_off of the batch (3.4 GB) exceeds L2; no flush"},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                         "frac": ach / peak if ach else None, "traffic": None, "kernel": "phase_a_tc_kernel",
+                         "frac": ach / peak if ach else None, "traffic": None,
+                         "kernel": "phase_a_tcp_kernel" if stats[-1].get("tc_kernel") == 2 else "phase_a_tc_kernel",
                          "launches": pa_n, "avg_launch_us": pa_ms * 1e3 / max(pa_n, 1),
                          "algorithmic_bytes_per_launch": by / max(pa_n, 1),
                          "tflops": flops / (pa_ms * 1e-3) / 1e12 if pa_ms > 0 else None, "peak_kind": peak_kind},
