@@ -16,7 +16,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["lib", "Opts", "Stats", "opts", "solve", "solve_batched", "penalized_eval", "inner_run",
+__all__ = ["lib", "Opts", "Stats", "opts", "solve", "solve_batched", "penalized_eval", "penalized_vjp", "inner_run",
            "penalty_probe", "initial_point", "PenalizedObjective", "UBQPError", "PABB", "PPA", "FP32",
            "BF16X2_TC", "BF16_TC", "LIB_PATH"]
 
@@ -43,12 +43,14 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("ms_to_target", C.c_double), ("phase_a_flops", C.c_int64),
                 ("cluster_size", C.c_int32), ("gemv_kernel", C.c_int32), ("restarts", C.c_int32),
                 ("restart_probe_us", C.c_float * 5), ("tc_kernel", C.c_int32), ("sym_storage", C.c_int32),
-                ("inner_hist", C.c_int64 * HIST_BINS)]
+                ("inner_hist", C.c_int64 * HIST_BINS), ("alg_bytes", C.c_int64), ("alg_flops", C.c_int64),
+                ("cluster_probe_us", C.c_float * 9), ("cluster_tuned", C.c_int32)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("inner_hist", "restart_probe_us")}
-        d["inner_hist"] = list(self.inner_hist)
-        d["restart_probe_us"] = list(self.restart_probe_us)
+        arrays = ("inner_hist", "restart_probe_us", "cluster_probe_us")
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in arrays}
+        for k in arrays:
+            d[k] = list(getattr(self, k))
         return d
 
 
@@ -60,7 +62,8 @@ class Opts(C.Structure):
                 ("sigma_rel", C.c_double), ("seed", C.c_uint64), ("restarts", C.c_int),
                 ("precision", C.c_int), ("lobpcg_max_iter", C.c_int), ("lobpcg_tol", C.c_double),
                 ("jacobi_max_iter", C.c_int), ("max_ticks_per_sync", C.c_int), ("profile_kernels", C.c_int),
-                ("stop_at_target", C.c_int), ("tc_cluster", C.c_int), ("gemv_kernel", C.c_int), ("lane_budget", C.c_int), ("rows_per_item", C.c_int), ("sym_storage", C.c_int), ("target_objective", C.c_double),
+                ("stop_at_target", C.c_int), ("tc_cluster", C.c_int), ("gemv_kernel", C.c_int), ("lane_budget", C.c_int), ("rows_per_item", C.c_int), ("sym_storage", C.c_int),
+                ("wait_limit_us", C.c_int), ("target_objective", C.c_double),
                 ("stream", C.c_void_p),
                 ("mu", C.c_void_p), ("x_starts", C.c_void_p), ("stats", C.POINTER(Stats))]
 
@@ -83,13 +86,16 @@ def lib():
             L.ubqp_solve.argtypes = [vp, vp, i64, C.POINTER(Opts), vp, vp]
             L.ubqp_solve_batched.argtypes = [i32, vp, vp, vp, C.POINTER(Opts), vp, vp]
             L.ubqp_penalized_eval.argtypes = [vp, vp, vp, vp, i64, i64, C.c_int, vp, vp, vp]
+            L.ubqp_penalized_vjp.argtypes = [vp, vp, vp, i64, i64, C.c_int, vp, vp, vp, vp]
+            L.ubqp_penalized_eval_noalloc.argtypes = [vp, vp, vp, vp, i64, i64, C.c_int, vp, vp, vp]
             L.ubqp_inner_run.argtypes = [vp, vp, vp, vp, i64, C.POINTER(Opts), i32, vp, vp, vp,
                                          C.POINTER(i32), C.POINTER(i32)]
             L.ubqp_penalty_probe.argtypes = [vp, vp, vp, vp, i64, C.POINTER(Opts), C.POINTER(C.c_double),
                                              C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i32)]
             L.ubqp_initial_point.argtypes = [vp, vp, vp, i64, C.POINTER(Opts), vp, vp]
-            for name in ("ubqp_solve", "ubqp_solve_batched", "ubqp_penalized_eval", "ubqp_inner_run",
-                         "ubqp_penalty_probe", "ubqp_initial_point"):
+            for name in ("ubqp_solve", "ubqp_solve_batched", "ubqp_penalized_eval", "ubqp_penalized_vjp",
+                         "ubqp_penalized_eval_noalloc", "ubqp_inner_run", "ubqp_penalty_probe",
+                         "ubqp_initial_point"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -249,14 +255,39 @@ def penalized_eval(Q, b, p, x, want_h: bool = True, want_g: bool = True, stream=
     return h, g
 
 
+def penalized_vjp(x, g, grad_h, want_x=True, want_p=False, want_b=False, stream=None):
+    """Backward of penalized_eval for CUDA tensors x, g (batch, n) or (n,) and grad_h (batch,)
+    or a scalar: returns (grad_h * g, sum_r grad_h[r] (x_r - x_r^2), sum_r grad_h[r] x_r), each
+    None unless asked for."""
+    import torch
+    squeeze = x.dim() == 1
+    X = x.reshape(1, -1) if squeeze else x
+    dt = X.dtype
+    code = 1 if dt == torch.float64 else 0
+    Xc = X.contiguous()
+    Gc = g.reshape(Xc.shape).to(dt).contiguous()
+    go = grad_h.reshape(-1).to(dt).contiguous()
+    gx = torch.empty_like(Xc) if want_x else None
+    gp = torch.empty(Xc.shape[1], dtype=dt, device=Xc.device) if want_p else None
+    gb = torch.empty(Xc.shape[1], dtype=dt, device=Xc.device) if want_b else None
+    s = stream if stream is not None else torch.cuda.current_stream(Xc.device).cuda_stream
+    rc = lib().ubqp_penalized_vjp(Xc.data_ptr(), Gc.data_ptr(), go.data_ptr(), Xc.shape[1], Xc.shape[0], code,
+                                  None if gx is None else gx.data_ptr(), None if gp is None else gp.data_ptr(),
+                                  None if gb is None else gb.data_ptr(), s)
+    _check(rc, "ubqp_penalized_vjp")
+    if squeeze and gx is not None:
+        gx = gx[0]
+    return gx, gp, gb
+
+
 def _make_autograd():
     import torch
 
     class PenalizedObjective(torch.autograd.Function):
         """h(x, p) = x^T Q x + b^T x + sum_i p_i (x_i - x_i^2) (Sec. 4.1, problem (p)).
-        Forward and backward both call the library's gradient kernel (the one the inner
-        loop of Alg. 2 uses); backward returns grad_out * (2 (Q - Diag p) x + b + p)
-        for x, grad_out * (x - x^2) for p and grad_out * x for b."""
+        Forward runs ubqp_penalized_eval (the inner loop's GEMV kernel with the gradient
+        epilogue) and keeps g; backward runs ubqp_penalized_vjp: grad_out * g for x,
+        sum grad_out * (x - x^2) for p and sum grad_out * x for b.  Q is data (no gradient)."""
 
         @staticmethod
         def forward(ctx, x, Q, b, p):
@@ -269,10 +300,10 @@ def _make_autograd():
         @staticmethod
         def backward(ctx, grad_out):
             x, g = ctx.saved_tensors
-            go = grad_out.unsqueeze(-1) if x.dim() == 2 else grad_out
-            gx = go * g
-            gb = (go * x).reshape(-1, x.shape[-1]).sum(0) if ctx.has_b and ctx.needs_input_grad[2] else None
-            gp = (go * (x - x * x)).reshape(-1, x.shape[-1]).sum(0) if ctx.has_p and ctx.needs_input_grad[3] else None
+            want_b = ctx.has_b and ctx.needs_input_grad[2]
+            want_p = ctx.has_p and ctx.needs_input_grad[3]
+            gx, gp, gb = penalized_vjp(x.detach(), g, grad_out.detach(), want_x=ctx.needs_input_grad[0],
+                                       want_p=want_p, want_b=want_b)
             return gx, None, gb, gp
 
     return PenalizedObjective

@@ -37,56 +37,141 @@ __device__ __forceinline__ float4 ldg_stream(const float4* p)
     return v;
 }
 
+// FP64 rows (the penalized objective in FP64 only): the two products of a 16-byte group
+// summed with an FMA, then added to a plain FP64 accumulator (each lane sums about n / 64
+// groups, so the accumulated rounding stays near 1e-14 of the sum of |terms|)
+__device__ __forceinline__ void cacc4(double& acc, double2 q, double2 u) { acc += fma(q.y, u.y, q.x * u.x); }
+
+__device__ __forceinline__ double2 ldg_stream(const double2* p)
+{
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v2.f64 {%0,%1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+
+// element type -> its 16-byte group, the accumulator of a row dot, and the warp reduction
+template <typename T> struct RowT;
+template <> struct RowT<float> {
+    using V = float4;
+    using A = float2;   // TwoSum-compensated (sum, error)
+    static constexpr int W = 4;
+    __device__ static A zero() { return make_float2(0.f, 0.f); }
+    __device__ static void add1(A& a, float q, float u) { csum_add(a, __fmul_rn(q, u)); }
+    __device__ static float finish(A a0, A a1)
+    {
+        const float2 a = csum_shfl_reduce(csum_merge(a0, a1));
+        return a.x + a.y;
+    }
+    __device__ static V lds(const float* s, int e) { return make_float4(s[e], s[e + 1], s[e + 2], s[e + 3]); }
+};
+template <> struct RowT<double> {
+    using V = double2;
+    using A = double;
+    static constexpr int W = 2;
+    __device__ static A zero() { return 0.0; }
+    __device__ static void add1(A& a, double q, double u) { a = fma(q, u, a); }
+    __device__ static double finish(A a0, A a1) { return dsum_shfl_reduce(a0 + a1); }
+    __device__ static V lds(const double* s, int e) { return make_double2(s[e], s[e + 1]); }
+};
+
 // dot of NR rows (1 or 2) with u: 16-byte groups at columns c, c + 32, c + 64, c + 96 (in
-// float4 units) are loaded for every row before any is used, so each lane keeps 4 * NR
+// group units) are loaded for every row before any is used, so each lane keeps 4 * NR
 // loads in flight.  Group j goes to accumulator j & 1 of its row, in column order; the
 // tails keep the same alternation, so the result does not depend on the unrolling or NR.
-template <int NR>
-__device__ __forceinline__ void rows_dot_f32(const float* const (&rows)[NR], const float* su, int ld, int lane,
-                                             float (&out)[NR])
+// The rows start 16-byte aligned and hold ngrp whole groups (the solver's padded rows:
+// ngrp = ld / 4, so every column is covered); u is read in groups from shared memory, at
+// element offset uoff.  UAL: uoff is a multiple of the group width (16-byte loads of u).
+template <typename T, int NR, bool UAL>
+__device__ __forceinline__ void rows_dot_body(const T* const (&rows)[NR], const T* su, int uoff, int ngrp, int lane,
+                                              typename RowT<T>::A (&acc)[NR][2])
 {
-    const float4* u4 = reinterpret_cast<const float4*>(su);
-    const int n4 = ld >> 2;
-    float2 acc[NR][2];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
+    using R = RowT<T>;
+    using V = typename R::V;
+    constexpr int W = R::W;
+    auto ul = [&](int g) -> V {
+        if constexpr (UAL) return reinterpret_cast<const V*>(su + uoff)[g];
+        else return R::lds(su, uoff + W * g);
+    };
     int c = lane;
-    for (; c + 96 < n4; c += 128) {
-        float4 q[NR][4];
+    for (; c + 96 < ngrp; c += 128) {
+        V q[NR][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int r = 0; r < NR; ++r) q[r][j] = ldg_stream(reinterpret_cast<const float4*>(rows[r]) + c + 32 * j);
+            for (int r = 0; r < NR; ++r) q[r][j] = ldg_stream(reinterpret_cast<const V*>(rows[r]) + c + 32 * j);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float4 u = u4[c + 32 * j];
+            const V u = ul(c + 32 * j);
 #pragma unroll
             for (int r = 0; r < NR; ++r) cacc4(acc[r][j & 1], q[r][j], u);
         }
     }
-    for (; c + 32 < n4; c += 64) {
-        float4 q[NR][2];
+    for (; c + 32 < ngrp; c += 64) {
+        V q[NR][2];
 #pragma unroll
         for (int j = 0; j < 2; ++j)
 #pragma unroll
-            for (int r = 0; r < NR; ++r) q[r][j] = ldg_stream(reinterpret_cast<const float4*>(rows[r]) + c + 32 * j);
+            for (int r = 0; r < NR; ++r) q[r][j] = ldg_stream(reinterpret_cast<const V*>(rows[r]) + c + 32 * j);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const float4 u = u4[c + 32 * j];
+            const V u = ul(c + 32 * j);
 #pragma unroll
             for (int r = 0; r < NR; ++r) cacc4(acc[r][j], q[r][j], u);
         }
     }
-    for (; c < n4; c += 32) {
-        const float4 u = u4[c];
+    for (; c < ngrp; c += 32) {
+        const V u = ul(c);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) cacc4(acc[r][0], ldg_stream(reinterpret_cast<const float4*>(rows[r]) + c), u);
+        for (int r = 0; r < NR; ++r) cacc4(acc[r][0], ldg_stream(reinterpret_cast<const V*>(rows[r]) + c), u);
+    }
+}
+
+// the solver's rows: 16-byte aligned, ld (a multiple of 4) columns, zero beyond n
+template <int NR>
+__device__ __forceinline__ void rows_dot_f32(const float* const (&rows)[NR], const float* su, int ld, int lane,
+                                             float (&out)[NR])
+{
+    float2 acc[NR][2];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = make_float2(0.f, 0.f);
+    rows_dot_body<float, NR, true>(rows, su, 0, ld >> 2, lane, acc);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) out[r] = RowT<float>::finish(acc[r][0], acc[r][1]);
+}
+
+// a caller's rows of n entries (row-major, no padding; the two rows of a pair lie 8 rows
+// apart, so they share their alignment).  The first `head` entries before the first 16-byte
+// boundary and the `tail` entries after the last whole group are taken one by one by the
+// first lanes; the groups in between run the solver's loop above.
+template <typename T, int NR>
+__device__ __forceinline__ void rows_dot_any(const T* const (&rows)[NR], const T* su, int n, int lane,
+                                             T (&out)[NR])
+{
+    using R = RowT<T>;
+    constexpr int W = R::W;
+    const int mis = (int)((reinterpret_cast<uintptr_t>(rows[0]) & 15u) / sizeof(T));
+    const int head = min((W - mis) % W, n);
+    const int ngrp = (n - head) / W;
+    const int tail = n - head - W * ngrp;
+    typename R::A acc[NR][2];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r][0] = acc[r][1] = R::zero();
+    const T* body[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) body[r] = rows[r] + head;
+    if (head % W == 0) rows_dot_body<T, NR, true>(body, su, head, ngrp, lane, acc);
+    else rows_dot_body<T, NR, false>(body, su, head, ngrp, lane, acc);
+    if (lane < head) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) R::add1(acc[r][1], rows[r][lane], su[lane]);
+    }
+    if (lane < tail) {
+        const int e = head + W * ngrp + lane;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) R::add1(acc[r][1], rows[r][e], su[e]);
     }
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        const float2 a = csum_shfl_reduce(csum_merge(acc[r][0], acc[r][1]));
-        out[r] = a.x + a.y;
-    }
+    for (int r = 0; r < NR; ++r) out[r] = R::finish(acc[r][0], acc[r][1]);
 }
 
 // dot of one row of the evaluation matrix (each FP64 entry q stored as FP32 hi + lo with
@@ -122,18 +207,27 @@ __device__ __forceinline__ double row_dot_eval(const float2* __restrict__ row, c
     return ((double)ah.x + (double)ah.y) + ((double)al.x + (double)al.y);
 }
 
-// u (written by the lane's last update, zero beyond n) into shared memory
-__device__ __forceinline__ void item_load_u(const LaneDev& L, float* su)
+// u (written by the lane's last update, zero beyond n) into shared memory; for a gradient
+// lane (penalized objective) the caller's point x, of the caller's element type T
+template <typename T = float>
+__device__ __forceinline__ void item_load_u(const LaneDev& L, T* su)
 {
-    const float4* g4 = reinterpret_cast<const float4*>(L.vec + (size_t)V_U * L.ld);
-    float4* s4 = reinterpret_cast<float4*>(su);
-    for (int c = threadIdx.x; c < (L.ld >> 2); c += kThreads) s4[c] = g4[c];
+    if (L.mode == MODE_GRAD) {
+        const T* x = static_cast<const T*>(L.gx);
+        for (int c = threadIdx.x; c < L.n; c += kThreads) su[c] = x[c];
+        return;
+    }
+    if constexpr (sizeof(T) == sizeof(float)) {
+        const float4* g4 = reinterpret_cast<const float4*>(L.vec + (size_t)V_U * L.ld);
+        float4* s4 = reinterpret_cast<float4*>(su);
+        for (int c = threadIdx.x; c < (L.ld >> 2); c += kThreads) s4[c] = g4[c];
+    }
 }
 
-// v_r = (row row0 + r of the phase's matrix) . u for r < rows, into sv[r]
-__device__ __forceinline__ void item_rows(const LaneDev& L, int ph, int row0, int rows, const float* su, double* sv)
+// the solver's matrices: the FP32 hi/lo evaluation rows (PH_EVAL) or the padded Q'_off rows
+__device__ __forceinline__ void item_rows_solver(const LaneDev& L, int ph, int row0, int rows, const float* su,
+                                                 double* sv, int lane, int warp)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ld = L.ld;
     if (ph == PH_EVAL) {
         for (int r = warp; r < rows; r += kWarps) {
@@ -160,6 +254,59 @@ __device__ __forceinline__ void item_rows(const LaneDev& L, int ph, int row0, in
             }
         }
     }
+}
+
+
+// v_r = (row row0 + r of the phase's matrix) . u for r < rows, into sv[r]
+template <typename T = float>
+__device__ __forceinline__ void item_rows(const LaneDev& L, int ph, int row0, int rows, const T* su, double* sv)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (ph == PH_GRAD) {
+        // the caller's Q (n x n, row stride gld, element type T), diagonal included
+        const T* Q = static_cast<const T*>(L.gQ);
+        for (int r = warp; r < rows; r += 2 * kWarps) {
+            const T* ra = Q + (size_t)(row0 + r) * L.gld;
+            if (r + kWarps < rows) {
+                const T* const rp[2] = {ra, ra + (size_t)kWarps * L.gld};
+                T v[2];
+                rows_dot_any<T, 2>(rp, su, L.n, lane, v);
+                if (lane == 0) {
+                    sv[r] = (double)v[0];
+                    sv[r + kWarps] = (double)v[1];
+                }
+            } else {
+                const T* const rp[1] = {ra};
+                T v[1];
+                rows_dot_any<T, 1>(rp, su, L.n, lane, v);
+                if (lane == 0) sv[r] = (double)v[0];
+            }
+        }
+        return;
+    }
+    if constexpr (sizeof(T) == sizeof(float)) item_rows_solver(L, ph, row0, rows, su, sv, lane, warp);
+}
+
+// Gradient lanes (the penalized objective of Sec. 4.1, problem (p)): row i received
+// v = (Q x)_i of the caller's Q (diagonal included); the epilogue writes
+//     g_i = 2 v - 2 p_i x_i + b_i + p_i          (grad of h = x^T (Q - P*) x + (b + p)^T x)
+// and adds h_i = x_i (v + b_i + p_i - p_i x_i) to the item's FP64 partial sum of h.
+template <typename T>
+__device__ __forceinline__ void item_finish_grad(const LaneDev& L, int blk, int row0, int rows, const double* sv,
+                                                 const T* su)
+{
+    Acc a;
+    a.zero();
+    if ((int)threadIdx.x < rows) {
+        const int i = row0 + threadIdx.x;
+        const T v = (T)sv[threadIdx.x];
+        const T x = su[i];
+        const T b = L.gb ? static_cast<const T*>(L.gb)[i] : T(0);
+        const T p = L.gp ? static_cast<const T*>(L.gp)[i] : T(0);
+        if (L.gg) static_cast<T*>(L.gg)[i] = T(2) * v - T(2) * p * x + b + p;
+        a.f = (double)x * ((double)v + (double)b + (double)p - (double)p * (double)x);
+    }
+    block_reduce_write<kWarps>(a, PH_GRAD, L.part + blk, true);
 }
 
 // per-row epilogue of the item's rows and its partial L.part[blk]; also counts the

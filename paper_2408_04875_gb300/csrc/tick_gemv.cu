@@ -6,38 +6,24 @@
 // loads while u sits in shared memory.  The kernel is bound by the bytes of Q it reads:
 // n * ld * 4 per lane per tick (FP32), 8 per entry for the evaluation tick.
 //
-// This file also holds the kernel that computes h and grad h for ubqp_penalized_eval
-// (MODE_GRAD lanes), so the autograd path and the inner loop share one gradient kernel.
+// The same kernel computes h and grad h of problem (p) for ubqp_penalized_eval: those
+// lanes (MODE_GRAD) read the caller's Q rows with the inner loop's row dot (gemv_rows.cuh)
+// and finish with the gradient epilogue; the FP32 instance is the one the inner loop runs,
+// the FP64 instance the same source on FP64 data.
 #include "gemv_rows.cuh"
 
 namespace ubqp {
 
-// generic (unaligned, unpadded) row dot for user matrices of penalized_eval
-template <typename T>
-__device__ __forceinline__ T row_dot_plain(const T* __restrict__ row, const T* su, int n, int lane)
-{
-    T a0 = 0, a1 = 0;
-    int c = lane;
-    for (; c + 32 < n; c += 64) {
-        a0 += row[c] * su[c];
-        a1 += row[c + 32] * su[c + 32];
-    }
-    for (; c < n; c += 32) a0 += row[c] * su[c];
-    T a = a0 + a1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    return a;
-}
-
 // ---------------------------------------------------------------------------------
-// solver lanes (FP32 GEMV path)
+// solver lanes (FP32) and gradient lanes (FP32 or FP64, element type T)
+template <typename T>
 __global__ void __launch_bounds__(kThreads, 4) phase_a_gemv_kernel(TickArgs A)
 {
     // Persistent: CTAs pull (lane, row-block) items from a queue until it is empty; the
     // items of the largest lanes come first.  u stays in shared memory while consecutive
     // items belong to the same lane.
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* su = reinterpret_cast<float*>(smem_raw);
+    T* su = reinterpret_cast<T*>(smem_raw);
     __shared__ double sv[kThreads];
     __shared__ int s_item, s_ulane, is_last;
     if (threadIdx.x == 0) s_ulane = -1;
@@ -48,21 +34,23 @@ __global__ void __launch_bounds__(kThreads, 4) phase_a_gemv_kernel(TickArgs A)
         if (item >= A.nitems) break;
         const int2 it = A.items[item];
         const LaneDev& L = A.lanes[it.x];
-        const int ph = L.st->phase;
-        if (ph == PH_DONE || ph == PH_GRAD) {
+        const bool grad = L.mode == MODE_GRAD;
+        const int ph = grad ? (int)PH_GRAD : L.st->phase;
+        if (ph == PH_DONE) {
             __syncthreads();
             continue;
         }
-        const int k = L.st->k;
+        const int k = grad ? 0 : L.st->k;
         const int row0 = it.y * A.rows_per_item;
         const int rows = min(A.rows_per_item, L.n - row0);
         if (s_ulane != it.x) item_load_u(L, su);   // consecutive items of one lane share u
         __syncthreads();
         if (threadIdx.x == 0) s_ulane = it.x;
-        item_rows(L, ph, row0, rows, su, sv);
+        item_rows<T>(L, ph, row0, rows, su, sv);
         __syncthreads();
-        item_finish(L, ph, k, it.y, row0, rows, sv, A.P);
-        if (A.fused) {
+        if (grad) item_finish_grad<T>(L, it.y, row0, rows, sv, su);
+        else item_finish(L, ph, k, it.y, row0, rows, sv, A.P);
+        if (A.fused && !grad) {
             // every CTA publishes its partial and epilogue writes, then counts itself in; the
             // CTA that completes the lane's count runs the lane's update.  No CTA waits.
             __threadfence();
@@ -87,57 +75,6 @@ __global__ void __launch_bounds__(kThreads, 4) phase_a_gemv_kernel(TickArgs A)
     }
 }
 
-// ---------------------------------------------------------------------------------
-// gradient lanes: h and g of problem (p) for one point, matrix of type T
-template <typename T>
-__global__ void __launch_bounds__(kThreads) phase_a_grad_kernel(TickArgs A)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* su = reinterpret_cast<T*>(smem_raw);
-    __shared__ T sv[kThreads];
-
-    const int2 it = A.items[blockIdx.x];
-    const LaneDev& L = A.lanes[it.x];
-    const int n = L.n;
-    const int row0 = it.y * A.rows_per_item;
-    const int rows = min(A.rows_per_item, n - row0);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const T* Q = static_cast<const T*>(L.gQ);
-    const T* x = static_cast<const T*>(L.gx);
-    const T* b = static_cast<const T*>(L.gb);
-    const T* p = static_cast<const T*>(L.gp);
-    T* g = static_cast<T*>(L.gg);
-
-    for (int c = threadIdx.x; c < n; c += kThreads) su[c] = x[c];
-    __syncthreads();
-    for (int r = warp; r < rows; r += kWarps) {
-        T v = row_dot_plain<T>(Q + (size_t)(row0 + r) * L.gld, su, n, lane);
-        if (lane == 0) sv[r] = v;
-    }
-    __syncthreads();
-
-    // g = 2 (Q - Diag p) x + b + p;  h contribution x_i (Qx)_i + b_i x_i + p_i (x_i - x_i^2)
-    double hpart = 0.0;
-    if ((int)threadIdx.x < rows) {
-        const int i = row0 + threadIdx.x;
-        T v = sv[threadIdx.x];
-        T xi = su[i];
-        T bi = b ? b[i] : T(0);
-        T pi = p ? p[i] : T(0);
-        if (g) g[i] = T(2) * v - T(2) * pi * xi + bi + pi;
-        hpart = (double)(xi * (v + bi + pi - pi * xi));
-    }
-    hpart = dsum_shfl_reduce(hpart);
-    __shared__ double sh[kWarps];
-    if (lane == 0) sh[warp] = hpart;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kWarps; ++w) t += sh[w];
-        L.part[it.y].f = t;
-    }
-}
-
 template <typename T>
 __global__ void grad_reduce_kernel(const LaneDev* lanes, int nlanes, T* h_out)
 {
@@ -149,21 +86,59 @@ __global__ void grad_reduce_kernel(const LaneDev* lanes, int nlanes, T* h_out)
     h_out[l] = (T)t;
 }
 
-cudaError_t prepare_phase_a_gemv(int max_ld)
+// vector-Jacobian product of h (backward of the penalized objective) for `batch` points:
+//   gx[r][i] = go[r] g[r][i],  gp[i] = sum_r go[r] (x_ri - x_ri^2),  gb[i] = sum_r go[r] x_ri
+// one thread per coordinate i; the sums over r run in order r = 0, 1, ... (FP64 accumulation)
+template <typename T>
+__global__ void penalized_vjp_kernel(const T* x, const T* g, const T* go, int64_t n, int64_t batch, T* gx, T* gp,
+                                     T* gb)
 {
-    size_t smem = (size_t)max_ld * sizeof(float);
-    if (smem <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(phase_a_gemv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double sp = 0.0, sb = 0.0;
+        for (int64_t r = 0; r < batch; ++r) {
+            const T w = go[r];
+            const T xi = x[r * n + i];
+            if (gx) gx[r * n + i] = w * g[r * n + i];
+            sp += (double)w * ((double)xi - (double)xi * (double)xi);
+            sb += (double)w * (double)xi;
+        }
+        if (gp) gp[i] = (T)sp;
+        if (gb) gb[i] = (T)sb;
+    }
 }
 
+cudaError_t launch_penalized_vjp(const void* x, const void* g, const void* go, int64_t n, int64_t batch, int dtype,
+                                 void* gx, void* gp, void* gb, cudaStream_t s)
+{
+    const int threads = 256;
+    const int64_t want = (n + threads - 1) / threads;
+    const int blocks = (int)(want < 4096 ? want : 4096);
+    if (dtype == 1)
+        penalized_vjp_kernel<double><<<blocks, threads, 0, s>>>((const double*)x, (const double*)g, (const double*)go, n,
+                                                                 batch, (double*)gx, (double*)gp, (double*)gb);
+    else
+        penalized_vjp_kernel<float><<<blocks, threads, 0, s>>>((const float*)x, (const float*)g, (const float*)go, n,
+                                                               batch, (float*)gx, (float*)gp, (float*)gb);
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t set_smem(size_t smem)
+{
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(phase_a_gemv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t prepare_phase_a_gemv(int max_ld) { return set_smem<float>((size_t)max_ld * sizeof(float)); }
+
 // persistent grid: every CTA that fits on the GPU at once, never more CTAs than items
-int gemv_grid(int max_ld, int nitems)
+template <typename T>
+static int grid_for(size_t smem, int nitems)
 {
     int dev = 0, sms = 148, per = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, phase_a_gemv_kernel, kThreads,
-                                                                  (size_t)max_ld * sizeof(float));
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, phase_a_gemv_kernel<T>, kThreads, smem);
     if (e != cudaSuccess || per < 1) {
         cudaGetLastError();
         per = 1;
@@ -172,31 +147,35 @@ int gemv_grid(int max_ld, int nitems)
     return nitems < g ? nitems : g;
 }
 
+int gemv_grid(int max_ld, int nitems) { return grid_for<float>((size_t)max_ld * sizeof(float), nitems); }
+
 cudaError_t launch_phase_a_gemv_f32(const TickArgs& a, cudaStream_t s)
 {
     // shared: u of the widest lane (ld floats); rows_per_item <= kThreads
     size_t smem = (size_t)a.max_ld * sizeof(float);
-    phase_a_gemv_kernel<<<a.grid, kThreads, smem, s>>>(a);
+    phase_a_gemv_kernel<float><<<a.grid, kThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
+// gradient lanes on the GEMV kernel: shared memory holds one point (n entries of T); the
+// queue counters a.work / a.done must be zero (the last CTA leaves them zero again)
 cudaError_t launch_phase_a_grad(const TickArgs& a, int dtype, int64_t n, cudaStream_t s)
 {
-    size_t smem = (size_t)n * (dtype == 1 ? sizeof(double) : sizeof(float));
+    TickArgs t = a;
+    t.fused = 0;
+    t.active_count = nullptr;
     if (dtype == 1) {
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(phase_a_grad_kernel<double>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        phase_a_grad_kernel<double><<<a.nitems, kThreads, smem, s>>>(a);
+        const size_t smem = (size_t)n * sizeof(double);
+        cudaError_t e = set_smem<double>(smem);
+        if (e != cudaSuccess) return e;
+        t.grid = grid_for<double>(smem, a.nitems);
+        phase_a_gemv_kernel<double><<<t.grid, kThreads, smem, s>>>(t);
     } else {
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(phase_a_grad_kernel<float>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        phase_a_grad_kernel<float><<<a.nitems, kThreads, smem, s>>>(a);
+        const size_t smem = (size_t)n * sizeof(float);
+        cudaError_t e = set_smem<float>(smem);
+        if (e != cudaSuccess) return e;
+        t.grid = grid_for<float>(smem, a.nitems);
+        phase_a_gemv_kernel<float><<<t.grid, kThreads, smem, s>>>(t);
     }
     return cudaGetLastError();
 }
