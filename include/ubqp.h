@@ -79,7 +79,7 @@ typedef struct {
     int64_t phase_a_flops;   /* algorithmic flops of the tensor-core launches timed     */
     int32_t cluster_size;    /* CTAs per cluster of the tensor-core launches (0: none)  */
     int32_t gemv_kernel;     /* scheduler that ran the FP32 lanes: 1 lock-step, 2 lane  */
-                             /* loop (0: tensor-core lanes)                             */
+                             /* loop, 3 single-lane kernel (0: tensor-core lanes)       */
     int32_t restarts;        /* starts per instance that ran (the tuner's pick when     */
                              /* opts->restarts == 0)                                    */
     float restart_probe_us[5]; /* restart tuner: step time measured with 1, 8, 32, 64  */
@@ -88,6 +88,16 @@ typedef struct {
                              /* 2 persistent (many tiles), 0 none                       */
     int32_t sym_storage;     /* 1 when the FP32 lanes ran on the symmetric tiles        */
     int64_t inner_hist[UBQP_HIST_BINS]; /* projected steps per subproblem (Fig. 5)   */
+    int64_t alg_bytes;       /* sparse-minimum bytes of every matrix-vector product run:  */
+                             /* sum over lanes of steps x (6 nnz(Q_off) + 32 n), i.e. the */
+                             /* stored off-diagonal entries as 4-byte values with 2-byte  */
+                             /* column indices plus 8 vectors of n floats per step        */
+    int64_t alg_flops;       /* sum over lanes of steps x 2 nnz(Q_off)                    */
+    float cluster_probe_us[9]; /* tensor-core form tuner (tc_cluster = 0): contraction time */
+                             /* of the persistent many-tile kernel [0] and of split-K over */
+                             /* S = 1..8 CTAs [S], best of three launches (0: not probed)  */
+    int32_t cluster_tuned;   /* 0: rule or caller's tc_cluster, 1: measured in this call,  */
+                             /* 2: taken from the cache (see tc_cluster)                  */
 } ubqp_stats;
 
 /* Options; ubqp_opts_default() fills the paper's settings and this library's readings
@@ -122,17 +132,29 @@ typedef struct {
                              /* keep a per-tick timeline (ubqp_profile_timeline): 0     */
     int stop_at_target;      /* 1: stop once target_objective is reached: 0            */
     int tc_cluster;          /* CTAs splitting K in the tensor-core kernel, 1..8;      */
-                             /* 0 = chosen by the library's tuner                      */
+                             /* 0 = chosen by measurement: the contraction alone is     */
+                             /* timed with every feasible S and with the persistent      */
+                             /* many-tile kernel, on the call's operands, and the        */
+                             /* fastest kept; the choice is cached per shape in the      */
+                             /* process and, when the environment variable               */
+                             /* UBQP_TUNE_CACHE names a file, in that JSON file          */
     int gemv_kernel;         /* scheduler of the FP32 lanes: 1 lock-step (one launch   */
                              /* per step of all lanes), 2 persistent lane loop (lanes  */
-                             /* advance independently inside one launch); 0 = 2 for 4  */
-                             /* or more lanes, else 1 (and 1 when profile_kernels == 2) */
+                             /* advance independently inside one launch), 3 single-lane */
+                             /* persistent kernel (one lane only: many steps per        */
+                             /* cooperative launch, two grid barriers per step); 0 = 3  */
+                             /* for one lane, 2 for 4 or more lanes, else 1 (and 1 when */
+                             /* profile_kernels == 2)                                   */
     int lane_budget;         /* lane loop: steps per lane between host checks; 0 = 1024 */
     int rows_per_item;       /* FP32 lanes: matrix rows per work item, 8..256 (a multiple */
                              /* of 8); 0 = chosen from the batch size                  */
     int sym_storage;         /* FP32 lanes on the lane loop: 1 = store only the upper   */
                              /* triangle of Q'_off (128 x 128 tiles; each step reads    */
                              /* about half the bytes), 0 = dense rows: 1                */
+    int wait_limit_us;       /* lane loop and single-lane kernel: limit of one wait of a  */
+                             /* CTA (for its next ring slot / at a grid barrier), in     */
+                             /* microseconds; a wait that runs out ends the call with    */
+                             /* UBQP_ETIMEOUT and leaves the device usable; 0 = 5 s      */
     double target_objective; /* objective to time against (used when finite)           */
     void* stream;            /* cudaStream_t, NULL = default stream                    */
     const double* const* mu; /* optional perturbations, one n x n matrix per instance   */
@@ -191,32 +213,56 @@ int ubqp_solve_batched(int32_t num, const int64_t* n, const double* const* Q,
  * gradient (Sec. 3.1, used as g^k in Alg. 2), for `batch` points sharing Q, b, p:
  *     h_r = x_r^T Q x_r + b^T x_r + sum_i p_i (x_ri - x_ri^2)
  *     g_r = 2 (Q - Diag p) x_r + b + p
- * All pointers are DEVICE memory of element type dtype (UBQP_DTYPE_F32 / _F64):
- *   Q n x n row-major, b and p n (either may be NULL = 0), x batch x n row-major,
- *   h_out batch (may be NULL), g_out batch x n (may be NULL).
- * stream: cudaStream_t (NULL = default).  Runs the same gradient kernel the inner loop
- * uses.  Scratch is allocated and freed inside the call.
+ * All pointers are DEVICE memory of element type dtype (UBQP_DTYPE_F32 / _F64), each
+ * aligned to its element size:
+ *   Q n x n row-major (no padding), b and p n (either may be NULL = 0), x batch x n
+ *   row-major, h_out batch (may be NULL), g_out batch x n (may be NULL).
+ * 1 <= n <= 65536 and one point must fit in shared memory (n * element size <= 227 KiB,
+ * else UBQP_ENOTSUP).  stream: cudaStream_t (NULL = default).
+ * Runs the kernel of the inner loop's matrix-vector products (the lock-step GEMV kernel:
+ * the same row dot with compensated FP32 sums, here on the caller's rows) with the
+ * gradient epilogue; the FP64 dtype runs the same kernel source on FP64 data.  h is summed
+ * in FP64.  Scratch (descriptors, work items, partial sums) is allocated and freed on
+ * `stream` inside the call; returns after synchronizing `stream`.
  */
 int ubqp_penalized_eval(const void* Q, const void* b, const void* p, const void* x, int64_t n,
                         int64_t batch, int dtype, void* h_out, void* g_out, void* stream);
 
 /*
+ * ubqp_penalized_vjp - backward of ubqp_penalized_eval (the vector-Jacobian product of h
+ * with respect to x, p and b), for `batch` points and the output gradient grad_h:
+ *     gx[r][i] = grad_h[r] g[r][i],  gp[i] = sum_r grad_h[r] (x_ri - x_ri^2),
+ *     gb[i] = sum_r grad_h[r] x_ri
+ * (h is linear in p and b, so these are exact derivatives).  All pointers are DEVICE
+ * memory of element type dtype: x and g (the g_out of the forward call) batch x n,
+ * grad_h batch; gx_out batch x n, gp_out n and gb_out n, each may be NULL (g may be NULL
+ * when gx_out is).  The sums over r run in FP64 in order r = 0, 1, ...  Allocates nothing;
+ * returns after synchronizing `stream`.
+ */
+int ubqp_penalized_vjp(const void* x, const void* g, const void* grad_h, int64_t n, int64_t batch, int dtype,
+                       void* gx_out, void* gp_out, void* gb_out, void* stream);
+
+/*
  * ubqp_penalized_eval_noalloc - the computation of ubqp_penalized_eval (h and grad h of
- * problem (p) for `batch` points, same arguments, same kernels) without any device
- * allocation, for callers that cannot call cudaMalloc/cudaFree: code that owns all device
- * memory through its own pool or a fixed memory budget, and code that cannot afford the
- * device-wide synchronization those calls may cause.  The paper has no counterpart; this
- * is an interface variant of this library.
+ * problem (p) for `batch` points, same arguments, same kernel, same work partition) without
+ * any device allocation, for callers that cannot call cudaMalloc/cudaFree: code that owns
+ * all device memory through its own pool or a fixed memory budget, and code that cannot
+ * afford the device-wide synchronization those calls may cause.  The paper has no
+ * counterpart; this is an interface variant of this library.
  *   Scratch: a static device array of UBQP_NOALLOC_SCRATCH_BYTES that every GPU loading the
  *   library holds until the process exits.  Limits: batch <= 256, n * element size <=
- *   200 KiB, and batch * ceil(n / 256) <= 16384; larger requests return UBQP_EINVAL.
- *   The first call on a device resolves the array's device address (cudaGetSymbolAddress),
- *   so make that first call before any stream capture on that device.
+ *   200 KiB, and batch * ceil(n / rows per item) <= 16384 work items (rows per item as in
+ *   ubqp_penalized_eval, at most 256); larger requests return UBQP_EINVAL with the limit
+ *   named in ubqp_last_error().
+ *   The array's device address is resolved (cudaGetSymbolAddress) on the first call in each
+ *   CUDA context, so make that first call before any stream capture in that context; a new
+ *   context (after a device reset) gets its own first call.
  *   All calls share the array and it keeps the last call's contents (each call rewrites
  *   what it reads); calls that overlap on the GPU (other streams, other host threads) race.
- *   All pointers are device memory; returns after synchronizing `stream`.
+ *   All pointers are device memory.  The call ends with cudaStreamSynchronize(stream), so
+ *   it cannot be called on a stream that is being captured.
  */
-#define UBQP_NOALLOC_SCRATCH_BYTES 2293760
+#define UBQP_NOALLOC_SCRATCH_BYTES 2294016
 int ubqp_penalized_eval_noalloc(const void* Q, const void* b, const void* p, const void* x, int64_t n,
                                 int64_t batch, int dtype, void* h_out, void* g_out, void* stream);
 
@@ -237,6 +283,9 @@ int ubqp_inner_run(const double* Qp, const double* bp, const double* p, const do
  * state (Qp, bp, p, x as in ubqp_inner_run): lambda_min of Z^-1/2 Qbar_II Z^-1/2 by the
  * device eigen-solver, the step alpha (Eq. (eq:alpha1) with the resolution floor, no
  * previous floor steps), |I| and the eigen-solver iterations.  Outputs are host memory.
+ * o->precision selects the matrix-vector products: UBQP_FP32 (the FP32 GEMV kernels) or a
+ * tensor-core precision (the BF16 contraction of the batched path; the off-diagonal of Qp
+ * must then be exact in BF16, else UBQP_ENOTSUP).
  */
 int ubqp_penalty_probe(const double* Qp, const double* bp, const double* p, const double* x,
                        int64_t n, const ubqp_opts* o, double* lambda_out, double* alpha_out,

@@ -17,10 +17,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libubqp.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["engine.cu", "tick_gemv.cu", "lane_loop.cu", "tick_update.cu", "init.cu", "noalloc.cu", "tc_gemm.cu"]
-# the lane loop reads, within one launch, lane vectors that CTAs on other SMs wrote: its
-# plain loads are cached in L2 only
-EXTRA = {"lane_loop.cu": ["-Xptxas", "-dlcm=cg"]}
+SOURCES = ["engine.cu", "tick_gemv.cu", "lane_loop.cu", "solo.cu", "tick_update.cu", "init.cu", "noalloc.cu",
+           "tc_gemm.cu"]
+# the lane loop and the single-lane kernel read, within one launch, lane vectors that CTAs on
+# other SMs wrote: their plain loads are cached in L2 only
+EXTRA = {"lane_loop.cu": ["-Xptxas", "-dlcm=cg"], "solo.cu": ["-Xptxas", "-dlcm=cg"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -14,7 +14,11 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "../../include/ubqp.h"
@@ -27,13 +31,15 @@ static thread_local char g_last_error[512] = "";
 static thread_local std::vector<float> g_tl_ms;
 static thread_local std::vector<int64_t> g_tl_work;
 
-static void set_error(const char* fmt, ...)
+void set_error(const char* fmt, ...)
 {
     va_list ap;
     va_start(ap, fmt);
     vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
     va_end(ap);
 }
+
+void clear_error() { g_last_error[0] = 0; }
 
 #define UBQP_CK(call)                                                                        \
     do {                                                                                     \
@@ -154,8 +160,9 @@ static int check_opts(const ubqp_opts& o)
     if (o.max_ticks_per_sync < 1 || o.max_ticks_per_sync > 4096) { set_error("max_ticks_per_sync out of range"); return UBQP_EINVAL; }
     if (!(o.sigma_rel >= 0.0) || !(o.gamma_margin > 0.0)) { set_error("sigma_rel >= 0 and gamma_margin > 0 required"); return UBQP_EINVAL; }
     if (o.tc_cluster < 0 || o.tc_cluster > 8) { set_error("tc_cluster must be in [0, 8]"); return UBQP_EINVAL; }
-    if (o.gemv_kernel < 0 || o.gemv_kernel > 2) { set_error("gemv_kernel must be 0, 1 or 2"); return UBQP_EINVAL; }
+    if (o.gemv_kernel < 0 || o.gemv_kernel > 3) { set_error("gemv_kernel must be 0, 1, 2 or 3"); return UBQP_EINVAL; }
     if (o.lane_budget < 0) { set_error("lane_budget must be >= 0"); return UBQP_EINVAL; }
+    if (o.wait_limit_us < 0) { set_error("wait_limit_us must be >= 0"); return UBQP_EINVAL; }
     if (o.rows_per_item != 0 && (o.rows_per_item < 8 || o.rows_per_item > 256 || o.rows_per_item % 8 != 0)) {
         set_error("rows_per_item must be 0 or a multiple of 8 in [8, 256]");
         return UBQP_EINVAL;
@@ -194,6 +201,57 @@ struct InstDev {
     int bn, n_tiles, rows_b;   // tensor-core tiling of this instance's lanes
     int lane0, nl;
 };
+
+// ---------------------------------------------------------------------------------
+// Measured choice of the tensor-core launch form, cached per shape.  Key: compute capability,
+// SM count, output tiles, smallest k-block count, widest N tile, terms, instances and widest
+// ld.  Value: the split-K cluster size S (1..8) or 0 for the persistent many-tile kernel.  The
+// cache lives in this process; when the environment variable UBQP_TUNE_CACHE names a file, it
+// is also read from and written back to that file (one JSON object of "key": value pairs).
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+static std::string g_tune_file_loaded;
+
+static void tune_load_file_locked(const char* path)
+{
+    if (!path || g_tune_file_loaded == path) return;
+    g_tune_file_loaded = path;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    std::string txt;
+    char buf[4096];
+    size_t k;
+    while ((k = fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, k);
+    fclose(f);
+    // "key": value pairs; keys hold no quotes
+    size_t pos = 0;
+    for (;;) {
+        const size_t a = txt.find('"', pos);
+        if (a == std::string::npos) break;
+        const size_t b = txt.find('"', a + 1);
+        if (b == std::string::npos) break;
+        const size_t c = txt.find(':', b + 1);
+        if (c == std::string::npos) break;
+        char* end = nullptr;
+        const long v = strtol(txt.c_str() + c + 1, &end, 10);
+        if (end && end != txt.c_str() + c + 1) g_tune[txt.substr(a + 1, b - a - 1)] = (int)v;
+        pos = end ? (size_t)(end - txt.c_str()) : b + 1;
+    }
+}
+
+static void tune_save_file_locked(const char* path)
+{
+    if (!path) return;
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto& kv : g_tune) fprintf(f, " \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++i < g_tune.size() ? "," : "");
+    fprintf(f, "}\n");
+    fclose(f);
+    rename(tmp.c_str(), path);
+}
 
 class Solver {
   public:
@@ -284,6 +342,7 @@ class Solver {
         o_valargs_ = ar_.reserve(insts.size() * sizeof(ValArgs));
         o_refargs_ = ar_.reserve(insts.size() * sizeof(RefArgs));
         o_valid_ = ar_.reserve(insts.size() * 4 * sizeof(float));
+        o_nnz_ = ar_.reserve(insts.size() * sizeof(unsigned long long));
         o_inexact_ = ar_.reserve(insts.size() * sizeof(int));
         o_hist_ = ar_.reserve(UBQP_HIST_BINS * sizeof(int64_t));
         o_active_ = ar_.reserve(sizeof(int32_t));
@@ -301,6 +360,11 @@ class Solver {
         while (rb < 32 && total_rows / rb > target_items) rb *= 2;
         if (o_.rows_per_item > 0) rb = o_.rows_per_item;
         if (sym_) rb = kSymT;   // the second stage works on whole tile rows
+        // one FP32 lane: the single-lane persistent kernel (a cooperative launch of one CTA per
+        // row block), unless another scheduler or the per-tick timeline is asked for
+        solo_ = !tc && !sym_ && lanes.size() == 1 && (size_t)max_ld * sizeof(float) <= 200 * 1024 &&
+                (o_.gemv_kernel == 3 || (o_.gemv_kernel == 0 && o_.profile_kernels < 2));
+        if (solo_) solo_shape((int)insts[lanes[0].inst].n, o_.rows_per_item, num_sms_, &solo_grid_, &rb, &solo_nblk_);
         rows_per_item_ = rb;
 
         lanes_.assign(lanes.size(), LaneDev());
@@ -315,9 +379,11 @@ class Solver {
         sym_host_.assign(sym_ ? lanes.size() : 0, SymLane());
         o_pbuf_.assign(lanes.size(), 0);
         int64_t nitems = 0;
+        lane_inst_.assign(lanes.size(), 0);
         for (size_t l = 0; l < lanes.size(); ++l) {
             const LaneIn& in = lanes[l];
             InstDev& I = inst_[in.inst];
+            lane_inst_[l] = in.inst;
             if (I.lane0 < 0) I.lane0 = (int)l;
             I.nl += 1;
             LaneDev& L = lanes_[l];
@@ -367,6 +433,7 @@ class Solver {
         o_symctr_ = sym_ ? ar_.reserve(lanes.size() * sizeof(unsigned int)) : 0;
         o_symlanes_ = sym_ ? ar_.reserve(lanes.size() * sizeof(SymLane)) : 0;
         o_queue_ = ar_.reserve(2 * sizeof(int32_t));
+        o_solo_ = ar_.reserve(4 * sizeof(int32_t));
         o_lanes_ = ar_.reserve(lanes.size() * sizeof(LaneDev));
         o_linit_ = ar_.reserve(lanes.size() * sizeof(LaneInit));
         o_items_ = ar_.reserve((size_t)std::max<int64_t>(nitems, 1) * sizeof(int2));
@@ -415,7 +482,9 @@ class Solver {
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_counters_), 0, lanes.size() * sizeof(unsigned int), stream_));
         if (sym_) UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_symctr_), 0, lanes.size() * sizeof(unsigned int), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_queue_), 0, 2 * sizeof(int32_t), stream_));
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_solo_), 0, 4 * sizeof(int32_t), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_valid_), 0, insts.size() * 4 * sizeof(float), stream_));
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_nnz_), 0, insts.size() * sizeof(unsigned long long), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_scal_), 0, insts.size() * 4 * sizeof(float), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_inexact_), 0, insts.size() * sizeof(int), stream_));
 
@@ -453,6 +522,7 @@ class Solver {
                 va[t].n = (int)inst_[t].n;
                 va[t].pad_ = 0;
                 va[t].out = ar_.at<float>(o_valid_) + 4 * t;
+                va[t].nnz = ar_.at<unsigned long long>(o_nnz_) + t;
             }
             UBQP_CK(cudaMemcpyAsync(ar_.at<int64_t>(o_row0_), row0.data(), row0.size() * sizeof(int64_t),
                                     cudaMemcpyHostToDevice, stream_));
@@ -463,6 +533,9 @@ class Solver {
         }
         std::vector<float> val(insts.size() * 4);
         UBQP_CK(cudaMemcpyAsync(val.data(), ar_.at<float>(o_valid_), val.size() * 4, cudaMemcpyDeviceToHost, stream_));
+        nnz_host_.assign(insts.size(), 0);
+        UBQP_CK(cudaMemcpyAsync(nnz_host_.data(), ar_.at<unsigned long long>(o_nnz_),
+                                insts.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, stream_));
         UBQP_CK(cudaStreamSynchronize(stream_));
         for (size_t t = 0; t < insts.size(); ++t) {
             if (val[4 * t + 2] != 0.f) { set_error("instance %zu: Q or b holds NaN/Inf", t); return UBQP_ENONFINITE; }
@@ -686,9 +759,130 @@ class Solver {
         return UBQP_OK;
     }
 
+    // Tensor-core launch form by measurement (tc_cluster = 0): every feasible split-K cluster
+    // size S (each CTA keeps >= 2 k-blocks, at least one cluster fits) and, when its ring
+    // fits, the persistent many-tile kernel each run one warm-up and three timed launches of
+    // the contraction alone on this call's operands (raw output into a scratch buffer; no lane
+    // state is read or written); the fastest (shortest of its three) is kept.
+    int tune_tc_form()
+    {
+        if (!tc_ || tc_tiles_ == 0 || o_.tc_cluster > 0) return UBQP_OK;
+        const bool two = o_.precision == UBQP_BF16X2_TC;
+        int dev = 0, major = 0, minor = 0;
+        UBQP_CK(cudaGetDevice(&dev));
+        UBQP_CK(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+        UBQP_CK(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+        int kb_min = 1 << 30;
+        size_t raw_elems = 1;
+        for (const InstDev& I : inst_) {
+            kb_min = std::min(kb_min, I.ld / 64);
+            raw_elems = std::max(raw_elems, (size_t)I.nl * (size_t)I.ld);
+        }
+        char key[160];
+        snprintf(key, sizeof(key), "sm%d%d:sms%d:tiles%d:kb%d:bn%d:terms%d:inst%zu:ld%d", major, minor, num_sms_,
+                 tc_tiles_, kb_min, max_bn_, two ? 2 : 1, inst_.size(), max_ld_);
+        const char* path = getenv("UBQP_TUNE_CACHE");
+        int choice = -1;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            tune_load_file_locked(path);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) choice = it->second;
+        }
+        const int tcp_stages = tcp_pick_stages(max_bn_, two);
+        if (choice >= 0 && choice <= 8 && !(choice == 0 && tcp_stages < 2)) {
+            cluster_tuned_ = 2;
+        } else {
+            float* raw = nullptr;
+            UBQP_CK(cudaMallocAsync((void**)&raw, raw_elems * sizeof(float), stream_));
+            AsyncTemp guard;
+            guard.hold(raw, stream_);
+            TcArgs a;
+            memset(&a, 0, sizeof(a));
+            a.inst = ar_.at<TcInst>(o_tcinst_);
+            a.ninst = (int)inst_.size();
+            a.max_bn = max_bn_;
+            a.two_any = two ? 1 : 0;
+            a.lanes = ar_.at<LaneDev>(o_lanes_);
+            a.raw = raw;
+            a.err = ar_.at<int32_t>(o_tcerr_);
+            a.P = make_params(o_, nullptr);
+            cudaEvent_t e0, e1;
+            UBQP_CK(cudaEventCreate(&e0));
+            UBQP_CK(cudaEventCreate(&e1));
+            float best = INFINITY;
+            for (int S = 0; S <= 8; ++S) {
+                cudaError_t le = cudaSuccess;
+                if (S == 0) {
+                    if (tcp_stages < 2) continue;
+                    a.stages = tcp_stages;
+                    a.tmem_cols = tcp_tmem_cols(two);
+                } else {
+                    if (S > 1 && kb_min / S < 2) break;
+                    a.stages = tc_pick_stages(max_bn_, two);
+                    a.tmem_cols = tc_tmem_cols(max_bn_, two);
+                    if (tc_max_active_clusters(max_bn_, two, a.stages, S) < 1) continue;
+                }
+                const int grid = S == 0 ? tcp_grid(a, tc_tiles_) : 0;
+                float t = INFINITY;
+                for (int rep = 0; rep < 4 && le == cudaSuccess; ++rep) {
+                    le = cudaEventRecord(e0, stream_);
+                    if (le == cudaSuccess)
+                        le = S == 0 ? tcp_launch(a, tc_tiles_, grid, stream_) : tc_launch(a, tc_tiles_, S, stream_);
+                    if (le == cudaSuccess) le = cudaEventRecord(e1, stream_);
+                    if (le == cudaSuccess) le = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (le == cudaSuccess && rep > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+                        t = std::min(t, ms * 1e3f);
+                }
+                if (le != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    set_error("tensor-core form probe (S = %d) failed: %s", S, cudaGetErrorString(le));
+                    return UBQP_ECUDA;
+                }
+                cluster_probe_us_[S] = t;
+                if (t < best) {
+                    best = t;
+                    choice = S;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            int32_t err = 0;
+            UBQP_CK(cudaMemcpy(&err, a.err, sizeof(err), cudaMemcpyDeviceToHost));
+            if (err) {
+                set_error("a bounded wait in the tensor-core kernel ran out while tuning its launch form");
+                return UBQP_ETIMEOUT;
+            }
+            guard.release();
+            UBQP_CK(cudaFreeAsync(raw, stream_));
+            if (choice < 0) choice = 1;
+            cluster_tuned_ = 1;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = choice;
+            tune_save_file_locked(path);
+        }
+        if (choice == 0) {
+            tc_S_ = 1;
+            tcp_ = true;
+            tc_stages_ = tcp_stages;
+        } else {
+            tc_S_ = choice;
+            tcp_ = false;
+            tc_stages_ = tc_pick_stages(max_bn_, two);
+        }
+        return UBQP_OK;
+    }
+
     int run()
     {
         if (loop_) return run_loop();
+        if (solo_) return run_solo();
+        {
+            const int rc = tune_tc_form();
+            if (rc) return rc;
+        }
         TickArgs ta;
         ta.lanes = ar_.at<LaneDev>(o_lanes_);
         ta.items = ar_.at<int2>(o_items_);
@@ -876,6 +1070,73 @@ class Solver {
         return UBQP_OK;
     }
 
+    // one FP32 lane on the single-lane persistent kernel: each cooperative launch runs up to
+    // lane_budget (1024) steps; the host checks between launches
+    int run_solo()
+    {
+        SoloArgs sa;
+        memset(&sa, 0, sizeof(sa));
+        sa.lane = ar_.at<LaneDev>(o_lanes_);
+        sa.rows_per_item = rows_per_item_;
+        sa.nblk = solo_nblk_;
+        sa.budget = probe_ticks_ > 0 ? probe_ticks_ : (o_.lane_budget > 0 ? o_.lane_budget : 1024);
+        sa.grid = solo_grid_;
+        int32_t* ctl = ar_.at<int32_t>(o_solo_);
+        sa.bar = reinterpret_cast<unsigned*>(ctl);
+        sa.err = ctl + 2;
+        sa.active_after = ctl + 3;
+        sa.wait_ns = o_.wait_limit_us > 0 ? 1000ull * (unsigned long long)o_.wait_limit_us : 5000000000ull;
+        sa.P = make_params(o_, ar_.at<int64_t>(o_hist_));
+        const bool prof = o_.profile_kernels != 0;
+        if (prof) sa.P.bytes = ar_.at<unsigned long long>(o_bytes_);
+        UBQP_CK(prepare_solo(max_ld_));
+        UBQP_CK(cudaMallocHost(&h_active_, 2 * sizeof(int32_t)));
+        if (prof) {
+            evA_.resize(2);
+            for (auto& e : evA_) UBQP_CK(cudaEventCreate(&e));
+        }
+        UBQP_CK(cudaEventRecord(ev0_, stream_));
+        const int64_t cap = (int64_t)(o_.jacobi_max_iter + 2) +
+                            (int64_t)(o_.max_outer + 1) * (int64_t)(o_.max_inner + o_.lobpcg_max_iter + 8);
+        int64_t granted = 0;
+        for (;;) {
+            if (prof) UBQP_CK(cudaEventRecord(evA_[0], stream_));
+            UBQP_CK(launch_solo(sa, max_ld_, stream_));
+            if (prof) UBQP_CK(cudaEventRecord(evA_[1], stream_));
+            UBQP_CK(cudaMemcpyAsync(h_active_, ctl + 2, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream_));
+            launches_ += 1;
+            granted += sa.budget;
+            UBQP_CK(cudaStreamSynchronize(stream_));
+            if (prof) {
+                float ms = 0.f;
+                UBQP_CK(cudaEventElapsedTime(&ms, evA_[0], evA_[1]));
+                phase_a_ms_ += ms;
+                phase_a_launches_ += 1;
+            }
+            if (h_active_[0]) {
+                set_error("a bounded wait in the single-lane kernel ran out (limit %.0f us)", (double)sa.wait_ns * 1e-3);
+                return UBQP_ETIMEOUT;
+            }
+            if (probe_ticks_ > 0) break;
+            bool stop = false;
+            int rc = check_target(stop);
+            if (rc) return rc;
+            if (stop) break;
+            if (h_active_[1] == 0) break;
+            if (granted > cap) {
+                set_error("step cap %lld exceeded", (long long)cap);
+                return UBQP_ETIMEOUT;
+            }
+        }
+        UBQP_CK(cudaEventRecord(ev1_, stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0_, ev1_);
+        ms_device_ = ms;
+        ticks_ = -1;   // filled from the lane's own step count
+        return UBQP_OK;
+    }
+
     // FP32 lanes on the persistent lane loop: each launch (seed + loop, one graph) lets
     // every lane take up to loop_budget_ steps; the host checks between launches
     int run_loop()
@@ -900,6 +1161,7 @@ class Solver {
         la.err = ctr + 2;
         la.budget_left = ar_.at<int32_t>(o_budget_);
         la.sym = sym_ ? ar_.at<SymLane>(o_symlanes_) : nullptr;
+        la.wait_ns = o_.wait_limit_us > 0 ? 1000ull * (unsigned long long)o_.wait_limit_us : 5000000000ull;
         la.P = make_params(o_, ar_.at<int64_t>(o_hist_));
         const bool prof = o_.profile_kernels != 0;
         if (prof) la.P.bytes = ar_.at<unsigned long long>(o_bytes_);
@@ -947,7 +1209,7 @@ class Solver {
             int32_t err = 0;
             UBQP_CK(cudaMemcpy(&err, la.err, sizeof(err), cudaMemcpyDeviceToHost));
             if (err) {
-                set_error("a bounded wait in the lane loop ran out");
+                set_error("a bounded wait in the lane loop ran out (limit %.0f us)", (double)la.wait_ns * 1e-3);
                 return UBQP_ETIMEOUT;
             }
             if (probe_ticks_ > 0) break;
@@ -1035,6 +1297,11 @@ class Solver {
             s->jacobi_iters += S.jac_iters;
             s->floor_steps += S.floor_steps;
             s->lanes_capped += S.status == 1 ? 1 : 0;
+            // the sparse minimum of the step's matrix-vector product (the stored entries of
+            // Q_off as 4-byte values with 2-byte column indices, and 8 vectors of n floats)
+            const int64_t nnz = (int64_t)nnz_host_[(size_t)lane_inst_[l]];
+            s->alg_bytes += S.updates * (6 * nnz + 32 * (int64_t)lanes_[l].n);
+            s->alg_flops += S.updates * 2 * nnz;
         }
         s->lanes = nlanes_;
         int64_t most = 0;
@@ -1054,9 +1321,11 @@ class Solver {
         UBQP_CK(cudaStreamSynchronize(stream_));
         s->phase_a_flops = (int64_t)fl;
         s->cluster_size = tc_ ? tc_S_ : 0;
+        s->cluster_tuned = cluster_tuned_;
+        for (int c = 0; c < 9; ++c) s->cluster_probe_us[c] = cluster_probe_us_[c];
         s->tc_kernel = tc_ ? (tcp_ ? 2 : 1) : 0;
         s->sym_storage = sym_ ? 1 : 0;
-        s->gemv_kernel = tc_ ? 0 : (loop_ ? 2 : 1);
+        s->gemv_kernel = tc_ ? 0 : (solo_ ? 3 : (loop_ ? 2 : 1));
         UBQP_CK(cudaMemcpyAsync(s->inner_hist, ar_.at<int64_t>(o_hist_), sizeof(s->inner_hist), cudaMemcpyDeviceToHost,
                                 stream_));
         UBQP_CK(cudaStreamSynchronize(stream_));
@@ -1139,6 +1408,9 @@ class Solver {
     int max_ld_ = 32;
     int rows_per_item_ = 32;
     bool loop_ = false;          // FP32 lanes on the persistent lane loop
+    bool solo_ = false;          // one FP32 lane on the single-lane persistent kernel
+    int solo_grid_ = 0, solo_nblk_ = 0;
+    size_t o_solo_ = 0;
     int loop_grid_ = 0, loop_budget_ = 0;
     uint64_t loop_cap_ = 0;
     int nitems_ = 0;
@@ -1168,7 +1440,12 @@ class Solver {
     size_t o_symctr_ = 0, o_symlanes_ = 0;
     size_t ntact_total_ = 0, o_ntact_ = 0, o_row0_ = 0, o_valargs_ = 0, o_refargs_ = 0;
     std::vector<int32_t> ntact_host_;   // staged until the copy completes (the stream syncs in run)
+    std::vector<unsigned long long> nnz_host_;   // stored off-diagonal entries per instance
+    std::vector<int> lane_inst_;                 // instance of each lane
+    size_t o_nnz_ = 0;
     int tcp_grid_ = 0;
+    int cluster_tuned_ = 0;               // 0 rule or caller's choice, 1 measured now, 2 from the cache
+    float cluster_probe_us_[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     size_t o_final_lane0_ = 0, o_final_nl_ = 0, o_final_obj_ = 0, o_final_best_ = 0, o_final_xptr_ = 0,
            o_final_xbuf_ = 0;
 };
@@ -1212,6 +1489,7 @@ void ubqp_opts_default(ubqp_opts* o)
     o->lane_budget = 0;
     o->rows_per_item = 0;
     o->sym_storage = 1;
+    o->wait_limit_us = 0;
     o->target_objective = INFINITY;
     o->stream = nullptr;
     o->mu = nullptr;
@@ -1420,7 +1698,6 @@ int ubqp_penalty_probe(const double* Qp, const double* bp, const double* p, cons
     ubqp_opts o;
     if (o_in) o = *o_in;
     else ubqp_opts_default(&o);
-    o.precision = UBQP_FP32;
     o.restarts = 1;
     if (o.max_outer < 1) o.max_outer = 1;
     std::vector<InstIn> insts(1);
@@ -1428,7 +1705,7 @@ int ubqp_penalty_probe(const double* Qp, const double* bp, const double* p, cons
     std::vector<LaneIn> lanes(1);
     lanes[0] = LaneIn{0, 0, PH_EVAL, 0, x, p, STOP_LOB, 0};
     Solver S(o);
-    int rc = S.setup(insts, lanes, false);
+    int rc = S.setup(insts, lanes, o.precision != UBQP_FP32);
     if (rc) return rc;
     rc = S.run();
     if (rc) return rc;
@@ -1470,45 +1747,81 @@ int ubqp_initial_point(const double* Q, const double* b, const double* mu, int64
     return rc;
 }
 
+// the rows per work item of a gradient launch: the smallest power of two from 8 that keeps
+// the items of all points within about 8 per SM (at most 256, one epilogue thread per row)
+static int grad_rows_per_item(int64_t n, int64_t batch, int sms)
+{
+    int rb = 8;
+    while (rb < 256 && batch * n / rb > 8 * (int64_t)sms) rb *= 2;
+    return rb;
+}
+
+static int check_grad_args(const char* who, const void* Q, const void* b, const void* p, const void* x, int64_t n,
+                           int64_t batch, int dtype, const void* h_out, const void* g_out, bool need_dev)
+{
+    if (!Q || !x || n < 1 || n > 65536 || batch < 1 || (dtype != UBQP_DTYPE_F32 && dtype != UBQP_DTYPE_F64)) {
+        set_error("%s: need Q, x, 1 <= n <= 65536, batch >= 1 and dtype UBQP_DTYPE_F32 or UBQP_DTYPE_F64", who);
+        return UBQP_EINVAL;
+    }
+    const uintptr_t es = dtype == UBQP_DTYPE_F64 ? 8 : 4;
+    const void* ptrs[6] = {Q, b, p, x, h_out, g_out};
+    for (const void* q : ptrs)
+        if (q && (reinterpret_cast<uintptr_t>(q) % es) != 0) {
+            set_error("%s: every pointer must be aligned to its element size", who);
+            return UBQP_EINVAL;
+        }
+    if (need_dev)
+        for (const void* q : ptrs)
+            if (q && !is_device_ptr(q)) {
+                set_error("%s: all pointers must be device memory", who);
+                return UBQP_EINVAL;
+            }
+    return UBQP_OK;
+}
+
 int ubqp_penalized_eval(const void* Q, const void* b, const void* p, const void* x, int64_t n, int64_t batch,
                         int dtype, void* h_out, void* g_out, void* stream)
 {
     g_last_error[0] = 0;
-    if (!Q || !x || n < 1 || n > 65536 || batch < 1 || (dtype != UBQP_DTYPE_F32 && dtype != UBQP_DTYPE_F64)) {
-        set_error("ubqp_penalized_eval: bad arguments");
-        return UBQP_EINVAL;
-    }
-    if (!is_device_ptr(Q) || !is_device_ptr(x) || (b && !is_device_ptr(b)) || (p && !is_device_ptr(p)) ||
-        (h_out && !is_device_ptr(h_out)) || (g_out && !is_device_ptr(g_out))) {
-        set_error("ubqp_penalized_eval: all pointers must be device memory");
-        return UBQP_EINVAL;
-    }
+    int rc = check_grad_args("ubqp_penalized_eval", Q, b, p, x, n, batch, dtype, h_out, g_out, true);
+    if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t es = dtype == UBQP_DTYPE_F64 ? 8 : 4;
+    if ((size_t)n * es > 227 * 1024) {
+        set_error("ubqp_penalized_eval: one point (n = %lld) does not fit in shared memory", (long long)n);
+        return UBQP_ENOTSUP;
+    }
     int dev = 0, sms = 148;
     UBQP_CK(cudaGetDevice(&dev));
     UBQP_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int rb = 8;
-    while (rb < 256 && (int64_t)batch * n / rb > 8 * sms) rb *= 2;
-    const int nblk = (int)((n + rb - 1) / rb);
+    const int rb = grad_rows_per_item(n, batch, sms);
+    const int64_t nblk = (n + rb - 1) / rb;
+    if (batch * nblk > INT32_MAX) {
+        set_error("ubqp_penalized_eval: batch x row blocks exceeds 2^31");
+        return UBQP_EINVAL;
+    }
     std::vector<LaneDev> lanes((size_t)batch);
     std::vector<int2> items;
-    items.reserve((size_t)batch * nblk);
+    items.reserve((size_t)(batch * nblk));
     const size_t bytes_lanes = round_up((size_t)batch * sizeof(LaneDev), 256);
-    const size_t bytes_items = round_up((size_t)batch * nblk * sizeof(int2), 256);
-    const size_t bytes_part = (size_t)batch * nblk * sizeof(Partial);
+    const size_t bytes_items = round_up((size_t)(batch * nblk) * sizeof(int2), 256);
+    const size_t bytes_queue = 256;
+    const size_t bytes_part = (size_t)(batch * nblk) * sizeof(Partial);
     char* scratch = nullptr;
-    UBQP_CK(cudaMallocAsync((void**)&scratch, bytes_lanes + bytes_items + bytes_part, s));
+    UBQP_CK(cudaMallocAsync((void**)&scratch, bytes_lanes + bytes_items + bytes_queue + bytes_part, s));
+    AsyncTemp guard;
+    guard.hold(scratch, s);
     LaneDev* d_lanes = reinterpret_cast<LaneDev*>(scratch);
     int2* d_items = reinterpret_cast<int2*>(scratch + bytes_lanes);
-    Partial* d_part = reinterpret_cast<Partial*>(scratch + bytes_lanes + bytes_items);
+    int32_t* d_queue = reinterpret_cast<int32_t*>(scratch + bytes_lanes + bytes_items);
+    Partial* d_part = reinterpret_cast<Partial*>(scratch + bytes_lanes + bytes_items + bytes_queue);
     for (int64_t r = 0; r < batch; ++r) {
         LaneDev& L = lanes[(size_t)r];
         memset(&L, 0, sizeof(L));
         L.n = (int)n;
         L.ld = (int)n;
         L.mode = MODE_GRAD;
-        L.nblk = nblk;
+        L.nblk = (int)nblk;
         L.part = d_part + (size_t)r * nblk;
         L.gQ = Q;
         L.gb = b;
@@ -1516,10 +1829,11 @@ int ubqp_penalized_eval(const void* Q, const void* b, const void* p, const void*
         L.gx = static_cast<const char*>(x) + (size_t)r * n * es;
         L.gg = g_out ? static_cast<char*>(g_out) + (size_t)r * n * es : nullptr;
         L.gld = (int)n;
-        for (int blk = 0; blk < nblk; ++blk) items.push_back(make_int2((int)r, blk));
+        for (int64_t blk = 0; blk < nblk; ++blk) items.push_back(make_int2((int)r, (int)blk));
     }
-    cudaError_t e = cudaMemcpyAsync(d_lanes, lanes.data(), lanes.size() * sizeof(LaneDev), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    UBQP_CK(cudaMemcpyAsync(d_lanes, lanes.data(), lanes.size() * sizeof(LaneDev), cudaMemcpyHostToDevice, s));
+    UBQP_CK(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    UBQP_CK(cudaMemsetAsync(d_queue, 0, 2 * sizeof(int32_t), s));
     TickArgs ta;
     memset(&ta, 0, sizeof(ta));
     ta.lanes = d_lanes;
@@ -1528,15 +1842,33 @@ int ubqp_penalized_eval(const void* Q, const void* b, const void* p, const void*
     ta.rows_per_item = rb;
     ta.nlanes = (int)batch;
     ta.max_ld = (int)n;
-    if (e == cudaSuccess) e = launch_phase_a_grad(ta, dtype, n, s);
-    if (e == cudaSuccess && h_out) e = launch_grad_reduce(d_lanes, (int)batch, h_out, dtype, s);
-    cudaError_t ef = cudaFreeAsync(scratch, s);
-    if (e == cudaSuccess) e = ef;
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-        set_error("ubqp_penalized_eval: %s", cudaGetErrorString(e));
-        return UBQP_ECUDA;
+    ta.work = d_queue;
+    ta.done = d_queue + 1;
+    UBQP_CK(launch_phase_a_grad(ta, dtype, n, s));
+    if (h_out) UBQP_CK(launch_grad_reduce(d_lanes, (int)batch, h_out, dtype, s));
+    guard.release();
+    UBQP_CK(cudaFreeAsync(scratch, s));
+    UBQP_CK(cudaStreamSynchronize(s));
+    return UBQP_OK;
+}
+
+int ubqp_penalized_vjp(const void* x, const void* g, const void* grad_h, int64_t n, int64_t batch, int dtype,
+                       void* gx_out, void* gp_out, void* gb_out, void* stream)
+{
+    g_last_error[0] = 0;
+    if (!x || !grad_h || (gx_out && !g) || n < 1 || batch < 1 || (dtype != UBQP_DTYPE_F32 && dtype != UBQP_DTYPE_F64)) {
+        set_error("ubqp_penalized_vjp: need x, grad_h (and g when gx_out is set), n >= 1, batch >= 1 and a valid dtype");
+        return UBQP_EINVAL;
     }
+    const void* ptrs[6] = {x, g, grad_h, gx_out, gp_out, gb_out};
+    for (const void* q : ptrs)
+        if (q && !is_device_ptr(q)) {
+            set_error("ubqp_penalized_vjp: all pointers must be device memory");
+            return UBQP_EINVAL;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    UBQP_CK(launch_penalized_vjp(x, g, grad_h, n, batch, dtype, gx_out, gp_out, gb_out, s));
+    UBQP_CK(cudaStreamSynchronize(s));
     return UBQP_OK;
 }
 

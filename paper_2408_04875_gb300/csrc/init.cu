@@ -82,14 +82,17 @@ __device__ __forceinline__ void atomic_max_nonneg(float* addr, float v)
 }
 
 // out[0] = max |Q_ij - Q_ji|, out[1] = max |Q_ij| (i != j), out[2] = nonfinite flag, out[3] = max|Q|
+// and *nnz += the row's stored (nonzero) off-diagonal entries
 __device__ __forceinline__ void validate_row(const double* __restrict__ Q, const double* __restrict__ b, int n,
-                                             float* out, int i)
+                                             float* out, unsigned long long* nnz, int i)
 {
     __shared__ float sh[8];
     float asym = 0.f, offmax = 0.f, qmax = 0.f, bad = 0.f;
+    unsigned cnt = 0;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
         double q = Q[(size_t)i * n + j];
         double qt = Q[(size_t)j * n + i];
+        cnt += (j != i && q != 0.0) ? 1u : 0u;
         if (!isfinite(q)) bad = 1.f;
         float aq = (float)fabs(q);
         qmax = fmaxf(qmax, aq);
@@ -98,6 +101,8 @@ __device__ __forceinline__ void validate_row(const double* __restrict__ Q, const
         asym = fmaxf(asym, isfinite(dq) ? (float)dq : 0.f);
     }
     if (threadIdx.x == 0 && b && !isfinite(b[i])) bad = 1.f;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(nnz, (unsigned long long)cnt);
     asym = block_max<256>(asym, sh);
     offmax = block_max<256>(offmax, sh);
     bad = block_max<256>(bad, sh);
@@ -208,7 +213,7 @@ __global__ void validate_kernel(const ValArgs* v, const int64_t* row0, int ninst
 {
     const int t = batch_instance(row0, ninst, blockIdx.x);
     const ValArgs& a = v[t];
-    validate_row(a.Q, a.b, a.n, a.out, (int)(blockIdx.x - row0[t]));
+    validate_row(a.Q, a.b, a.n, a.out, a.nnz, (int)(blockIdx.x - row0[t]));
 }
 
 __global__ void reformulate_kernel(const RefArgs* args, const int64_t* row0, int ninst)

@@ -13,7 +13,9 @@
 // launch; the last lane to stop pushes one poison entry per CTA and every CTA leaves at
 // its poison.  Ring slots carry a sequence number (position / capacity + 1) in their high
 // 32 bits, so a consumer that popped position q waits until the slot holds position q's
-// entry; every wait gives up after kLoopWaitNs, sets the error flag and ends the CTA.
+// entry; every wait gives up after A.wait_ns (5 s unless the caller sets a limit), sets the
+// error flag and ends the CTA.  No asynchronous copy is in flight during that wait, so a CTA
+// can always leave there; every other CTA then ends at its own next wait.
 //
 // With symmetric storage (A.sym set) a step that multiplies by Q_off has two stages: one
 // entry per kSymGroup stored tiles (entry block < kBlockFlag), whose products go to the lane's partial
@@ -29,7 +31,6 @@
 
 namespace ubqp {
 
-constexpr uint64_t kLoopWaitNs = 5000000000ull;   // 5 s
 constexpr uint32_t kLaneSkip = 0xFFFEu;            // seeded block of a finished lane
 constexpr uint32_t kLanePoison = 0xFFFFu;          // ends the CTA that pops it
 constexpr uint32_t kBlockFlag = 0x8000u;           // symmetric storage: a row-block entry
@@ -131,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
             for (;;) {
                 v = ld_acquire(A.ring + (pos & mask));
                 if ((v & 0xFFFFFFFF00000000ull) == want) break;
-                if (loop_clock() - t0 > kLoopWaitNs) {
+                if (loop_clock() - t0 > A.wait_ns) {
                     atomicExch(A.err, 1);
                     v = (unsigned long long)kLanePoison << 16;
                     break;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
         } else {
             item_load_u(L, su);
             __syncthreads();
-            item_rows(L, ph, row0, rows, su, sv);
+            item_rows_solver(L, ph, row0, rows, su, sv, threadIdx.x & 31, threadIdx.x >> 5);
             __syncthreads();
         }
         item_finish(L, ph, k, blk, row0, rows, sv, A.P, sym_parts);

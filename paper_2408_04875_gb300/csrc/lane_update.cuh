@@ -292,7 +292,11 @@ static __device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, 
         int exit_code = -1;
         if (R.m[0] / S.rho < P.tol_inner) exit_code = 0;
         else if (k >= P.max_inner) exit_code = 1;
-        else if (L.method == 0 && k >= 1) {
+        else if (L.method == 1 && k >= 1) {
+            // Alg. 1 ends when the projected step left x unchanged (s = x_k - x_{k-1} = 0): in
+            // FP32 a step g / (2 h_p) below half an ulp of x stalls the iteration
+            if (csum_value(R.s[0]) == 0.f) exit_code = 2;
+        } else if (L.method == 0 && k >= 1) {
             float ss = csum_value(R.s[0]), sy = csum_value(R.s[1]), yy = csum_value(R.s[2]);
             if (ss == 0.f) exit_code = 2;
             else {
@@ -330,75 +334,63 @@ static __device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, 
     }
 }
 
-// The update of one lane by one CTA of 32..kBThreads threads (a multiple of 32).  Called by
-// the stand-alone update kernel and by the CTA that completes a GEMV lane's step.  With at
-// most blockDim.x partials every thread merges at most one, so the reduction order (and the
-// result) does not depend on the CTA size.
-static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& P, int32_t* active_count)
+// The reduction of a lane's phase-A partials (all threads of the CTA; the result is in R when
+// the call returns).  Thread t merges partials t, t + blockDim.x, ... in order, then the warps
+// and the CTA's warps in order: the result depends only on the partials and the CTA size.
+static __device__ void reduce_partials(const Partial* part, int nblk, int ph, Partial& R)
 {
-    __shared__ LaneState S;
-    __shared__ Partial R;
-    __shared__ Decision D;
-    __shared__ int32_t phase0;
-
-    if (L.mode == MODE_GRAD) return;
-    if (threadIdx.x == 0) {
-        S = *L.st;
-        phase0 = S.phase;
-    }
-    __syncthreads();
-    const int ph = phase0;
-    if (ph == PH_DONE) return;
-
-    // ---- reduce the partials of this lane
-    {
-        Acc a;
-        a.zero();
-        const int ns = phase_nsum(ph), nm = phase_nmax(ph);
-        for (int b = threadIdx.x; b < L.nblk; b += blockDim.x) {
-            const Partial& p = L.part[b];
-#pragma unroll
-            for (int t = 0; t < 12; ++t)
-                if (t < ns) a.s[t] = csum_merge(a.s[t], p.s[t]);
-#pragma unroll
-            for (int t = 0; t < 6; ++t)
-                if (t < nm) a.m[t] = fmaxf(a.m[t], p.m[t]);
-            a.f += p.f;
-        }
-        __shared__ float2 sh_s[kBWarps][12];
-        __shared__ float sh_m[kBWarps][6];
-        __shared__ double sh_f[kBWarps];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Acc a;
+    a.zero();
+    const int ns = phase_nsum(ph), nm = phase_nmax(ph);
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+        const Partial& p = part[b];
 #pragma unroll
         for (int t = 0; t < 12; ++t)
-            if (t < ns) a.s[t] = csum_shfl_reduce(a.s[t]);
+            if (t < ns) a.s[t] = csum_merge(a.s[t], p.s[t]);
 #pragma unroll
         for (int t = 0; t < 6; ++t)
-            if (t < nm) a.m[t] = max_shfl_reduce(a.m[t]);
-        if (ph == PH_EVAL) a.f = dsum_shfl_reduce(a.f);
-        if (lane == 0) {
-#pragma unroll
-            for (int t = 0; t < 12; ++t) sh_s[warp][t] = a.s[t];
-#pragma unroll
-            for (int t = 0; t < 6; ++t) sh_m[warp][t] = a.m[t];
-            sh_f[warp] = a.f;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int t = 0; t < 12; ++t) R.s[t] = make_float2(0.f, 0.f);
-            for (int t = 0; t < 6; ++t) R.m[t] = 0.f;
-            R.f = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                for (int t = 0; t < 12; ++t) R.s[t] = csum_merge(R.s[t], sh_s[w][t]);
-                for (int t = 0; t < 6; ++t) R.m[t] = fmaxf(R.m[t], sh_m[w][t]);
-                if (ph == PH_EVAL) R.f += sh_f[w];
-            }
-            decide(L, S, R, P, D);
-        }
-        __syncthreads();
+            if (t < nm) a.m[t] = fmaxf(a.m[t], p.m[t]);
+        a.f += p.f;
     }
-    // ---- element-wise update
+    __shared__ float2 sh_s[kBWarps][12];
+    __shared__ float sh_m[kBWarps][6];
+    __shared__ double sh_f[kBWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int t = 0; t < 12; ++t)
+        if (t < ns) a.s[t] = csum_shfl_reduce(a.s[t]);
+#pragma unroll
+    for (int t = 0; t < 6; ++t)
+        if (t < nm) a.m[t] = max_shfl_reduce(a.m[t]);
+    if (ph == PH_EVAL) a.f = dsum_shfl_reduce(a.f);
+    if (lane == 0) {
+#pragma unroll
+        for (int t = 0; t < 12; ++t) sh_s[warp][t] = a.s[t];
+#pragma unroll
+        for (int t = 0; t < 6; ++t) sh_m[warp][t] = a.m[t];
+        sh_f[warp] = a.f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int t = 0; t < 12; ++t) R.s[t] = make_float2(0.f, 0.f);
+        for (int t = 0; t < 6; ++t) R.m[t] = 0.f;
+        R.f = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            for (int t = 0; t < 12; ++t) R.s[t] = csum_merge(R.s[t], sh_s[w][t]);
+            for (int t = 0; t < 6; ++t) R.m[t] = fmaxf(R.m[t], sh_m[w][t]);
+            if (ph == PH_EVAL) R.f += sh_f[w];
+        }
+    }
+    __syncthreads();
+}
+
+// The element-wise part of a lane's update for the decision D, over elements [ia, ib) (and,
+// for the plain projected step, 16-byte groups [qa, qb) of the padded length).  Every element
+// is computed on its own, so a lane's result does not depend on how the range is split.
+static __device__ void lane_apply(const LaneDev& L, const Params& P, const Decision& D, int ia, int ib, int qa, int qb)
+{
     const int n = L.n, ld = L.ld;
+    (void)P;
     float* vec = L.vec;
     const int act = D.act, usrc = D.usrc;
     if (act == A_STEP_PABB && usrc == U_X) {
@@ -410,13 +402,13 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
         const float4* G4 = reinterpret_cast<const float4*>(vec + (size_t)V_G * ld);
         float4* U4 = reinterpret_cast<float4*>(vec + (size_t)V_U * ld);
         // two groups per thread per pass, both loaded before either is stored
-        const int n4 = ld >> 2, nt = blockDim.x;
-        for (int q0 = threadIdx.x; q0 < n4; q0 += 2 * nt) {
+        const int nt = blockDim.x;
+        for (int q0 = qa + (int)threadIdx.x; q0 < qb; q0 += 2 * nt) {
             float4 xs[2], gs[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int q = q0 + h * nt;
-                if (q < n4) {
+                if (q < qb) {
                     xs[h] = X4[q];
                     gs[h] = G4[q];
                 }
@@ -424,7 +416,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
             const int q = q0 + h * nt;
-            if (q >= n4) break;
+            if (q >= qb) break;
             const float4 x = xs[h], g = gs[h];
             XP4[q] = x;
             float4 y;
@@ -449,7 +441,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
             }
         }
     }
-    for (int i = threadIdx.x; i < n && !(act == A_STEP_PABB && usrc == U_X); i += blockDim.x) {
+    for (int i = ia + (int)threadIdx.x; i < ib && !(act == A_STEP_PABB && usrc == U_X); i += blockDim.x) {
         float x = vec[V_X * ld + i];
         if (act & A_TRACE) L.trace_x[(size_t)D.trace_k * n + i] = x;
         if (act & A_COPY_W_X) {
@@ -527,6 +519,35 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
             }
         }
     }
+}
+
+// The update of one lane by one CTA of 32..kBThreads threads (a multiple of 32).  Called by
+// the stand-alone update kernel and by the CTA that completes a GEMV lane's step.  With at
+// most blockDim.x partials every thread merges at most one, so the reduction order (and the
+// result) does not depend on the CTA size.
+static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& P, int32_t* active_count)
+{
+    __shared__ LaneState S;
+    __shared__ Partial R;
+    __shared__ Decision D;
+    __shared__ int32_t phase0;
+
+    if (L.mode == MODE_GRAD) return;
+    if (threadIdx.x == 0) {
+        S = *L.st;
+        phase0 = S.phase;
+    }
+    __syncthreads();
+    const int ph = phase0;
+    if (ph == PH_DONE) return;
+
+    // ---- reduce the partials of this lane and take its decision
+    reduce_partials(L.part, L.nblk, ph, R);
+    if (threadIdx.x == 0) decide(L, S, R, P, D);
+    __syncthreads();
+    // ---- element-wise update
+    lane_apply(L, P, D, 0, L.n, 0, L.ld >> 2);
+    const int act = D.act;
     if (threadIdx.x == 0) {
         if ((act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
         S.updates += 1;

@@ -1,0 +1,162 @@
+// One FP32 lane (a single instance solved from a single start: the plain FP32 path) as one
+// persistent launch that runs many steps of Alg. 3 with Alg. 2 (or Alg. 1).
+//
+// A step is the matrix-vector product of the lane's phase over all CTAs, then its update.
+// CTA c owns row block c of the lane (rows_per_item rows, as many blocks as CTAs) and a
+// contiguous slice of the elements.  Per step:
+//   1. every CTA loads u, computes its block's rows and row epilogue with the same functions as
+//      the other schedulers (gemv_rows.cuh) and writes the block's partial record;
+//   2. grid barrier;
+//   3. every CTA reduces all partial records in the same order (reduce_partials) and takes the
+//      same decision (decide) on its own copy of the lane state, so all copies stay equal;
+//      then it applies the element-wise update (lane_apply) to its slice;
+//   4. grid barrier (u complete).
+// The arithmetic is that of the lock-step scheduler with the same rows per item, so both give
+// the same bits.  The launch is cooperative (every CTA resident), and each barrier wait is
+// bounded: when it runs out the CTA sets the error flag and leaves, and the others leave at
+// their own next wait.  With one CTA (n <= 256) the barriers are the CTA's own.
+//
+// Lane vectors and partial records written by one CTA are read by others within the launch,
+// so this file is compiled with plain loads cached in L2 only (-dlcm=cg); Q keeps its
+// non-coherent streaming loads.
+#include "gemv_rows.cuh"
+
+namespace ubqp {
+
+__device__ __forceinline__ uint64_t solo_clock()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// sense by generation: bar[0] counts arrivals, bar[1] is the generation released so far
+__device__ __forceinline__ bool solo_grid_sync(const SoloArgs& A, unsigned& gen, int* s_ok)
+{
+    __syncthreads();
+    if (gridDim.x == 1) return *s_ok != 0;
+    if (threadIdx.x == 0) {
+        const unsigned target = gen + 1u;
+        __threadfence();
+        if (atomicAdd(&A.bar[0], 1u) == gridDim.x - 1u) {
+            A.bar[0] = 0u;
+            __threadfence();
+            atomicExch(&A.bar[1], target);
+        } else {
+            const uint64_t t0 = solo_clock();
+            while (ld_acquire_u32(&A.bar[1]) != target) {
+                if (solo_clock() - t0 > A.wait_ns) {
+                    atomicExch(A.err, 1);
+                    *s_ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        gen = target;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) solo_lane_kernel(SoloArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* su = reinterpret_cast<float*>(smem_raw);
+    __shared__ double sv[kThreads];
+    __shared__ LaneState S;
+    __shared__ Partial R;
+    __shared__ Decision D;
+    __shared__ int s_ok;
+    __shared__ unsigned s_gen0;
+    const LaneDev& L = *A.lane;
+    if (threadIdx.x == 0) {
+        S = *L.st;
+        s_ok = 1;
+        s_gen0 = ld_acquire_u32(&A.bar[1]);
+    }
+    __syncthreads();
+    unsigned gen = s_gen0;
+    Params P = A.P;
+    if (blockIdx.x != 0) P.hist = nullptr;   // the subproblem histogram is counted once
+    const int ng = L.ld >> 2;
+    const int qa = (int)((int64_t)ng * blockIdx.x / gridDim.x), qb = (int)((int64_t)ng * (blockIdx.x + 1) / gridDim.x);
+    const int ia = min(4 * qa, L.n), ib = min(4 * qb, L.n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (int step = 0; step < A.budget; ++step) {
+        const int ph = S.phase;
+        if (ph == PH_DONE) break;
+        const int k = S.k;
+        // ---- phase A: this CTA's row block(s)
+        item_load_u(L, su);
+        __syncthreads();
+        for (int blk = blockIdx.x; blk < A.nblk; blk += gridDim.x) {
+            const int row0 = blk * A.rows_per_item;
+            const int rows = min(A.rows_per_item, L.n - row0);
+            item_rows_solver(L, ph, row0, rows, su, sv, lane, warp);
+            __syncthreads();
+            item_finish(L, ph, k, blk, row0, rows, sv, P);
+            __syncthreads();
+        }
+        if (!solo_grid_sync(A, gen, &s_ok)) break;
+        // ---- the update: the same reduction and decision in every CTA, then this CTA's slice
+        reduce_partials(L.part, A.nblk, ph, R);
+        if (threadIdx.x == 0) decide(L, S, R, P, D);
+        __syncthreads();
+        lane_apply(L, P, D, ia, ib, qa, qb);
+        if (threadIdx.x == 0) {
+            S.updates += 1;
+            if (blockIdx.x == 0 && (D.act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
+        }
+        if (!solo_grid_sync(A, gen, &s_ok)) break;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *L.st = S;
+        *A.active_after = S.phase != PH_DONE ? 1 : 0;
+    }
+}
+
+// CTAs and rows per block of a lane of n rows: one CTA up to 256 rows, else as many CTAs as
+// SMs (at most one per 8 rows), rows split evenly in multiples of 8 (or the caller's count)
+void solo_shape(int n, int rows_per_item, int sms, int* grid, int* rb, int* nblk)
+{
+    int r;
+    if (rows_per_item > 0) r = rows_per_item;
+    else if (n <= kThreads) r = n;
+    else {
+        const int g = std::min(sms, (n + 7) / 8);
+        r = ((n + g - 1) / g + 7) / 8 * 8;
+    }
+    r = std::max(1, std::min(r, kThreads));
+    *rb = r;
+    *nblk = (n + r - 1) / r;
+    *grid = std::min(*nblk, sms);
+}
+
+cudaError_t prepare_solo(int ld)
+{
+    const size_t smem = (size_t)ld * sizeof(float);
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(solo_lane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// every CTA must be resident: a cooperative launch fails instead of starting a grid that
+// could not be
+cudaError_t launch_solo(const SoloArgs& a, int ld, cudaStream_t s)
+{
+    SoloArgs args = a;
+    void* params[] = {&args};
+    return cudaLaunchCooperativeKernel((const void*)solo_lane_kernel, dim3((unsigned)a.grid), dim3(kThreads), params,
+                                       (size_t)ld * sizeof(float), s);
+}
+
+}  // namespace ubqp

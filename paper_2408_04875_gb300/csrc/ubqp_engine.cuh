@@ -38,6 +38,7 @@ struct ValArgs {
     const double* Q;
     const double* b;
     float* out;
+    unsigned long long* nnz;   // stored off-diagonal entries (nonzero Q_ij, i != j)
     int32_t n, pad_;
 };
 

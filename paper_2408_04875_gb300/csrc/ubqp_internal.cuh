@@ -423,8 +423,26 @@ struct LoopArgs {
     int32_t* err;               // set when a bounded wait runs out
     int32_t* budget_left;       // per lane
     const SymLane* sym;         // per lane, or null: dense rows
+    unsigned long long wait_ns; // limit of one wait for a ring slot
     Params P;
 };
+
+// one FP32 lane as one persistent cooperative launch (solo.cu)
+struct SoloArgs {
+    const LaneDev* lane;
+    int32_t rows_per_item;
+    int32_t nblk;
+    int32_t budget;             // steps this launch may take
+    int32_t grid;
+    unsigned* bar;              // grid barrier: [0] arrivals, [1] generation released
+    int32_t* err;               // set when a bounded wait runs out
+    int32_t* active_after;      // 1 when the lane is unfinished at the end of the launch
+    unsigned long long wait_ns; // limit of one barrier wait
+    Params P;
+};
+void solo_shape(int n, int rows_per_item, int sms, int* grid, int* rb, int* nblk);
+cudaError_t prepare_solo(int ld);
+cudaError_t launch_solo(const SoloArgs& a, int ld, cudaStream_t s);
 
 cudaError_t prepare_lane_loop(int max_ld);
 int lane_loop_grid(int max_ld);
@@ -432,5 +450,11 @@ cudaError_t launch_lane_loop(const LoopArgs& a, cudaStream_t s);   // seed + loo
 cudaError_t launch_phase_b(const TickArgs& a, int32_t* active_count, cudaStream_t s);
 cudaError_t launch_grad_reduce(const LaneDev* lanes, int nlanes, void* h_out, int dtype,
                                cudaStream_t s);
+cudaError_t launch_penalized_vjp(const void* x, const void* g, const void* go, int64_t n, int64_t batch, int dtype,
+                                 void* gx, void* gp, void* gb, cudaStream_t s);
+
+// the calling thread's last-error text (ubqp_last_error), shared by every entry point
+void set_error(const char* fmt, ...);
+void clear_error();
 
 }  // namespace ubqp

@@ -112,9 +112,9 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     (dict(jacobi_max_iter=0), "iteration caps"), (dict(max_ticks_per_sync=0), "max_ticks_per_sync"),
     (dict(max_ticks_per_sync=4097), "max_ticks_per_sync"), (dict(sigma_rel=-1.0), "sigma_rel"),
     (dict(gamma_margin=0.0), "gamma_margin"), (dict(tc_cluster=9), "tc_cluster"),
-    (dict(gemv_kernel=3), "gemv_kernel"), (dict(lane_budget=-1), "lane_budget"),
+    (dict(gemv_kernel=4), "gemv_kernel"), (dict(lane_budget=-1), "lane_budget"),
     (dict(rows_per_item=12), "rows_per_item"), (dict(rows_per_item=4), "rows_per_item"),
-    (dict(rows_per_item=264), "rows_per_item"),
+    (dict(rows_per_item=264), "rows_per_item"), (dict(wait_limit_us=-1), "wait_limit_us"),
 ])
 def test_invalid_options_are_rejected_before_any_cuda_call(built, kw, msg):
     """Every option outside its documented range returns UBQP_EINVAL with a message naming
