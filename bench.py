@@ -134,6 +134,38 @@ C4_WORKLOAD = ("batched restarts: n=2500, density 0.1, integers in [-100,100], b
                "FP32 accumulation, diagonal-only perturbation")
 
 
+def c4_time_to_objective(device: int, restarts: int = 256):
+    """The metric's second half, measured once outside the timed sweep: on the batched-restart
+    instance (n = 2500, density 0.1, diagonal-only perturbation), the plain FP32 path with one
+    start (x^0 of Eq. (gamma)) runs to completion; its objective f32 and device time are the
+    reference.  The tensor-core batch (256 starts, BF16 x2 terms) then runs until its best exact
+    objective is within 0.1 % of f32 (stop_at_target), and its device time to that point is
+    compared.  Clocks are sampled over both runs."""
+    import numpy as np
+    import torch
+    import paper_2408_04875_gb300 as ub
+    from paper_2408_04875_gb300 import instances as I
+    Q, _ = I.c4_instance(2500, 2)
+    mu = np.diag(np.diag(I.perturbation(Q, 2)))
+    starts = I.random_starts(2500, restarts - 1, 2)
+    Qd, Md, Sd = (torch.from_numpy(a).cuda() for a in (Q, mu, starts))
+    ub.solve(Qd, None, mu=Md, starts=Sd, restarts=restarts, precision=ub.BF16X2_TC, max_outer=1)   # warm
+    sampler = ClockSampler(device)
+    sampler.start()
+    _, f32, s32 = ub.solve(Qd, None, mu=Md)
+    target = f32 + 1e-3 * abs(f32)
+    _, ftc, stc = ub.solve(Qd, None, mu=Md, starts=Sd, restarts=restarts, precision=ub.BF16X2_TC,
+                           target_objective=target, stop_at_target=1)
+    clocks = sampler.stop()
+    t_tc = stc["ms_to_target"]
+    return {"workload": C4_WORKLOAD, "fp32_single_start": {"objective": f32, "ms": s32["ms_device"],
+                                                           "steps": s32["ticks"], "scheduler": s32["gemv_kernel"]},
+            "batched": {"restarts": restarts, "best_objective_at_stop": float(ftc), "ms_to_target": t_tc,
+                        "steps": stc["ticks"], "tc_kernel": stc["tc_kernel"], "cluster_size": stc["cluster_size"]},
+            "target": target, "speedup": (s32["ms_device"] / t_tc) if t_tc and t_tc > 0 else None,
+            "clocks": clocks}
+
+
 def run_c4(args):
     """Tensor-core batched path on the batched-restart workload, next to the FP32 path on the
     same instance with one start: throughput, and device time until the batch's best rounded
@@ -191,6 +223,126 @@ def run_c4(args):
                          "launches": pa_n, "avg_launch_us": pa_ms * 1e3 / max(pa_n, 1),
                          "algorithmic_flops_per_launch": flops / max(pa_n, 1)},
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+C3_WORKLOAD = ("differentiable objective: n=1000 dense Q in [-100,100], b in [-50,50], p uniform in [0,100], "
+               "64 box points, h and grad h (ubqp_penalized_eval)")
+
+
+def run_c3(args):
+    """The penalized objective and its gradient (the autograd forward) on the 64 C3 points,
+    FP32 and FP64: value = gradient entries per second (64 x n per call).  Each call is timed
+    with CUDA events on its stream (the entry point's scratch set-up, the GEMV kernel and the
+    reduction of h).  Algorithmic bytes: Q once per call plus the points and gradients; the
+    kernel reads Q once per point, from L2 after the first (reported as l2_bytes_per_call)."""
+    import numpy as np
+    import torch
+    import paper_2408_04875_gb300 as ub
+    from paper_2408_04875_gb300 import instances as I
+    torch.cuda.set_device(0)
+    Q, b = I.c3_instance(1000, 1)
+    X = I.box_points(1000, 64, 1)
+    p = np.random.default_rng(1).uniform(0, 100, 1000)
+    peak, peak_kind = _peaks()
+    out = {}
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        Qt, bt, pt, Xt = (torch.tensor(a, dtype=dt, device="cuda") for a in (Q, b, p, X))
+        for _ in range(max(args.warmup, 3)):
+            ub.penalized_eval(Qt, bt, pt, Xt)
+        n_calls = max(args.steps, 1) * 50
+        es = 8 if dt == torch.float64 else 4
+        ms = []
+        for _ in range(n_calls):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ub.penalized_eval(Qt, bt, pt, Xt)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms) * 1e-3
+        alg = es * (1000 * 1000 + 3 * 1000 + 2 * 64 * 1000) + es * 64
+        out[name] = {"us_per_call": t * 1e6, "value": 64 * 1000 / t, "algorithmic_bytes_per_call": alg,
+                     "achieved_gbs": alg / t / 1e9, "frac_hbm": alg / t / 1e9 / peak,
+                     "l2_bytes_per_call": 64 * es * 1000 * 1000, "l2_gbs": 64 * es * 1e6 / t / 1e9,
+                     "fp_gflops": 2 * 64 * 1e6 / t / 1e9}
+    line = {"metric": "penalized objective + gradient entries/s", "value": out["f32"]["value"],
+            "unit": "gradient entries/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["f32"]["us_per_call"] * 1e-3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": C3_WORKLOAD, "f64": out["f64"], "l2": "Q (4 MB FP32) is L2-resident"},
+            "roofline": {"bound": "hbm", "achieved": out["f32"]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": out["f32"]["frac_hbm"], "traffic": None, "kernel": "phase_a_gemv_kernel",
+                         "peak_kind": peak_kind, "f32": out["f32"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+PPA_WORKLOAD = ("PPA (Alg. 1) against PABB (Alg. 2) as the subproblem solver: the 10 n=250 and 10 n=500 "
+                "instances of the sweep on the FP32 path (one start), and the batched-restart instance at n=1000 "
+                "with 32 starts on the BF16 x2 tensor-core path")
+
+
+def run_ppa(args):
+    """The paper compares its two subproblem solvers (Tables 1-5: CPU time and objective).
+    Same comparison on the GPU paths: for each solver, the device time of the whole solve, the
+    inner iterations (gradient evaluations), the outer steps and the best objectives."""
+    import numpy as np
+    import torch
+    import paper_2408_04875_gb300 as ub
+    from paper_2408_04875_gb300 import instances as I
+    torch.cuda.set_device(0)
+    out = {}
+    Qs, mus = _instances(0, (250, 500), SEEDS_PER_SIZE)
+    Qd = [torch.from_numpy(Q).cuda() for Q in Qs]
+    Md = [torch.from_numpy(m).cuda() for m in mus]
+    Q4, _ = I.c4_instance(1000, 2)
+    M4 = np.diag(np.diag(I.perturbation(Q4, 2)))
+    S4 = I.random_starts(1000, 31, 2)
+    Q4d, M4d, S4d = (torch.from_numpy(a).cuda() for a in (Q4, M4, S4))
+    for name, method in (("pabb", ub.PABB), ("ppa", ub.PPA)):
+        ub.solve_batched(Qd[:2], None, Md[:2], method=method, max_outer=2)   # warm
+        _, f2, s2 = ub.solve_batched(Qd, None, Md, method=method)
+        _, f4, s4 = ub.solve(Q4d, None, mu=M4d, starts=S4d, restarts=32, precision=ub.BF16X2_TC, method=method)
+        out[name] = {"fp32_sweep": {"ms": s2["ms_device"], "inner_iters": s2["inner_iters"],
+                                    "outer_steps": s2["outer_steps"], "objective_sum": float(np.sum(f2))},
+                     "tc_batch_n1000_R32": {"ms": s4["ms_device"], "inner_iters": s4["inner_iters"],
+                                            "outer_steps": s4["outer_steps"], "objective": float(f4)}}
+    ratio = {k: out["ppa"][k]["ms"] / out["pabb"][k]["ms"] for k in out["ppa"]}
+    line = {"metric": "PPA vs PABB device time and objective", "value": ratio["fp32_sweep"],
+            "unit": "PPA time / PABB time", "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": False,
+            "dtype": "f32", "data": "synthetic", "config": {"workload": PPA_WORKLOAD, "results": out,
+                                                             "time_ratio": ratio}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+SYNC_WORKLOAD = ("penalty update every K inner iterations (subproblems capped at K = max_inner): the 10 n=250 and "
+                 "10 n=500 instances of the sweep, FP32 path, one start")
+
+
+def run_sync(args):
+    """The paper's closing suggestion (update the penalty in step with the inner iterations),
+    read as capping each subproblem at K iterations: objective and device time against K."""
+    import numpy as np
+    import torch
+    import paper_2408_04875_gb300 as ub
+    torch.cuda.set_device(0)
+    Qs, mus = _instances(0, (250, 500), SEEDS_PER_SIZE)
+    Qd = [torch.from_numpy(Q).cuda() for Q in Qs]
+    Md = [torch.from_numpy(m).cuda() for m in mus]
+    ub.solve_batched(Qd[:2], None, Md[:2], max_outer=2)   # warm
+    rows = []
+    for K in (5, 20, 100, 1000, 10000):
+        _, f, st = ub.solve_batched(Qd, None, Md, max_inner=K)
+        rows.append({"K": K, "ms": st["ms_device"], "objective_sum": float(np.sum(f)),
+                     "inner_iters": st["inner_iters"], "outer_steps": st["outer_steps"],
+                     "lanes_capped": st["lanes_capped"]})
+    base = rows[-1]
+    line = {"metric": "objective and device time against the subproblem cap K", "value": rows[0]["ms"] / base["ms"],
+            "unit": "time(K=5) / time(K=10000)", "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": False,
+            "dtype": "f32", "data": "synthetic", "config": {"workload": SYNC_WORKLOAD, "rows": rows}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -402,12 +554,17 @@ def run_gpu(args):
     h2d = sum(Q.nbytes + m.nbytes for Q, m in zip(Qs, mus))
     d2h = sum(Q.shape[0] for Q in Qs) + 8 * len(Qs)
 
-    # roofline of the dominant kernel (phase-A GEMV), CUDA events around every launch
+    # roofline of the dominant kernel (phase-A GEMV), CUDA events around every launch.  The
+    # algorithmic bytes are the sparse minimum of every matrix-vector product (the stored
+    # off-diagonal entries as 4-byte values with 2-byte column indices, plus 8 vectors of n
+    # floats per step); the bytes of the storage the kernel reads give frac_storage
     pa_ms = sum(s["phase_a_ms"] for s in stats)
     pa_n = sum(s["phase_a_launches"] for s in stats)
     pa_bytes = sum(s["phase_a_bytes"] for s in stats)
+    alg_bytes = sum(s["alg_bytes"] for s in stats)
     peak, peak_kind = _peaks()
-    achieved = pa_bytes / (pa_ms * 1e-3) / 1e9 if pa_ms > 0 else None
+    achieved = alg_bytes / (pa_ms * 1e-3) / 1e9 if pa_ms > 0 else None
+    achieved_storage = pa_bytes / (pa_ms * 1e-3) / 1e9 if pa_ms > 0 else None
 
     if rank == 0:
         line = {
@@ -425,7 +582,13 @@ def run_gpu(args):
                                      if stats[-1]["gemv_kernel"] == 2 and pa_n else None),
                          "kernel": GEMV_KERNELS.get(stats[-1]["gemv_kernel"], "?"), "launches": pa_n,
                          "avg_launch_us": pa_ms * 1e3 / max(pa_n, 1),
-                         "algorithmic_bytes_per_launch": pa_bytes / max(pa_n, 1), "peak_kind": peak_kind},
+                         "algorithmic_bytes_per_launch": alg_bytes / max(pa_n, 1),
+                         "algorithmic_bytes": "sparse minimum: per lane-step 6 B x stored off-diagonal entries "
+                                              "+ 32 B x n",
+                         "storage_bytes_per_launch": pa_bytes / max(pa_n, 1),
+                         "achieved_storage": achieved_storage,
+                         "frac_storage": (achieved_storage / peak) if achieved_storage else None,
+                         "peak_kind": peak_kind},
             "e2e": None if st_e2e is None else {"value": st_e2e["var_updates"] / e2e_s, "unit": UNIT,
                                                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
@@ -434,6 +597,8 @@ def run_gpu(args):
         if args.sizes != SIZES or args.seeds != SEEDS_PER_SIZE or args.max_outer is not None:
             line["config"]["workload"] = (f"profiling case: n in {list(args.sizes)} x {args.seeds} seeds, "
                                           f"max_outer={args.max_outer}")
+        if not args.no_c4:
+            line["config"]["time_to_oracle_objective"] = c4_time_to_objective(local)
         line["cpu_baseline"] = None if args.no_cpu_baseline else cpu_baseline()
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -454,7 +619,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"])
+    ap.add_argument("--no-c4", action="store_true",
+                    help="skip the batched-restart time-to-objective comparison of the default line")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "ppa", "sync"])
     ap.add_argument("--c5-count", type=int, default=512, help="instances of the ragged batch")
     ap.add_argument("--c5-restarts", type=int, default=0, help="starts per instance (0 = restart tuner)")
     ap.add_argument("--restarts", type=int, default=256)
@@ -467,6 +634,12 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c3":
+        return run_c3(args)
+    if args.workload == "ppa":
+        return run_ppa(args)
+    if args.workload == "sync":
+        return run_sync(args)
     if args.workload == "c4":
         return run_c4(args)
     if args.workload == "c5":

@@ -135,3 +135,54 @@ def test_tc_rejects_data_bf16_cannot_hold():
     with pytest.raises(ub.UBQPError) as e:
         ub.solve(Q, precision=ub.BF16X2_TC)
     assert e.value.status == -7
+
+
+def test_tc_ppa_restart_batch_vs_oracle():
+    """Alg. 1 (PPA) as the subproblem solver on the batched tensor-core lanes (BF16 x2
+    terms): two instances, 4 starts each, against the oracle's Alg. 1 over the same starts.
+    Bars: exact objectives, and within 0.1 % of the oracle's best (or better); the FP32 path's
+    PPA on the same starts is held to the same bar."""
+    import oracle as O
+    import paper_2408_04875_gb300 as ub
+    from paper_2408_04875_gb300 import instances as I
+    specs = [(150, 61), (130, 62)]
+    R = 4
+    Qs = [I.random_ubqp(n, 0.1, s)[0] for n, s in specs]
+    mus = [np.diag(np.diag(I.perturbation(Q, s))) for Q, (n, s) in zip(Qs, specs)]
+    starts = [I.random_starts(n, R - 1, s) for n, s in specs]
+    xtc, ftc, st = ub.solve_batched(Qs, None, mus, starts, restarts=R, precision=ub.BF16X2_TC, method=ub.PPA)
+    x32, f32, _ = ub.solve_batched(Qs, None, mus, starts, restarts=R, method=ub.PPA)
+    po = O.opts(method=1)
+    for Q, mu, S0, xa, fa, xb, fb in zip(Qs, mus, starts, xtc, ftc, x32, f32):
+        fo = [O.solve(Q, None, mu, o=po)[1]] + [O.solve(Q, None, mu, x_start=S0[r], o=po)[1] for r in range(R - 1)]
+        print(f"PPA n={Q.shape[0]}: tc {fa} fp32 {fb} oracle best {min(fo)}")
+        assert fa == O.objective(Q, None, xa) and fb == O.objective(Q, None, xb)
+        assert fa - min(fo) <= 1e-3 * abs(min(fo)) and fb - min(fo) <= 1e-3 * abs(min(fo))
+    assert st["inner_steps"] > 0
+
+
+def test_tc_launch_form_tuner_measures_and_caches(tmp_path, monkeypatch):
+    """tc_cluster = 0: the contraction is timed with every feasible split-K cluster size and
+    the persistent kernel on the call's own operands, and the fastest is used; the choice is
+    cached per shape (a second call with the same shape reuses it without probing) and written
+    to the JSON file named by UBQP_TUNE_CACHE."""
+    import json
+    import paper_2408_04875_gb300 as ub
+    from paper_2408_04875_gb300 import instances as I
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("UBQP_TUNE_CACHE", str(path))
+    Q, _ = I.random_ubqp(1152, 0.1, 71)
+    kw = dict(restarts=48, precision=ub.BF16X2_TC, max_outer=1)
+    _, f1, s1 = ub.solve(Q, **kw)
+    probe = s1["cluster_probe_us"]
+    assert s1["cluster_tuned"] == 1
+    timed = {c: t for c, t in enumerate(probe) if t > 0}
+    assert 1 in timed                      # split-K with S = 1 is always a candidate
+    best = min(timed, key=timed.get)
+    chosen = 0 if s1["tc_kernel"] == 2 else s1["cluster_size"]
+    assert chosen == best, (probe, s1["tc_kernel"], s1["cluster_size"])
+    entries = json.loads(path.read_text())
+    assert list(entries.values()).count(best) >= 1 and any("tiles" in k for k in entries)
+    _, f2, s2 = ub.solve(Q, **kw)
+    assert s2["cluster_tuned"] == 2 and (0 if s2["tc_kernel"] == 2 else s2["cluster_size"]) == best
+    assert f1 == f2
