@@ -98,6 +98,8 @@ typedef struct {
                              /* S = 1..8 CTAs [S], best of three launches (0: not probed)  */
     int32_t cluster_tuned;   /* 0: rule or caller's tc_cluster, 1: measured in this call,  */
                              /* 2: taken from the cache (see tc_cluster)                  */
+    int32_t storage;         /* Q'_off as read by phase A: 0 dense FP32 rows, 1 symmetric  */
+                             /* tiles, 2 sliced rows (sparse), 3 BF16 tensor-core tiles    */
 } ubqp_stats;
 
 /* Options; ubqp_opts_default() fills the paper's settings and this library's readings
@@ -155,6 +157,15 @@ typedef struct {
                              /* CTA (for its next ring slot / at a grid barrier), in     */
                              /* microseconds; a wait that runs out ends the call with    */
                              /* UBQP_ETIMEOUT and leaves the device usable; 0 = 5 s      */
+    int tc_fuse;             /* tensor-core lanes: 1 = the contraction's epilogue warps run */
+                             /* each lane's update as soon as its last M tile is done (one */
+                             /* launch per step; lanes of at most 32 M tiles), 0 = a      */
+                             /* separate update launch after every contraction: 1        */
+    int sparse_storage;      /* FP32 lanes: Q'_off in sliced row storage (32-row slices of */
+                             /* the stored entries: 4-byte value, 2-byte column), read by  */
+                             /* every scheduler; 0 = when its bytes are fewer than the     */
+                             /* symmetric tiles' (stored off-diagonal entries < n^2 / 3),  */
+                             /* 1 = always, 2 = never: 0                                  */
     double target_objective; /* objective to time against (used when finite)           */
     void* stream;            /* cudaStream_t, NULL = default stream                    */
     const double* const* mu; /* optional perturbations, one n x n matrix per instance   */
@@ -262,7 +273,7 @@ int ubqp_penalized_vjp(const void* x, const void* g, const void* grad_h, int64_t
  *   All pointers are device memory.  The call ends with cudaStreamSynchronize(stream), so
  *   it cannot be called on a stream that is being captured.
  */
-#define UBQP_NOALLOC_SCRATCH_BYTES 2294016
+#define UBQP_NOALLOC_SCRATCH_BYTES 2310400
 int ubqp_penalized_eval_noalloc(const void* Q, const void* b, const void* p, const void* x, int64_t n,
                                 int64_t batch, int dtype, void* h_out, void* g_out, void* stream);
 

@@ -44,7 +44,7 @@ class Stats(C.Structure):
                 ("cluster_size", C.c_int32), ("gemv_kernel", C.c_int32), ("restarts", C.c_int32),
                 ("restart_probe_us", C.c_float * 5), ("tc_kernel", C.c_int32), ("sym_storage", C.c_int32),
                 ("inner_hist", C.c_int64 * HIST_BINS), ("alg_bytes", C.c_int64), ("alg_flops", C.c_int64),
-                ("cluster_probe_us", C.c_float * 9), ("cluster_tuned", C.c_int32)]
+                ("cluster_probe_us", C.c_float * 9), ("cluster_tuned", C.c_int32), ("storage", C.c_int32)]
 
     def as_dict(self):
         arrays = ("inner_hist", "restart_probe_us", "cluster_probe_us")
@@ -63,7 +63,8 @@ class Opts(C.Structure):
                 ("precision", C.c_int), ("lobpcg_max_iter", C.c_int), ("lobpcg_tol", C.c_double),
                 ("jacobi_max_iter", C.c_int), ("max_ticks_per_sync", C.c_int), ("profile_kernels", C.c_int),
                 ("stop_at_target", C.c_int), ("tc_cluster", C.c_int), ("gemv_kernel", C.c_int), ("lane_budget", C.c_int), ("rows_per_item", C.c_int), ("sym_storage", C.c_int),
-                ("wait_limit_us", C.c_int), ("target_objective", C.c_double),
+                ("wait_limit_us", C.c_int), ("tc_fuse", C.c_int), ("sparse_storage", C.c_int),
+                ("target_objective", C.c_double),
                 ("stream", C.c_void_p),
                 ("mu", C.c_void_p), ("x_starts", C.c_void_p), ("stats", C.POINTER(Stats))]
 

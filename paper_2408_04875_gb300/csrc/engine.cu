@@ -163,6 +163,8 @@ static int check_opts(const ubqp_opts& o)
     if (o.gemv_kernel < 0 || o.gemv_kernel > 3) { set_error("gemv_kernel must be 0, 1, 2 or 3"); return UBQP_EINVAL; }
     if (o.lane_budget < 0) { set_error("lane_budget must be >= 0"); return UBQP_EINVAL; }
     if (o.wait_limit_us < 0) { set_error("wait_limit_us must be >= 0"); return UBQP_EINVAL; }
+    if (o.tc_fuse != 0 && o.tc_fuse != 1) { set_error("tc_fuse must be 0 or 1"); return UBQP_EINVAL; }
+    if (o.sparse_storage < 0 || o.sparse_storage > 2) { set_error("sparse_storage must be 0, 1 or 2"); return UBQP_EINVAL; }
     if (o.rows_per_item != 0 && (o.rows_per_item < 8 || o.rows_per_item > 256 || o.rows_per_item % 8 != 0)) {
         set_error("rows_per_item must be 0 or a multiple of 8 in [8, 256]");
         return UBQP_EINVAL;
@@ -198,6 +200,7 @@ struct InstDev {
     int nb = 0;           // row blocks of kSymT rows (symmetric storage)
     size_t o_Qsym = 0;    // symmetric storage tiles
     size_t o_Uhi, o_Ulo;
+    size_t o_spv = 0, o_spc = 0, o_spo = 0;   // sliced storage (in the second allocation)
     int bn, n_tiles, rows_b;   // tensor-core tiling of this instance's lanes
     int lane0, nl;
 };
@@ -290,9 +293,52 @@ class Solver {
         UBQP_CK(cudaGetDevice(&dev));
         UBQP_CK(cudaDeviceGetAttribute(&num_sms_, cudaDevAttrMultiProcessorCount, dev));
 
+        // ---- sliced row storage of Q'_off (sparse data): the stored off-diagonal entries of
+        // every instance are counted here, before the layout; the storage is used when they take
+        // fewer bytes (4-byte value + 2-byte column) than the symmetric tiles would (2 bytes per
+        // matrix entry), or when asked for
+        sparse_ = false;
+        if (!tc && o_.sparse_storage != 2) {
+            std::vector<unsigned long long> cnt(insts.size(), 0);
+            unsigned long long* dcnt = nullptr;
+            AsyncTemp guard;
+            bool any_dev = false;
+            for (size_t t = 0; t < insts.size(); ++t) {
+                const InstIn& in = insts[t];
+                if (is_device_ptr(in.Q)) {
+                    any_dev = true;
+                    continue;
+                }
+                unsigned long long c = 0;
+                for (int64_t i = 0; i < in.n; ++i)
+                    for (int64_t j = 0; j < in.n; ++j) c += (i != j && in.Q[i * in.n + j] != 0.0) ? 1ull : 0ull;
+                cnt[t] = c;
+            }
+            if (any_dev) {
+                UBQP_CK(cudaMallocAsync((void**)&dcnt, insts.size() * sizeof(unsigned long long), stream_));
+                guard.hold(dcnt, stream_);
+                UBQP_CK(cudaMemsetAsync(dcnt, 0, insts.size() * sizeof(unsigned long long), stream_));
+                for (size_t t = 0; t < insts.size(); ++t)
+                    if (is_device_ptr(insts[t].Q)) UBQP_CK(launch_count_offdiag(insts[t].Q, (int)insts[t].n, dcnt + t, stream_));
+                std::vector<unsigned long long> dv(insts.size(), 0);
+                UBQP_CK(cudaMemcpyAsync(dv.data(), dcnt, insts.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                        stream_));
+                UBQP_CK(cudaStreamSynchronize(stream_));
+                for (size_t t = 0; t < insts.size(); ++t)
+                    if (is_device_ptr(insts[t].Q)) cnt[t] = dv[t];
+                guard.release();
+                UBQP_CK(cudaFreeAsync(dcnt, stream_));
+            }
+            double by_sparse = 0.0, by_sym = 0.0;
+            for (size_t t = 0; t < insts.size(); ++t) {
+                by_sparse += 6.0 * (double)cnt[t];
+                by_sym += 2.0 * (double)insts[t].n * (double)insts[t].n;
+            }
+            sparse_ = o_.sparse_storage == 1 || by_sparse < by_sym;
+        }
         // ---- symmetric storage: only with the lane loop (decided here because it fixes the
         // row padding and the row blocks); tiles are indexed in 15 bits per lane
-        {
+        if (!sparse_) {
             const bool loop_likely =
                 !tc && lanes.size() < 0xFFFEu &&
                 (o_.gemv_kernel == 2 || (o_.gemv_kernel == 0 && o_.profile_kernels < 2 && lanes.size() >= 4));
@@ -360,11 +406,27 @@ class Solver {
         while (rb < 32 && total_rows / rb > target_items) rb *= 2;
         if (o_.rows_per_item > 0) rb = o_.rows_per_item;
         if (sym_) rb = kSymT;   // the second stage works on whole tile rows
+        // sliced storage: items of whole 32-row slices (32, 64, 128 or 256 rows), 128 unless
+        // the caller asked for one of these
+        if (sparse_) rb = (o_.rows_per_item == 32 || o_.rows_per_item == 64 || o_.rows_per_item == 256) ? o_.rows_per_item : 128;
         // one FP32 lane: the single-lane persistent kernel (a cooperative launch of one CTA per
         // row block), unless another scheduler or the per-tick timeline is asked for
         solo_ = !tc && !sym_ && lanes.size() == 1 && (size_t)max_ld * sizeof(float) <= 200 * 1024 &&
                 (o_.gemv_kernel == 3 || (o_.gemv_kernel == 0 && o_.profile_kernels < 2));
-        if (solo_) solo_shape((int)insts[lanes[0].inst].n, o_.rows_per_item, num_sms_, &solo_grid_, &rb, &solo_nblk_);
+        if (solo_ && sparse_) {
+            // one CTA per 32-row slice (one CTA for up to 256 rows), unless the caller chose
+            const int n0 = (int)insts[lanes[0].inst].n;
+            if (o_.rows_per_item != 64 && o_.rows_per_item != 128 && o_.rows_per_item != 256 && o_.rows_per_item != 32)
+            {
+                rb = 32;   // one slice per CTA; up to 256 rows: one CTA of 32, 64, 128 or 256 rows
+                if (n0 <= 256)
+                    while (rb < n0) rb *= 2;
+            }
+            solo_nblk_ = (n0 + rb - 1) / rb;
+            solo_grid_ = std::min(solo_nblk_, num_sms_);
+        } else if (solo_) {
+            solo_shape((int)insts[lanes[0].inst].n, o_.rows_per_item, num_sms_, &solo_grid_, &rb, &solo_nblk_);
+        }
         rows_per_item_ = rb;
 
         lanes_.assign(lanes.size(), LaneDev());
@@ -595,6 +657,10 @@ class Solver {
                 UBQP_CK(launch_pack_sym(ar_.at<float>(I.o_Qoff), (int)I.n, I.ld, ar_.at<float>(I.o_Qsym), stream_));
                 launches_ += 1;
             }
+        if (sparse_) {
+            int rc2 = build_sliced();
+            if (rc2) return rc2;
+        }
         std::vector<float> scal(insts.size() * 4);
         UBQP_CK(cudaMemcpyAsync(scal.data(), ar_.at<float>(o_scal_), scal.size() * 4, cudaMemcpyDeviceToHost, stream_));
         std::vector<int> inexact(insts.size());
@@ -637,6 +703,12 @@ class Solver {
             InstDev& I = inst_[in.inst];
             LaneDev& L = lanes_[l];
             L.Qoff = tc ? nullptr : ar_.at<float>(I.o_Qoff);
+            if (sparse_ && I.nl > 0) {
+                L.spv = sp_ar_.at<float>(I.o_spv);
+                L.spc = sp_ar_.at<uint16_t>(I.o_spc);
+                L.spo = sp_ar_.at<int64_t>(I.o_spo);
+                L.spwps = 256 / rows_per_item_;   // 256 threads per GEMV CTA
+            }
             L.Qeval = tc ? nullptr : ar_.at<float2>(I.o_Qeval);
             L.d = ar_.at<float>(I.o_d);
             L.bprime = ar_.at<float>(I.o_bp);
@@ -920,6 +992,9 @@ class Solver {
             tca.err = ar_.at<int32_t>(o_tcerr_);
             tca.flops = prof ? ar_.at<unsigned long long>(o_flops_) : nullptr;
             tca.P = ta.P;
+            // the update runs in the contraction's epilogue when every lane has at most 32 M
+            // tiles (the warp-level reduction then merges partials in the CTA-level order)
+            tca.fuse = (max_ld_ / 128 <= 32 && o_.tc_fuse != 0) ? 1 : 0;
             if (tcp_) {
                 tca.tmem_cols = tcp_tmem_cols(o_.precision == UBQP_BF16X2_TC);
                 tcp_grid_ = tcp_grid(tca, tc_tiles_);
@@ -941,8 +1016,9 @@ class Solver {
         }
 
         // GEMV lanes: one fused kernel per tick (the last CTA of each lane updates it);
-        // tensor-core lanes: contraction kernel, then the stand-alone update kernel
-        const bool fused = has_a && !tc_;
+        // tensor-core lanes: the contraction kernel, whose epilogue warps update the lanes when
+        // tca.fuse is set, else followed by the stand-alone update kernel
+        const bool fused = has_a && (!tc_ || tca.fuse);
         auto enqueue = [&](int nt) -> cudaError_t {
             for (int t = 0; t < nt; ++t) {
                 cudaError_t e = cudaSuccess;
@@ -959,7 +1035,9 @@ class Solver {
                     tt.active_count = last ? d_active : nullptr;
                     e = launch_phase_a_gemv_f32(tt, stream_);
                 } else if (has_a) {
-                    e = tcp_ ? tcp_launch(tca, tc_tiles_, tcp_grid_, stream_) : tc_launch(tca, tc_tiles_, tc_S_, stream_);
+                    TcArgs tt = tca;
+                    tt.active_count = last ? d_active : nullptr;
+                    e = tcp_ ? tcp_launch(tt, tc_tiles_, tcp_grid_, stream_) : tc_launch(tt, tc_tiles_, tc_S_, stream_);
                 }
                 if (e != cudaSuccess) return e;
                 if (prof && has_a) e = cudaEventRecord(evA_[2 * t + 1], stream_);
@@ -1067,6 +1145,56 @@ class Solver {
             ms_to_target_ = m;
             stop = o_.stop_at_target != 0;
         }
+        return UBQP_OK;
+    }
+
+    // the sliced storage of every instance with lanes: widths per 32-row slice from the dense
+    // FP32 rows, offsets on the host, one allocation, then the packing
+    int build_sliced()
+    {
+        size_t nsl_total = 0;
+        std::vector<size_t> sl0(inst_.size());
+        for (size_t t = 0; t < inst_.size(); ++t) {
+            sl0[t] = nsl_total;
+            nsl_total += (size_t)(inst_[t].n + 31) / 32;
+        }
+        int32_t* dw = nullptr;
+        UBQP_CK(cudaMallocAsync((void**)&dw, std::max<size_t>(nsl_total, 1) * sizeof(int32_t), stream_));
+        AsyncTemp guard;
+        guard.hold(dw, stream_);
+        for (size_t t = 0; t < inst_.size(); ++t)
+            if (inst_[t].nl > 0)
+                UBQP_CK(launch_sell_width(ar_.at<float>(inst_[t].o_Qoff), (int)inst_[t].n, inst_[t].ld, dw + sl0[t], stream_));
+        std::vector<int32_t> w(nsl_total, 0);
+        UBQP_CK(cudaMemcpyAsync(w.data(), dw, nsl_total * sizeof(int32_t), cudaMemcpyDeviceToHost, stream_));
+        UBQP_CK(cudaStreamSynchronize(stream_));
+        guard.release();
+        UBQP_CK(cudaFreeAsync(dw, stream_));
+        std::vector<std::vector<int64_t>> offs(inst_.size());
+        for (size_t t = 0; t < inst_.size(); ++t) {
+            InstDev& I = inst_[t];
+            if (I.nl == 0) continue;
+            const size_t ns = (size_t)(I.n + 31) / 32;
+            offs[t].assign(ns + 1, 0);
+            for (size_t q = 0; q < ns; ++q) offs[t][q + 1] = offs[t][q] + 32 * (int64_t)w[sl0[t] + q];
+            const size_t entries = (size_t)offs[t][ns];
+            I.o_spv = sp_ar_.reserve(std::max<size_t>(entries, 1) * 4);
+            I.o_spc = sp_ar_.reserve(std::max<size_t>(entries, 1) * 2);
+            I.o_spo = sp_ar_.reserve((ns + 1) * 8);
+            sliced_entries_ += (int64_t)entries;
+        }
+        int rc = sp_ar_.commit();
+        if (rc) return rc;
+        for (size_t t = 0; t < inst_.size(); ++t) {
+            InstDev& I = inst_[t];
+            if (I.nl == 0) continue;
+            UBQP_CK(cudaMemcpyAsync(sp_ar_.at<int64_t>(I.o_spo), offs[t].data(), offs[t].size() * 8, cudaMemcpyHostToDevice,
+                                    stream_));
+            UBQP_CK(launch_sell_pack(ar_.at<float>(I.o_Qoff), (int)I.n, I.ld, sp_ar_.at<int64_t>(I.o_spo),
+                                     sp_ar_.at<float>(I.o_spv), sp_ar_.at<uint16_t>(I.o_spc), stream_));
+            launches_ += 2;
+        }
+        UBQP_CK(cudaStreamSynchronize(stream_));   // offsets staged from host vectors
         return UBQP_OK;
     }
 
@@ -1325,6 +1453,7 @@ class Solver {
         for (int c = 0; c < 9; ++c) s->cluster_probe_us[c] = cluster_probe_us_[c];
         s->tc_kernel = tc_ ? (tcp_ ? 2 : 1) : 0;
         s->sym_storage = sym_ ? 1 : 0;
+        s->storage = tc_ ? 3 : (sparse_ ? 2 : (sym_ ? 1 : 0));
         s->gemv_kernel = tc_ ? 0 : (solo_ ? 3 : (loop_ ? 2 : 1));
         UBQP_CK(cudaMemcpyAsync(s->inner_hist, ar_.at<int64_t>(o_hist_), sizeof(s->inner_hist), cudaMemcpyDeviceToHost,
                                 stream_));
@@ -1409,6 +1538,9 @@ class Solver {
     int rows_per_item_ = 32;
     bool loop_ = false;          // FP32 lanes on the persistent lane loop
     bool solo_ = false;          // one FP32 lane on the single-lane persistent kernel
+    bool sparse_ = false;        // FP32 lanes read Q'_off from the sliced row storage
+    Arena sp_ar_;                // the sliced storage (allocated once its size is known)
+    int64_t sliced_entries_ = 0;
     int solo_grid_ = 0, solo_nblk_ = 0;
     size_t o_solo_ = 0;
     int loop_grid_ = 0, loop_budget_ = 0;
@@ -1490,6 +1622,8 @@ void ubqp_opts_default(ubqp_opts* o)
     o->rows_per_item = 0;
     o->sym_storage = 1;
     o->wait_limit_us = 0;
+    o->tc_fuse = 1;
+    o->sparse_storage = 0;
     o->target_objective = INFINITY;
     o->stream = nullptr;
     o->mu = nullptr;
@@ -1800,9 +1934,6 @@ int ubqp_penalized_eval(const void* Q, const void* b, const void* p, const void*
         set_error("ubqp_penalized_eval: batch x row blocks exceeds 2^31");
         return UBQP_EINVAL;
     }
-    std::vector<LaneDev> lanes((size_t)batch);
-    std::vector<int2> items;
-    items.reserve((size_t)(batch * nblk));
     const size_t bytes_lanes = round_up((size_t)batch * sizeof(LaneDev), 256);
     const size_t bytes_items = round_up((size_t)(batch * nblk) * sizeof(int2), 256);
     const size_t bytes_queue = 256;
@@ -1815,30 +1946,13 @@ int ubqp_penalized_eval(const void* Q, const void* b, const void* p, const void*
     int2* d_items = reinterpret_cast<int2*>(scratch + bytes_lanes);
     int32_t* d_queue = reinterpret_cast<int32_t*>(scratch + bytes_lanes + bytes_items);
     Partial* d_part = reinterpret_cast<Partial*>(scratch + bytes_lanes + bytes_items + bytes_queue);
-    for (int64_t r = 0; r < batch; ++r) {
-        LaneDev& L = lanes[(size_t)r];
-        memset(&L, 0, sizeof(L));
-        L.n = (int)n;
-        L.ld = (int)n;
-        L.mode = MODE_GRAD;
-        L.nblk = (int)nblk;
-        L.part = d_part + (size_t)r * nblk;
-        L.gQ = Q;
-        L.gb = b;
-        L.gp = p;
-        L.gx = static_cast<const char*>(x) + (size_t)r * n * es;
-        L.gg = g_out ? static_cast<char*>(g_out) + (size_t)r * n * es : nullptr;
-        L.gld = (int)n;
-        for (int64_t blk = 0; blk < nblk; ++blk) items.push_back(make_int2((int)r, (int)blk));
-    }
-    UBQP_CK(cudaMemcpyAsync(d_lanes, lanes.data(), lanes.size() * sizeof(LaneDev), cudaMemcpyHostToDevice, s));
-    UBQP_CK(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-    UBQP_CK(cudaMemsetAsync(d_queue, 0, 2 * sizeof(int32_t), s));
+    UBQP_CK(launch_grad_setup(d_lanes, d_items, d_queue, d_part, Q, b, p, x, g_out, (int)n, (int)batch, (int)nblk,
+                              (int)es, s));
     TickArgs ta;
     memset(&ta, 0, sizeof(ta));
     ta.lanes = d_lanes;
     ta.items = d_items;
-    ta.nitems = (int)items.size();
+    ta.nitems = (int)(batch * nblk);
     ta.rows_per_item = rb;
     ta.nlanes = (int)batch;
     ta.max_ld = (int)n;

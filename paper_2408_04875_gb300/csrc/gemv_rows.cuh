@@ -224,11 +224,62 @@ __device__ __forceinline__ void item_load_u(const LaneDev& L, T* su)
     }
 }
 
-// the solver's matrices: the FP32 hi/lo evaluation rows (PH_EVAL) or the padded Q'_off rows
+// Q'_off rows from the sliced storage: an item of 32 * m rows (m = 1, 2, 4 or 8 slices) with
+// L.spwps = 8 / m warps per slice; the warps of a slice take consecutive shares of its stored
+// entries (lane r: row r of the slice), groups of four products summed with FMAs and added to
+// a TwoSum-compensated sum, and the shares are merged per row in share order.
+__device__ __forceinline__ void item_rows_sell(const LaneDev& L, int row0, int rows, const float* su, double* sv,
+                                               int lane, int warp)
+{
+    __shared__ float2 s_share[kThreads];
+    const int wps = L.spwps;
+    const int sl = warp / wps, part = warp - sl * wps;
+    float2 acc = make_float2(0.f, 0.f);
+    if (sl * 32 < rows) {
+        const int64_t b = L.spo[(row0 >> 5) + sl];
+        const int width = (int)((L.spo[(row0 >> 5) + sl + 1] - b) >> 5);
+        const int k0 = width * part / wps, k1 = width * (part + 1) / wps;
+        const float* V = L.spv + b + lane;
+        const uint16_t* C = L.spc + b + lane;
+        int k = k0;
+        for (; k + 8 <= k1; k += 8) {
+            float q[8];
+            int c[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                q[j] = __ldg(V + 32 * (k + j));
+                c[j] = __ldg(C + 32 * (k + j));
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float t = __fmul_rn(q[4 * h], su[c[4 * h]]);
+                t = fmaf(q[4 * h + 1], su[c[4 * h + 1]], t);
+                t = fmaf(q[4 * h + 2], su[c[4 * h + 2]], t);
+                t = fmaf(q[4 * h + 3], su[c[4 * h + 3]], t);
+                csum_add(acc, t);
+            }
+        }
+        for (; k < k1; ++k) csum_add(acc, __fmul_rn(__ldg(V + 32 * k), su[__ldg(C + 32 * k)]));
+    }
+    s_share[(sl * 32 + lane) * wps + part] = acc;
+    __syncthreads();
+    if ((int)threadIdx.x < rows) {
+        float2 a = s_share[threadIdx.x * wps];
+        for (int q = 1; q < wps; ++q) a = csum_merge(a, s_share[threadIdx.x * wps + q]);
+        sv[threadIdx.x] = (double)(a.x + a.y);
+    }
+}
+
+// the solver's matrices: the FP32 hi/lo evaluation rows (PH_EVAL), the sliced storage or the
+// padded Q'_off rows
 __device__ __forceinline__ void item_rows_solver(const LaneDev& L, int ph, int row0, int rows, const float* su,
                                                  double* sv, int lane, int warp)
 {
     const int ld = L.ld;
+    if (ph != PH_EVAL && L.spv) {
+        item_rows_sell(L, row0, rows, su, sv, lane, warp);
+        return;
+    }
     if (ph == PH_EVAL) {
         for (int r = warp; r < rows; r += kWarps) {
             double v = row_dot_eval(L.Qeval + (size_t)(row0 + r) * ld, su, ld, lane);
@@ -327,6 +378,9 @@ __device__ __forceinline__ void item_finish(const LaneDev& L, int ph, int k, int
                                     ? (unsigned long long)rows * (unsigned long long)sym_parts * 4ull + 16ull * rows
                                     : (unsigned long long)rows * L.n * (ph == PH_EVAL ? 8ull : 4ull) +
                                           (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
+        if (L.spv && ph != PH_EVAL)   // the item's stored entries (4-byte value, 2-byte column)
+            by = 6ull * (unsigned long long)(L.spo[(row0 + rows + 31) >> 5] - L.spo[row0 >> 5]) +
+                 (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
         atomicAdd(P.bytes, by);
     }
 }

@@ -343,6 +343,92 @@ __global__ void pack_sym_kernel(const float* __restrict__ Qoff, int n, int ld, f
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Sliced row storage of Q'_off (32-row slices): slice s holds, for k < width_s, the k-th
+// stored entry of each of its 32 rows at entry spo[s] + 32 k + r (value, column); rows with
+// fewer entries are padded with (0, column 0).  Built from the dense FP32 rows the
+// reformulation wrote, so the stored entries are exactly the nonzero ones of Q'_off.
+
+// stored entries per row, maximum per slice (one warp per row, a CTA per slice)
+__global__ void sell_width_kernel(const float* __restrict__ Qoff, int n, int ld, int32_t* width)
+{
+    const int slice = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ int wmax[8];
+    int mx = 0;
+    for (int r = warp; r < 32; r += 8) {
+        const int row = slice * 32 + r;
+        if (row >= n) continue;
+        int cnt = 0;
+        for (int c0 = 0; c0 < ld; c0 += 32) cnt += __popc(__ballot_sync(0xffffffffu, Qoff[(size_t)row * ld + c0 + lane] != 0.f));
+        mx = max(mx, cnt);
+    }
+    if (lane == 0) wmax[warp] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int m = 0;
+        for (int w = 0; w < 8; ++w) m = max(m, wmax[w]);
+        width[slice] = m;
+    }
+}
+
+// entries of each row in column order, one warp per row
+__global__ void sell_pack_kernel(const float* __restrict__ Qoff, int n, int ld, const int64_t* __restrict__ spo,
+                                 float* __restrict__ vals, uint16_t* __restrict__ cols)
+{
+    const int slice = blockIdx.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = spo[slice];
+    const int width = (int)((spo[slice + 1] - base) / 32);
+    for (int r = warp; r < 32; r += 8) {
+        const int row = slice * 32 + r;
+        int pos = 0;
+        if (row < n) {
+            for (int c0 = 0; c0 < ld; c0 += 32) {
+                const float v = Qoff[(size_t)row * ld + c0 + lane];
+                const unsigned m = __ballot_sync(0xffffffffu, v != 0.f);
+                if (v != 0.f) {
+                    const int p = pos + __popc(m & ((1u << lane) - 1u));
+                    vals[base + (int64_t)p * 32 + r] = v;
+                    cols[base + (int64_t)p * 32 + r] = (uint16_t)(c0 + lane);
+                }
+                pos += __popc(m);
+            }
+        }
+        for (int p = pos + lane; p < width; p += 32) {
+            vals[base + (int64_t)p * 32 + r] = 0.f;
+            cols[base + (int64_t)p * 32 + r] = 0;
+        }
+    }
+}
+
+cudaError_t launch_sell_width(const float* Qoff, int n, int ld, int32_t* width, cudaStream_t s)
+{
+    sell_width_kernel<<<(n + 31) / 32, 256, 0, s>>>(Qoff, n, ld, width);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sell_pack(const float* Qoff, int n, int ld, const int64_t* spo, float* vals, uint16_t* cols,
+                             cudaStream_t s)
+{
+    sell_pack_kernel<<<(n + 31) / 32, 256, 0, s>>>(Qoff, n, ld, spo, vals, cols);
+    return cudaGetLastError();
+}
+
+// stored (nonzero) off-diagonal entries of a device n x n FP64 matrix, added to *out
+__global__ void count_offdiag_kernel(const double* __restrict__ Q, int n, unsigned long long* out)
+{
+    const int i = blockIdx.x;
+    unsigned c = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) c += (j != i && Q[(size_t)i * n + j] != 0.0) ? 1u : 0u;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+
+cudaError_t launch_count_offdiag(const double* Q, int n, unsigned long long* out, cudaStream_t s)
+{
+    count_offdiag_kernel<<<n, 256, 0, s>>>(Q, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_sym(const float* Qoff, int n, int ld, float* Qsym, cudaStream_t s)
 {
     const int nb = ld / kSymT;

@@ -387,7 +387,8 @@ static __device__ void reduce_partials(const Partial* part, int nblk, int ph, Pa
 // The element-wise part of a lane's update for the decision D, over elements [ia, ib) (and,
 // for the plain projected step, 16-byte groups [qa, qb) of the padded length).  Every element
 // is computed on its own, so a lane's result does not depend on how the range is split.
-static __device__ void lane_apply(const LaneDev& L, const Params& P, const Decision& D, int ia, int ib, int qa, int qb)
+static __device__ void lane_apply(const LaneDev& L, const Params& P, const Decision& D, int ia, int ib, int qa, int qb,
+                                  int tid, int nt)
 {
     const int n = L.n, ld = L.ld;
     (void)P;
@@ -402,8 +403,7 @@ static __device__ void lane_apply(const LaneDev& L, const Params& P, const Decis
         const float4* G4 = reinterpret_cast<const float4*>(vec + (size_t)V_G * ld);
         float4* U4 = reinterpret_cast<float4*>(vec + (size_t)V_U * ld);
         // two groups per thread per pass, both loaded before either is stored
-        const int nt = blockDim.x;
-        for (int q0 = qa + (int)threadIdx.x; q0 < qb; q0 += 2 * nt) {
+        for (int q0 = qa + tid; q0 < qb; q0 += 2 * nt) {
             float4 xs[2], gs[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -441,7 +441,7 @@ static __device__ void lane_apply(const LaneDev& L, const Params& P, const Decis
             }
         }
     }
-    for (int i = ia + (int)threadIdx.x; i < ib && !(act == A_STEP_PABB && usrc == U_X); i += blockDim.x) {
+    for (int i = ia + tid; i < ib && !(act == A_STEP_PABB && usrc == U_X); i += nt) {
         float x = vec[V_X * ld + i];
         if (act & A_TRACE) L.trace_x[(size_t)D.trace_k * n + i] = x;
         if (act & A_COPY_W_X) {
@@ -546,7 +546,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
     if (threadIdx.x == 0) decide(L, S, R, P, D);
     __syncthreads();
     // ---- element-wise update
-    lane_apply(L, P, D, 0, L.n, 0, L.ld >> 2);
+    lane_apply(L, P, D, 0, L.n, 0, L.ld >> 2, (int)threadIdx.x, (int)blockDim.x);
     const int act = D.act;
     if (threadIdx.x == 0) {
         if ((act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
@@ -555,6 +555,64 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
         *L.st = S;
         if (S.phase != PH_DONE && active_count) atomicAdd(active_count, 1);
     }
+}
+
+// Per-warp shared-memory slots of warp_lane_update.
+struct WarpUpd {
+    LaneState S;
+    Partial R;
+    Decision D;
+};
+
+// The update of one lane by one warp (the tensor-core kernels run it in the epilogue warp
+// that finished the lane's last M tile).  Thread t merges partials t, t + 32, ...; with at
+// most 32 partials this is the order of lane_update with any CTA size (the cross-warp merge
+// there only adds zeros), so both give the same bits.
+static __device__ __noinline__ void warp_lane_update(const LaneDev& L, const Params& P, WarpUpd& W,
+                                                     int32_t* active_count)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) W.S = *L.st;
+    __syncwarp();
+    const int ph = W.S.phase;
+    if (ph == PH_DONE) return;
+    Acc a;
+    a.zero();
+    const int ns = phase_nsum(ph), nm = phase_nmax(ph);
+    for (int b = lane; b < L.nblk; b += 32) {
+        const Partial& p = L.part[b];
+#pragma unroll
+        for (int t = 0; t < 12; ++t)
+            if (t < ns) a.s[t] = csum_merge(a.s[t], p.s[t]);
+#pragma unroll
+        for (int t = 0; t < 6; ++t)
+            if (t < nm) a.m[t] = fmaxf(a.m[t], p.m[t]);
+        a.f += p.f;
+    }
+#pragma unroll
+    for (int t = 0; t < 12; ++t)
+        if (t < ns) a.s[t] = csum_shfl_reduce(a.s[t]);
+#pragma unroll
+    for (int t = 0; t < 6; ++t)
+        if (t < nm) a.m[t] = max_shfl_reduce(a.m[t]);
+    if (ph == PH_EVAL) a.f = dsum_shfl_reduce(a.f);
+    if (lane == 0) {
+        for (int t = 0; t < 12; ++t) W.R.s[t] = t < ns ? a.s[t] : make_float2(0.f, 0.f);
+        for (int t = 0; t < 6; ++t) W.R.m[t] = t < nm ? a.m[t] : 0.f;
+        W.R.f = ph == PH_EVAL ? a.f : 0.0;
+        decide(L, W.S, W.R, P, W.D);
+    }
+    __syncwarp();
+    lane_apply(L, P, W.D, 0, L.n, 0, L.ld >> 2, lane, 32);
+    __syncwarp();
+    if (lane == 0) {
+        if ((W.D.act & A_TRACE) && L.trace_alpha) L.trace_alpha[W.D.trace_k] = W.D.alpha;
+        W.S.updates += 1;
+        if (W.S.phase == PH_DONE && L.nt_active) atomicSub(L.nt_active, 1);
+        *L.st = W.S;
+        if (W.S.phase != PH_DONE && active_count) atomicAdd(active_count, 1);
+    }
+    __syncwarp();
 }
 
 }  // namespace ubqp

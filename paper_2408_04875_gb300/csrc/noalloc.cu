@@ -24,8 +24,8 @@ namespace ubqp {
 
 constexpr int kNoallocMaxLanes = 256;
 constexpr int kNoallocMaxItems = 16384;
-constexpr size_t kLanesBytes = (size_t)kNoallocMaxLanes * 256;   // room for one descriptor per point
-static_assert(sizeof(LaneDev) <= 256, "descriptor outgrew its scratch slot");
+constexpr size_t kLanesBytes = (size_t)kNoallocMaxLanes * 320;   // room for one descriptor per point
+static_assert(sizeof(LaneDev) <= 320, "descriptor outgrew its scratch slot");
 constexpr size_t kItemsBytes = (size_t)kNoallocMaxItems * sizeof(int2);
 constexpr size_t kQueueBytes = 256;
 constexpr size_t kPartBytes = (size_t)kNoallocMaxItems * sizeof(Partial);
@@ -98,36 +98,6 @@ static cudaError_t noalloc_scratch(void** out)
     return cudaSuccess;
 }
 
-// descriptors and work items of `batch` gradient lanes, and the cleared queue counters,
-// written on the device
-__global__ void noalloc_setup_kernel(unsigned char* scratch, const void* Q, const void* b, const void* p,
-                                     const void* x, void* g, int n, int batch, int nblk, int es)
-{
-    LaneDev* lanes = reinterpret_cast<LaneDev*>(scratch + kLanesOff);
-    int2* items = reinterpret_cast<int2*>(scratch + kItemsOff);
-    int32_t* queue = reinterpret_cast<int32_t*>(scratch + kQueueOff);
-    Partial* part = reinterpret_cast<Partial*>(scratch + kPartOff);
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid < 2) queue[tid] = 0;
-    if (tid < batch) {
-        LaneDev L;
-        memset(&L, 0, sizeof(L));
-        L.n = n;
-        L.ld = n;
-        L.mode = MODE_GRAD;
-        L.nblk = nblk;
-        L.part = part + (size_t)tid * nblk;
-        L.gQ = Q;
-        L.gb = b;
-        L.gp = p;
-        L.gx = static_cast<const char*>(x) + (size_t)tid * n * es;
-        L.gg = g ? static_cast<char*>(g) + (size_t)tid * n * es : nullptr;
-        L.gld = n;
-        lanes[tid] = L;
-    }
-    for (int t = tid; t < batch * nblk; t += gridDim.x * blockDim.x) items[t] = make_int2(t / nblk, t % nblk);
-}
-
 static bool on_device(const void* ptr)
 {
     if (!ptr) return false;
@@ -197,9 +167,9 @@ extern "C" int ubqp_penalized_eval_noalloc(const void* Q, const void* b, const v
     unsigned char* base = static_cast<unsigned char*>(scratch);
     cudaStream_t s = (cudaStream_t)stream;
     const int nitems = (int)(batch * nblk);
-    noalloc_setup_kernel<<<(nitems + 255) / 256, 256, 0, s>>>(base, Q, b, p, x, g_out, (int)n, (int)batch,
-                                                               (int)nblk, (int)es);
-    e = cudaGetLastError();
+    e = launch_grad_setup(reinterpret_cast<LaneDev*>(base + kLanesOff), reinterpret_cast<int2*>(base + kItemsOff),
+                          reinterpret_cast<int32_t*>(base + kQueueOff), reinterpret_cast<Partial*>(base + kPartOff), Q, b,
+                          p, x, g_out, (int)n, (int)batch, (int)nblk, (int)es, s);
     TickArgs ta;
     memset(&ta, 0, sizeof(ta));
     ta.lanes = reinterpret_cast<const LaneDev*>(base + kLanesOff);

@@ -76,7 +76,14 @@ __global__ void __launch_bounds__(kThreads, 1) solo_lane_kernel(SoloArgs A)
     __shared__ Decision D;
     __shared__ int s_ok;
     __shared__ unsigned s_gen0;
-    const LaneDev& L = *A.lane;
+    // the descriptor never changes: one copy in shared memory (this file's plain loads go to
+    // L2, so every field read from global memory would be an L2 round trip)
+    __shared__ __align__(16) LaneDev sL;
+    static_assert(sizeof(LaneDev) % 8 == 0, "descriptor copied in 8-byte pieces");
+    if (threadIdx.x < (int)(sizeof(LaneDev) / 8))
+        reinterpret_cast<int2*>(&sL)[threadIdx.x] = __ldg(reinterpret_cast<const int2*>(A.lane) + threadIdx.x);
+    __syncthreads();
+    const LaneDev& L = sL;
     if (threadIdx.x == 0) {
         S = *L.st;
         s_ok = 1;
@@ -111,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 1) solo_lane_kernel(SoloArgs A)
         reduce_partials(L.part, A.nblk, ph, R);
         if (threadIdx.x == 0) decide(L, S, R, P, D);
         __syncthreads();
-        lane_apply(L, P, D, ia, ib, qa, qb);
+        lane_apply(L, P, D, ia, ib, qa, qb, (int)threadIdx.x, (int)blockDim.x);
         if (threadIdx.x == 0) {
             S.updates += 1;
             if (blockIdx.x == 0 && (D.act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;

@@ -22,6 +22,7 @@
 #include <cstring>
 
 #include "../../include/ubqp.h"
+#include "lane_update.cuh"
 #include "ubqp_engine.cuh"
 #include "ubqp_tc.cuh"
 
@@ -273,6 +274,26 @@ __device__ __forceinline__ void tc_lane_epilogue(const TcArgs& A, const TcInst& 
     warp_reduce_write(a, ph, L.part + mt, ph == PH_EVAL);
 }
 
+// Fused update: after a warp has written lane L's partial for one M tile it counts itself in;
+// the warp that completes the lane's count (all its M tiles done, so no CTA of this launch
+// still reads the lane's inputs) runs the lane's update.
+__device__ __forceinline__ void tc_fused_count(const TcArgs& A, const LaneDev& L, WarpUpd& W)
+{
+    __threadfence();
+    __syncwarp();
+    unsigned last = 0;
+    if ((threadIdx.x & 31) == 0) last = atomicAdd(L.counter, 1u) == (unsigned)(L.nblk - 1) ? 1u : 0u;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+        __threadfence();
+        if ((threadIdx.x & 31) == 0) *L.counter = 0u;
+        __syncwarp();
+        warp_lane_update(L, A.P, W, A.active_count);
+        // the inputs written here are read by the next step's TMA loads (async proxy)
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+}
+
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
 {
@@ -283,6 +304,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
     __shared__ uint32_t tmem_base;
     __shared__ int s_inst, s_mt, s_nt, s_skip;
     __shared__ int s_fail;
+    __shared__ WarpUpd s_upd[kTcThreads / 32];
 
     cg::cluster_group cluster = cg::this_cluster();
     const int S = (int)cluster.num_blocks();
@@ -470,7 +492,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
                 }
             } else {
                 const int ph = s_ph[c - c0];
-                if (ph != PH_DONE) tc_lane_epilogue(A, I, mt, r, ph, s_k[c - c0], vv, lane, cur_ok ? &cur : nullptr);
+                if (ph != PH_DONE) {
+                    tc_lane_epilogue(A, I, mt, r, ph, s_k[c - c0], vv, lane, cur_ok ? &cur : nullptr);
+                    if (A.fuse) tc_fused_count(A, A.lanes[I.lane0 + r], s_upd[warp]);
+                }
             }
             cur = nxt;
             cur_ok = nxt_ok;
@@ -550,6 +575,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tcp_kernel(TcArgs A, in
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     __shared__ long long s_issued;
+    __shared__ WarpUpd s_upd[kTcThreads / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t col_stride = A.two_any ? 256u : 128u;   // one accumulator buffer: terms x chains x bn <= this
 
@@ -723,6 +749,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tcp_kernel(TcArgs A, in
                         }
                     } else if (cur_ph != PH_DONE) {
                         tc_lane_epilogue(A, I, T.mt, r, cur_ph, cur_k, vv, lane, cur_ph == PH_INNER ? &cur : nullptr);
+                        if (A.fuse) tc_fused_count(A, A.lanes[I.lane0 + r], s_upd[warp]);
                     }
                     cur = nxt;
                     cur_ph = nxt_ph;

@@ -86,6 +86,41 @@ __global__ void grad_reduce_kernel(const LaneDev* lanes, int nlanes, T* h_out)
     h_out[l] = (T)t;
 }
 
+// descriptors and work items of `batch` gradient lanes and the cleared queue counters, written
+// on the device (no host staging): point r has blocks (r, 0 .. nblk-1)
+__global__ void grad_setup_kernel(LaneDev* lanes, int2* items, int32_t* queue, Partial* part, const void* Q,
+                                  const void* b, const void* p, const void* x, void* g, int n, int batch, int nblk,
+                                  int es)
+{
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid < 2) queue[tid] = 0;
+    if (tid < batch) {
+        LaneDev L;
+        memset(&L, 0, sizeof(L));
+        L.n = n;
+        L.ld = n;
+        L.mode = MODE_GRAD;
+        L.nblk = nblk;
+        L.part = part + (size_t)tid * nblk;
+        L.gQ = Q;
+        L.gb = b;
+        L.gp = p;
+        L.gx = static_cast<const char*>(x) + (size_t)tid * n * es;
+        L.gg = g ? static_cast<char*>(g) + (size_t)tid * n * es : nullptr;
+        L.gld = n;
+        lanes[tid] = L;
+    }
+    for (int t = tid; t < batch * nblk; t += gridDim.x * blockDim.x) items[t] = make_int2(t / nblk, t % nblk);
+}
+
+cudaError_t launch_grad_setup(LaneDev* lanes, int2* items, int32_t* queue, Partial* part, const void* Q, const void* b,
+                              const void* p, const void* x, void* g, int n, int batch, int nblk, int es, cudaStream_t s)
+{
+    const int work = batch * nblk > batch ? batch * nblk : batch;
+    grad_setup_kernel<<<(work + 255) / 256, 256, 0, s>>>(lanes, items, queue, part, Q, b, p, x, g, n, batch, nblk, es);
+    return cudaGetLastError();
+}
+
 // vector-Jacobian product of h (backward of the penalized objective) for `batch` points:
 //   gx[r][i] = go[r] g[r][i],  gp[i] = sum_r go[r] (x_ri - x_ri^2),  gb[i] = sum_r go[r] x_ri
 // one thread per coordinate i; the sums over r run in order r = 0, 1, ... (FP64 accumulation)

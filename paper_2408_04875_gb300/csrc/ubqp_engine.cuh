@@ -71,6 +71,10 @@ cudaError_t launch_pack_sym(const float* Qoff, int n, int ld, float* Qsym, cudaS
 // one launch for every instance of a batch; row0[t] = first global row of instance t
 cudaError_t launch_validate(const ValArgs* v, const int64_t* row0, int ninst, int64_t rows, cudaStream_t s);
 cudaError_t launch_reformulate(const RefArgs* args, const int64_t* row0, int ninst, int64_t rows, cudaStream_t s);
+cudaError_t launch_sell_width(const float* Qoff, int n, int ld, int32_t* width, cudaStream_t s);
+cudaError_t launch_sell_pack(const float* Qoff, int n, int ld, const int64_t* spo, float* vals, uint16_t* cols,
+                             cudaStream_t s);
+cudaError_t launch_count_offdiag(const double* Q, int n, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_lane_init(const LaneInitArgs& a, int nlanes, cudaStream_t s);
 cudaError_t launch_finalize(const FinalArgs& a, int ninst, cudaStream_t s);
 cudaError_t launch_lane_vec_to_f64(const LaneDev* lanes, int lane, int v, int n, double* out, cudaStream_t s);

@@ -127,9 +127,14 @@ struct LaneDev {
     const void* gx;
     void* gg;
     int32_t gld;
-    int32_t pad_;
+    int32_t spwps;         // sliced storage: warps per 32-row slice (8 / slices per item)
     int32_t* nt_active;    // TC lanes: unfinished lanes of this lane's N tile (decremented
                            // by the update that finishes the lane), else null
+    // sliced row storage of Q'_off (GEMV lanes, sparse data), or null: entry spo[s] + 32 k + r
+    // of slice s is the k-th stored entry of row 32 s + r (value spv, column spc)
+    const float* spv;
+    const uint16_t* spc;
+    const int64_t* spo;
 };
 
 // solver constants (kernel parameter)
@@ -450,6 +455,8 @@ cudaError_t launch_lane_loop(const LoopArgs& a, cudaStream_t s);   // seed + loo
 cudaError_t launch_phase_b(const TickArgs& a, int32_t* active_count, cudaStream_t s);
 cudaError_t launch_grad_reduce(const LaneDev* lanes, int nlanes, void* h_out, int dtype,
                                cudaStream_t s);
+cudaError_t launch_grad_setup(LaneDev* lanes, int2* items, int32_t* queue, Partial* part, const void* Q, const void* b,
+                              const void* p, const void* x, void* g, int n, int batch, int nblk, int es, cudaStream_t s);
 cudaError_t launch_penalized_vjp(const void* x, const void* g, const void* go, int64_t n, int64_t batch, int dtype,
                                  void* gx, void* gp, void* gb, cudaStream_t s);
 

@@ -36,6 +36,9 @@ struct TcArgs {
     float* raw;          // probe mode: D written as [lane][row] (ld stride) instead of the epilogue
     int32_t* err;        // set when a bounded wait ran out
     unsigned long long* flops;  // algorithmic flops of the tiles computed (may be null)
+    int32_t fuse;        // 1: the warp that finishes a lane's last M tile runs its update
+                         // (every lane has at most 32 M tiles); 0: a separate update launch
+    int32_t* active_count;  // fused: incremented by every lane still active after its update
     Params P;
 };
 

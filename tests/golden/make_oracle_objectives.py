@@ -19,7 +19,8 @@ An oracle solve takes about 1 s at n = 250, 11 s at n = 500, 3 min at n = 1000 a
 n = 2500 on one core, so the cases run in a process pool and the file is rewritten after
 each finished case (a later run computes only the cases still missing).  Run from the
 repository root:
-    python tests/golden/make_oracle_objectives.py [--workers K] [--only c2|c4]
+    python tests/golden/make_oracle_objectives.py [--workers K] [--only c2|c4|c5] [--out FILE]
+    python tests/golden/make_oracle_objectives.py --merge FILE   # add FILE's cases to the golden file
 """
 import argparse
 import json
@@ -78,36 +79,44 @@ def run_case(c):
     return out
 
 
-def load():
-    if os.path.exists(PATH):
-        with open(PATH) as fh:
+def load(path=PATH):
+    if os.path.exists(path):
+        with open(path) as fh:
             return json.load(fh)
     return {"source": "FP64 oracle (oracle/ubqp_oracle.c), Alg. 3 with Alg. 2, default options",
             "generator": "tests/golden/make_oracle_objectives.py", "cases": {}}
 
 
-def save(d):
-    tmp = PATH + ".tmp"
+def save(d, path=PATH):
+    tmp = path + ".tmp"
     with open(tmp, "w") as fh:
         json.dump(d, fh, indent=1, sort_keys=True)
-    os.replace(tmp, PATH)
+    os.replace(tmp, path)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workers", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     ap.add_argument("--only", default=None)
+    ap.add_argument("--out", default=PATH)
+    ap.add_argument("--merge", default=None)
     args = ap.parse_args()
+    if args.merge:
+        d = load()
+        d["cases"].update(load(args.merge)["cases"])
+        save(d)
+        print("merged", args.merge, "->", PATH, len(d["cases"]), "cases")
+        return
     import oracle as O
     O.build()
-    d = load()
+    d = load(args.out)
     todo = [c for c in case_list() if key(c) not in d["cases"] and (args.only is None or c["family"] == args.only)]
     todo.sort(key=lambda c: -c["n"])   # the long solves start first
     ctx = mp.get_context("spawn")
     with ctx.Pool(args.workers) as pool:
         for res in pool.imap_unordered(run_case, todo):
             d["cases"][key(res)] = res
-            save(d)
+            save(d, args.out)
             print(key(res), res["f"], res["cpu_s"], "s", flush=True)
 
 

@@ -97,7 +97,8 @@ def test_c5_full_batch_properties(ub):
     xs, objs, st = ub.solve_batched(Qd, bd, None, restarts=0, precision=ub.BF16X2_TC, max_outer=1)
     assert st["restarts"] in (1, 8, 32, 64, 128)
     assert st["lanes"] == 512 * st["restarts"]
-    assert st["tc_kernel"] == 2          # thousands of tiles: the persistent contraction
+    assert st["tc_kernel"] in (1, 2)     # the launch form the tuner measured fastest
+    assert st["cluster_tuned"] in (1, 2)
     for i, x in enumerate(xs):
         assert x.shape == (specs[i][0],) and set(np.unique(x)) <= {0, 1}
     for i, (Q, b) in host.items():

@@ -7,7 +7,7 @@ Bars: the returned objective is the exact f(x) of the returned point (integer da
 evaluates it exactly), and the GPU's best objective is not worse than the oracle's by more
 than 0.1 % (the method is a heuristic minimiser: a better objective always passes).
 - plain sweep law (C2): n = 500 and 1000 (3 seeds each) and n = 2500 (seed 0), FP32 path,
-  both storages of Q'_off (symmetric tiles on the lane loop, dense rows);
+  the three storages of Q'_off on the lane loop (sliced rows, symmetric tiles, dense rows);
 - restart batches on the tensor cores (C4 law, BF16 x2 terms, diagonal-only perturbation):
   n = 1000 with 32 starts against the oracle's best over the same 32 starts, and the full
   configuration n = 2500 with 256 starts against the oracle's single start x^0;
@@ -53,18 +53,19 @@ def _within(f, f_orc):
 C2_CASES = [(500, 0), (500, 1), (500, 2), (1000, 0), (1000, 1), (1000, 2), (2500, 0)]
 
 
-@pytest.mark.parametrize("sym", [1, 0])
-def test_c2_bench_sizes_within_tenth_percent_of_oracle(ub, gold, sym):
+@pytest.mark.parametrize("storage", [2, 1, 0])
+def test_c2_bench_sizes_within_tenth_percent_of_oracle(ub, gold, storage):
     Qs, mus = [], []
     for n, s in C2_CASES:
         Q, _ = I.c2_instance(n, s)
         Qs.append(Q)
         mus.append(I.perturbation(Q, s))
-    xs, obj, st = ub.solve_batched(Qs, None, mus, gemv_kernel=2, sym_storage=sym)
-    assert st["sym_storage"] == sym
+    kw = {2: dict(sparse_storage=1), 1: dict(sparse_storage=2, sym_storage=1), 0: dict(sparse_storage=2, sym_storage=0)}
+    xs, obj, st = ub.solve_batched(Qs, None, mus, gemv_kernel=2, **kw[storage])
+    assert st["storage"] == storage
     for (n, s), Q, x, f in zip(C2_CASES, Qs, xs, obj):
         f_orc = _case(gold, "c2", n, s)["f"]
-        print(f"C2 n={n} seed={s} sym={sym}: gpu {f} oracle {f_orc} ({(f - f_orc) / abs(f_orc):+.2e})")
+        print(f"C2 n={n} seed={s} storage={storage}: gpu {f} oracle {f_orc} ({(f - f_orc) / abs(f_orc):+.2e})")
         assert f == O.objective(Q, None, x)
         assert _within(f, f_orc), (n, s, f, f_orc)
 

@@ -186,3 +186,31 @@ def test_tc_launch_form_tuner_measures_and_caches(tmp_path, monkeypatch):
     _, f2, s2 = ub.solve(Q, **kw)
     assert s2["cluster_tuned"] == 2 and (0 if s2["tc_kernel"] == 2 else s2["cluster_size"]) == best
     assert f1 == f2
+
+
+@pytest.mark.parametrize("cluster", [1, 3, -1])
+def test_tc_fused_update_matches_separate_update_bitwise(cluster):
+    """The update run by the epilogue warp that finishes a lane's last M tile (one launch per
+    step) against the separate update kernel after each contraction: same bits (the warp-level
+    reduction merges the lane's partials in the CTA-level order), for split-K clusters of 1 and
+    3 CTAs and for the persistent many-tile kernel (tc_cluster = -1 is not an option; the
+    persistent form is reached through a ragged batch with more tiles than SMs)."""
+    import paper_2408_04875_gb300 as ub
+    from paper_2408_04875_gb300 import instances as I
+    if cluster == -1:
+        specs = I.c5_specs(48, seed=5, n_lo=300, n_hi=900)
+        data = [I.c5_instance(sp) for sp in specs]
+        Qs, bs = [Q for Q, _ in data], [b for _, b in data]
+        kw = dict(restarts=4, precision=ub.BF16X2_TC, max_outer=3, tc_cluster=1)
+    else:
+        Q, _ = I.random_ubqp(700, 0.1, 81)
+        Qs, bs = [Q], None
+        kw = dict(restarts=40, precision=ub.BF16X2_TC, max_outer=3, tc_cluster=cluster)
+    x1, f1, s1 = ub.solve_batched(Qs, bs, None, tc_fuse=1, **kw)
+    x0, f0, s0 = ub.solve_batched(Qs, bs, None, tc_fuse=0, **kw)
+    assert np.array_equal(f1, f0) and all(np.array_equal(a, b) for a, b in zip(x1, x0))
+    for key in ("inner_iters", "outer_steps", "lobpcg_iters", "jacobi_iters"):
+        assert s1[key] == s0[key], key
+    assert s1["kernel_launches"] < s0["kernel_launches"]
+    if cluster == -1:
+        assert s1["tc_kernel"] == 2

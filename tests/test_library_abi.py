@@ -115,6 +115,7 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     (dict(gemv_kernel=4), "gemv_kernel"), (dict(lane_budget=-1), "lane_budget"),
     (dict(rows_per_item=12), "rows_per_item"), (dict(rows_per_item=4), "rows_per_item"),
     (dict(rows_per_item=264), "rows_per_item"), (dict(wait_limit_us=-1), "wait_limit_us"),
+    (dict(tc_fuse=2), "tc_fuse"), (dict(sparse_storage=3), "sparse_storage"),
 ])
 def test_invalid_options_are_rejected_before_any_cuda_call(built, kw, msg):
     """Every option outside its documented range returns UBQP_EINVAL with a message naming
