@@ -347,6 +347,92 @@ def run_sync(args):
     return 0
 
 
+SINGLE_WORKLOAD = ("plain FP32 path, one lane: C1 (n=50, density 0.1, seed 0) and one n=2500 instance of the "
+                   "sweep law (seed 0), whole solves")
+
+
+def run_single(args):
+    """The plain FP32 single-instance path: whole solves of one lane on the single-lane persistent
+    kernel (gemv_kernel = 3) and on the lock-step scheduler (gemv_kernel = 1), device time per
+    step.  Roofline of the single-lane kernel at n = 2500: algorithmic bytes per step (the sparse
+    minimum, 6 B per stored entry + 32 B per row) over the time per step, against HBM (the
+    sliced storage of one lane, 3.8 MB, is L2-resident, so the fraction can exceed 1)."""
+    import torch
+    import paper_2408_04875_gb300 as ub
+    from paper_2408_04875_gb300 import instances as I
+    torch.cuda.set_device(0)
+    peak, peak_kind = _peaks()
+    out = {}
+    for n in (50, 2500):
+        Q, _ = I.c2_instance(n, 0)
+        mu = I.perturbation(Q, 0)
+        Qd, Md = torch.from_numpy(Q).cuda(), torch.from_numpy(mu).cuda()
+        for gk in (3, 1):
+            for _ in range(max(args.warmup, 1)):
+                ub.solve(Qd, None, mu=Md, gemv_kernel=gk, max_outer=2)
+            ms, steps, alg, f = [], 0, 0, None
+            for _ in range(max(args.steps, 1)):
+                _, f, st = ub.solve(Qd, None, mu=Md, gemv_kernel=gk)
+                ms.append(st["ms_device"])
+                steps, alg = st["ticks"], st["alg_bytes"]
+            t = statistics.median(ms)
+            out[f"n{n}_k{gk}"] = {"ms": t, "steps": steps, "us_per_step": 1e3 * t / max(steps, 1), "objective": f,
+                                  "storage": st["storage"], "alg_bytes_per_step": alg / max(steps, 1),
+                                  "achieved_gbs": alg / (t * 1e-3) / 1e9}
+    big = out["n2500_k3"]
+    line = {"metric": "plain FP32 path: device time per step of one lane", "value": big["us_per_step"],
+            "unit": "us/step", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": big["ms"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": {"workload": SINGLE_WORKLOAD, "results": out},
+            "roofline": {"bound": "hbm", "achieved": big["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": big["achieved_gbs"] / peak, "traffic": None, "kernel": "solo_lane_kernel",
+                         "peak_kind": peak_kind, "l2": "the lane's sliced storage is L2-resident"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+TCRAW_WORKLOAD = "raw tensor-core contraction: n=2500 BF16 Q_off (integers), 256 starts as two BF16 terms"
+
+
+def run_tcraw(args):
+    """The batched path's contraction alone (ubqp_tc_matmul_probe: D = A (B_hi + B_lo)^T, no
+    solver epilogue) at the batched-restart shape, for profiling.  Prints the host wall time of
+    each probe call (which includes its allocation and copies)."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    import paper_2408_04875_gb300 as ub
+    L = ub.lib()
+    L.ubqp_tc_matmul_probe.restype = C.c_int
+    n, R = 2500, 256
+    rng = np.random.default_rng(0)
+    A = rng.integers(-100, 101, (n, n)).astype(np.float32)
+    A = np.triu(A) + np.triu(A, 1).T
+    np.fill_diagonal(A, 0)
+    X = rng.random((R, n))
+
+    def bits(a):
+        t = torch.tensor(np.asarray(a, np.float32)).to(torch.bfloat16)
+        return t.view(torch.int16).numpy().view(np.uint16).copy(), t.float().numpy()
+
+    Ab, _ = bits(A)
+    hb, hf = bits(X)
+    lb, _ = bits(X - hf)
+    D = np.zeros((R, n), np.float32)
+    walls = []
+    for _ in range(max(args.steps, 1) + max(args.warmup, 1)):
+        t0 = time.perf_counter()
+        rc = L.ubqp_tc_matmul_probe(Ab.ctypes.data_as(C.c_void_p), hb.ctypes.data_as(C.c_void_p),
+                                    lb.ctypes.data_as(C.c_void_p), C.c_int64(n), C.c_int64(R),
+                                    C.c_int32(args.tc_cluster), D.ctypes.data_as(C.c_void_p))
+        walls.append((time.perf_counter() - t0) * 1e3)
+        if rc != 0:
+            print(json.dumps({"workload": TCRAW_WORKLOAD, "error": rc}))
+            return 1
+    print(json.dumps({"workload": TCRAW_WORKLOAD, "cluster": args.tc_cluster, "wall_ms": walls}), flush=True)
+    return 0
+
+
 C5_WORKLOAD = ("ragged multi-instance batch: 512 instances, n uniform in [100,3000], density uniform in "
                "[0.05,1], half integer-[-100,100] Q, half Max-Cut (+-1 edges, f = -cut), BF16 Q_off on tensor "
                "cores with FP32 accumulation, FP64 exact evaluation, starts per instance from the restart tuner")
@@ -621,7 +707,8 @@ def main():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-c4", action="store_true",
                     help="skip the batched-restart time-to-objective comparison of the default line")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "ppa", "sync"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "ppa", "sync", "single", "tcraw"])
+    ap.add_argument("--tc-cluster", type=int, default=0, help="tcraw: CTAs splitting K (0 = rule, -1 = persistent)")
     ap.add_argument("--c5-count", type=int, default=512, help="instances of the ragged batch")
     ap.add_argument("--c5-restarts", type=int, default=0, help="starts per instance (0 = restart tuner)")
     ap.add_argument("--restarts", type=int, default=256)
@@ -640,6 +727,10 @@ def main():
         return run_ppa(args)
     if args.workload == "sync":
         return run_sync(args)
+    if args.workload == "single":
+        return run_single(args)
+    if args.workload == "tcraw":
+        return run_tcraw(args)
     if args.workload == "c4":
         return run_c4(args)
     if args.workload == "c5":

@@ -160,7 +160,9 @@ typedef struct {
     int tc_fuse;             /* tensor-core lanes: 1 = the contraction's epilogue warps run */
                              /* each lane's update as soon as its last M tile is done (one */
                              /* launch per step; lanes of at most 32 M tiles), 0 = a      */
-                             /* separate update launch after every contraction: 1        */
+                             /* separate update launch (one CTA per lane) after every     */
+                             /* contraction: 0 (the lanes of an N tile all finish on one  */
+                             /* tile, so fused updates serialize in one CTA)              */
     int sparse_storage;      /* FP32 lanes: Q'_off in sliced row storage (32-row slices of */
                              /* the stored entries: 4-byte value, 2-byte column), read by  */
                              /* every scheduler; 0 = when its bytes are fewer than the     */

@@ -33,6 +33,7 @@ class Opts(C.Structure):
         ("tol_inner", C.c_double), ("tol_outer", C.c_double), ("eta", C.c_double),
         ("gamma_margin", C.c_double), ("alpha_min", C.c_double), ("alpha_max", C.c_double),
         ("tau_z", C.c_double), ("eps_hp_rel", C.c_double), ("lambda_floor_rel", C.c_double),
+        ("fp32_noise", C.c_double), ("noise_seed", C.c_ulonglong),
     ]
 
 

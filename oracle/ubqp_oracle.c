@@ -31,6 +31,8 @@ void orc_opts_default(orc_opts* o)
     o->tau_z = 1e-12;
     o->eps_hp_rel = 1e-8;      /* Sec. 3.1: "arbitrarily small" epsilon */
     o->lambda_floor_rel = 4.0;
+    o->fp32_noise = 0.0;       /* rounding model off */
+    o->noise_seed = 0;
 }
 
 /* Eq. (bqp): f(x) = x^T Q x + b^T x on a binary point. */
@@ -265,6 +267,40 @@ static void penalized_gradient(int n, const double* Qp, const double* bp, const 
 
 static double clip01(double v) { return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v); }
 
+/* Rounding model of orc_opts.fp32_noise: SplitMix64 (Steele, Lea, Flood 2014) of a key, mapped
+ * to a uniform number in [-1, 1]. */
+static double noise_uniform(unsigned long long seed, long long count, int i)
+{
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(count * 1000003LL + i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+static void noise_gradient(int n, const double* Qp, const double* bp, const double* p, const double* x,
+                           double* g, const orc_opts* o, long long count)
+{
+    if (!(o->fp32_noise > 0.0)) return;
+    for (int i = 0; i < n; ++i) {
+        /* the terms of g_i = 2 sum_{j != i} Q'_ij x_j + (d_i - p_i)(2 x_i - 1) + (d_i + b'_i),
+         * where the gamma-sized parts of 2 (d_i - p_i) x_i and b'_i + p_i cancel exactly */
+        double s = 0.0;
+        for (int j = 0; j < n; ++j)
+            if (j != i) s += fabs(Qp[IDX(i, j, n)] * x[j]);
+        const double d = Qp[IDX(i, i, n)];
+        s = 2.0 * s + fabs((d - p[i]) * (2.0 * x[i] - 1.0)) + fabs(d + bp[i]);
+        g[i] += o->fp32_noise * noise_uniform(o->noise_seed, count, i) * s;
+    }
+}
+
+static void noise_iterate(int n, double* x, const orc_opts* o, long long count)
+{
+    if (!(o->fp32_noise > 0.0)) return;
+    for (int i = 0; i < n; ++i)
+        x[i] = clip01(x[i] * (1.0 + o->fp32_noise * noise_uniform(o->noise_seed ^ 0x5DEECE66Dull, count, i)));
+}
+
 /* Alg. 2 (PABB): x^{k+1} = P(x^k - alpha_k g^k), Eq. (x2), with the alternating
  * Barzilai-Borwein step of Eq. (bb1); Alg. 1 (PPA): x^{k+1} = P(x^k - g^k/(2 h_p)),
  * Eq. (x1), with H_p of Sec. 3.1.  Both stop on Eq. (cret). */
@@ -277,6 +313,7 @@ int orc_inner(int n, const double* Qp, const double* bp, const double* p, double
     double* gp = (double*)malloc((size_t)n * sizeof(double));
     double* hp = (double*)malloc((size_t)n * sizeof(double));
     penalized_gradient(n, Qp, bp, p, x, g);
+    noise_gradient(n, Qp, bp, p, x, g, o, 0);
     long long ge = 1;
     double rho = orc_rho(n, Qp, bp, p);
     double alpha = 0.0;
@@ -336,7 +373,9 @@ int orc_inner(int n, const double* Qp, const double* bp, const double* p, double
         }
         ++k;
         if (!moved) { code = 2; break; }
+        noise_iterate(n, x, o, ge);
         penalized_gradient(n, Qp, bp, p, x, g);
+        noise_gradient(n, Qp, bp, p, x, g, o, ge);
         ++ge;
     }
     free(g); free(xp); free(gp); free(hp);

@@ -44,6 +44,15 @@ typedef struct {
     double tau_z;           /* z_i > tau_z defines the index set of Eq. (eq:alpha)    */
     double eps_hp_rel;      /* PPA epsilon = eps_hp_rel * max(1, max_j r_j), Sec. 3.1 */
     double lambda_floor_rel;/* floor F = lambda_floor_rel * tol_inner * rho (Sec. 3.4)  */
+    /* Rounding model for sensitivity studies (tests only; 0 = off, the default, and then
+     * nothing below changes the arithmetic): after every gradient evaluation of orc_inner,
+     * g_i += fp32_noise * r * s_i with s_i = 2 sum_{j != i} |Q'_ij x_j| + |(d_i - p_i)(2 x_i - 1)|
+     * + |d_i + b'_i| (d = diag Q'; the terms of g_i once the gamma-sized parts of
+     * 2 (d_i - p_i) x_i and b'_i + p_i cancel), and after every projected step
+     * x_i <- clip(x_i (1 + fp32_noise * r')); r, r' uniform in [-1, 1] from SplitMix64 keyed
+     * by (noise_seed, evaluation, i). */
+    double fp32_noise;
+    unsigned long long noise_seed;
 } orc_opts;
 
 typedef struct {

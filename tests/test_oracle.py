@@ -373,3 +373,35 @@ def test_solve_random_start_path():
     fstar, _ = enumerate_min(Q, b)
     xb, f, st = O.solve(Q, b, I.perturbation(Q, 11), x_start=xs)
     assert f >= fstar and st["status"] == 0
+
+
+def test_rounding_model_is_off_by_default_and_bounded_when_on():
+    """The oracle's FP32 rounding model (fp32_noise, a sensitivity tool for the GPU tests) does
+    not touch the arithmetic when off, whatever its seed; when on, the first projected step of
+    Alg. 2 moves by at most alpha_0 * 2^-24 * s_i (s_i the gradient's terms) plus one ulp of
+    the iterate, and differs between seeds."""
+    rng = np.random.default_rng(3)
+    n = 40
+    Q, b = I.random_ubqp(n, 0.3, 3)
+    Qp, bp, _ = O.reformulate(Q, b, I.perturbation(Q, 3))
+    x0 = O.initial_point(Qp, bp)
+    a, _, _, _ = O.penalty_step(Qp, bp, np.zeros(n), x0)
+    p = a * (x0 - x0 * x0)
+    x = rng.uniform(0.2, 0.8, n)
+    ref = O.inner(Qp, bp, p, x, trace_len=3)
+    o = O.opts()
+    o.noise_seed = 99
+    same = O.inner(Qp, bp, p, x, o, trace_len=3)
+    assert np.array_equal(same["trace_x"], ref["trace_x"]) and same["steps"] == ref["steps"]
+    d = np.diag(Qp)
+    s = 2 * (np.abs(Qp - np.diag(d)) @ np.abs(x)) + np.abs((d - p) * (2 * x - 1)) + np.abs(d + bp)
+    alpha0 = 1.0 / (2 * np.max(np.sum(np.abs(Qp - np.diag(p)), axis=1)))
+    steps = []
+    for seed in (1, 2):
+        o.fp32_noise = 2.0 ** -24
+        o.noise_seed = seed
+        got = O.inner(Qp, bp, p, x, o, trace_len=3)
+        dx = np.abs(got["trace_x"][1] - ref["trace_x"][1])
+        assert np.all(dx <= alpha0 * 2.0 ** -24 * s + 2.0 ** -23 * np.abs(ref["trace_x"][1]) + 1e-300)
+        steps.append(got["trace_x"][1])
+    assert not np.array_equal(steps[0], steps[1])
