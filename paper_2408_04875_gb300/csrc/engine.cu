@@ -406,12 +406,14 @@ class Solver {
         while (rb < 32 && total_rows / rb > target_items) rb *= 2;
         if (o_.rows_per_item > 0) rb = o_.rows_per_item;
         if (sym_) rb = kSymT;   // the second stage works on whole tile rows
-        // sliced storage: items of whole 32-row slices (32, 64, 128 or 256 rows), 128 unless
-        // the caller asked for one of these
-        if (sparse_) rb = (o_.rows_per_item == 32 || o_.rows_per_item == 64 || o_.rows_per_item == 256) ? o_.rows_per_item : 128;
+        // sliced storage: items of whole 32-row slices (32, 64, 128 or 256 rows); one slice per
+        // item unless the caller asked for another of these (measured on the 40-lane sweep:
+        // 32 rows 13.7 s per step, 64 rows 13.9 s, 128 rows 15.5 s: the eight warps of a slice
+        // keep more loads in flight than two)
+        if (sparse_) rb = (o_.rows_per_item == 64 || o_.rows_per_item == 128 || o_.rows_per_item == 256) ? o_.rows_per_item : 32;
         // one FP32 lane: the single-lane persistent kernel (a cooperative launch of one CTA per
         // row block), unless another scheduler or the per-tick timeline is asked for
-        solo_ = !tc && !sym_ && lanes.size() == 1 && (size_t)max_ld * sizeof(float) <= 200 * 1024 &&
+        solo_ = !tc && !sym_ && lanes.size() == 1 && 2 * (size_t)max_ld * sizeof(float) <= 200 * 1024 &&
                 (o_.gemv_kernel == 3 || (o_.gemv_kernel == 0 && o_.profile_kernels < 2));
         if (solo_ && sparse_) {
             // one CTA per 32-row slice (one CTA for up to 256 rows), unless the caller chose
@@ -1217,6 +1219,7 @@ class Solver {
         sa.err = ctl + 2;
         sa.active_after = ctl + 3;
         sa.wait_ns = o_.wait_limit_us > 0 ? 1000ull * (unsigned long long)o_.wait_limit_us : 5000000000ull;
+        sa.fast = 1;
         sa.P = make_params(o_, ar_.at<int64_t>(o_hist_));
         const bool prof = o_.profile_kernels != 0;
         if (prof) sa.P.bytes = ar_.at<unsigned long long>(o_bytes_);

@@ -11,6 +11,12 @@
 //      same decision (decide) on its own copy of the lane state, so all copies stay equal;
 //      then it applies the element-wise update (lane_apply) to its slice;
 //   4. grid barrier (u complete).
+// Alg. 2 steps (PABB) take one barrier: every CTA holds the whole x_k and x_{k-1} in shared
+// memory, and after the barrier computes the whole x_{k+1} = P(x_k - alpha g_k) itself from g_k
+// (every CTA's rows are in global memory by then), instead of updating a slice and exchanging
+// it.  g alternates between two global buffers by the parity of k (V_G, V_W), so a CTA that
+// writes g_{k+1} never overwrites the g_k another CTA may still be reading.  When the
+// subproblem ends, or the launch's budget does, the CTAs write x_k, x_{k-1} and u back.
 // The arithmetic is that of the lock-step scheduler with the same rows per item, so both give
 // the same bits.  The launch is cooperative (every CTA resident), and each barrier wait is
 // bounded: when it runs out the CTA sets the error flag and leaves, and the others leave at
@@ -66,6 +72,47 @@ __device__ __forceinline__ bool solo_grid_sync(const SoloArgs& A, unsigned& gen,
     return *s_ok != 0;
 }
 
+// Alg. 2 row epilogue of the single-barrier step: the arithmetic of row_epilogue (PH_INNER)
+// with x_k and x_{k-1} from shared memory, g_{k-1} from gold and g_k written to gnew
+__device__ __forceinline__ void solo_inner_finish(const LaneDev& L, int k, int blk, int row0, int rows,
+                                                  const double* sv, const Params& P, const float* sx,
+                                                  const float* sxp, const float* gold, float* gnew)
+{
+    Acc a;
+    a.zero();
+    const int ld = L.ld;
+    if ((int)threadIdx.x < rows) {
+        const int i = row0 + threadIdx.x;
+        const float v = (float)sv[threadIdx.x];
+        const float x = sx[i];
+        const float dmp = L.vec[V_DMP * ld + i];
+        const float bb = L.vec[V_BBAR * ld + i];
+        const float g = fmaf(dmp, 2.f * x - 1.f, fmaf(2.f, v, L.tsum[i]));
+        if (k >= 1) {
+            const float sd = x - sxp[i];
+            const float y = g - gold[i];
+            csum_add(a.s[0], sd * sd);
+            csum_add(a.s[1], sd * y);
+            csum_add(a.s[2], y * y);
+        } else {
+            a.m[1] = fmaxf(a.m[1], fabsf(dmp));
+            a.m[2] = fmaxf(a.m[2], fabsf(bb));
+            a.m[3] = fmaxf(a.m[3], L.oabs[i] + fabsf(dmp));
+        }
+        gnew[i] = g;
+        const float viol = (x > 0.f && x < 1.f) ? fabsf(g) : (x <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
+        a.m[0] = fmaxf(a.m[0], viol);
+    }
+    block_reduce_write<kWarps>(a, PH_INNER, L.part + blk, false);
+    if (P.bytes && threadIdx.x == 0) {
+        unsigned long long by = (unsigned long long)rows * L.n * 4ull + (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
+        if (L.spv)
+            by = 6ull * (unsigned long long)(L.spo[(row0 + rows + 31) >> 5] - L.spo[row0 >> 5]) +
+                 (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
+        atomicAdd(P.bytes, by);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 1) solo_lane_kernel(SoloArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -98,32 +145,88 @@ __global__ void __launch_bounds__(kThreads, 1) solo_lane_kernel(SoloArgs A)
     const int ia = min(4 * qa, L.n), ib = min(4 * qb, L.n);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
+    // single-barrier Alg. 2 state: su = x_k and sxp = x_{k-1} (whole vectors) while fast is set
+    float* sxp = su + L.ld;
+    bool fast = false;
+    const bool pabb = L.method == 0;
+    float* gbuf[2] = {L.vec + (size_t)V_G * L.ld, L.vec + (size_t)V_W * L.ld};
+
     for (int step = 0; step < A.budget; ++step) {
         const int ph = S.phase;
         if (ph == PH_DONE) break;
         const int k = S.k;
+        const bool fast_step = A.fast && pabb && ph == PH_INNER;
+        if (!fast) {
+            item_load_u(L, su);
+            if (fast_step && k >= 1)
+                for (int c = threadIdx.x; c < L.ld; c += kThreads) sxp[c] = L.vec[(size_t)V_XPREV * L.ld + c];
+            __syncthreads();
+        }
         // ---- phase A: this CTA's row block(s)
-        item_load_u(L, su);
-        __syncthreads();
         for (int blk = blockIdx.x; blk < A.nblk; blk += gridDim.x) {
             const int row0 = blk * A.rows_per_item;
             const int rows = min(A.rows_per_item, L.n - row0);
             item_rows_solver(L, ph, row0, rows, su, sv, lane, warp);
             __syncthreads();
-            item_finish(L, ph, k, blk, row0, rows, sv, P);
+            if (fast_step) solo_inner_finish(L, k, blk, row0, rows, sv, P, su, sxp, gbuf[(k + 1) & 1], gbuf[k & 1]);
+            else item_finish(L, ph, k, blk, row0, rows, sv, P);
             __syncthreads();
         }
         if (!solo_grid_sync(A, gen, &s_ok)) break;
-        // ---- the update: the same reduction and decision in every CTA, then this CTA's slice
+        // ---- the update: the same reduction and decision in every CTA
         reduce_partials(L.part, A.nblk, ph, R);
         if (threadIdx.x == 0) decide(L, S, R, P, D);
         __syncthreads();
+        if (fast_step && (D.act & ~A_TRACE) == A_STEP_PABB && D.usrc == U_X) {
+            // x_{k+1} = P(x_k - alpha g_k) for every element, into the x_{k-1} buffer; the trace
+            // (x_k) is written for this CTA's slice
+            const float al = D.alpha;
+            const float* g = gbuf[k & 1];
+            if (D.act & A_TRACE)
+                for (int i = ia + (int)threadIdx.x; i < ib; i += kThreads) L.trace_x[(size_t)D.trace_k * L.n + i] = su[i];
+            __syncthreads();
+            for (int i = threadIdx.x; i < L.ld; i += kThreads) sxp[i] = fminf(fmaxf(fmaf(-al, g[i], su[i]), 0.f), 1.f);
+            __syncthreads();
+            float* t = su;
+            su = sxp;
+            sxp = t;
+            fast = true;
+            if (threadIdx.x == 0) {
+                S.updates += 1;
+                if (blockIdx.x == 0 && (D.act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
+            }
+            __syncthreads();
+            continue;
+        }
+        if (fast_step) {
+            // the subproblem ends (or the step is not a plain projected step): this CTA's slice of
+            // x_k, x_{k-1} and g_k back to the lane's vectors, then the general update
+            const float* g = gbuf[k & 1];
+            for (int i = ia + (int)threadIdx.x; i < ib; i += kThreads) {
+                L.vec[(size_t)V_X * L.ld + i] = su[i];
+                L.vec[(size_t)V_XPREV * L.ld + i] = sxp[i];
+                L.vec[(size_t)V_G * L.ld + i] = g[i];
+            }
+            __syncthreads();
+            fast = false;
+        }
         lane_apply(L, P, D, ia, ib, qa, qb, (int)threadIdx.x, (int)blockDim.x);
         if (threadIdx.x == 0) {
             S.updates += 1;
             if (blockIdx.x == 0 && (D.act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
         }
         if (!solo_grid_sync(A, gen, &s_ok)) break;
+    }
+    if (fast) {
+        // the launch ends inside a subproblem: x_k (also the next u) and x_{k-1} back to the lane
+        for (int i = ia + (int)threadIdx.x; i < ib; i += kThreads) {
+            L.vec[(size_t)V_X * L.ld + i] = su[i];
+            L.vec[(size_t)V_U * L.ld + i] = su[i];
+            L.vec[(size_t)V_XPREV * L.ld + i] = sxp[i];
+        }
+        // padding of u beyond n stays zero (x is zero there)
+        for (int i = L.n + (int)threadIdx.x + (int)blockIdx.x * kThreads; i < L.ld; i += kThreads * (int)gridDim.x)
+            L.vec[(size_t)V_U * L.ld + i] = 0.f;
     }
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -151,7 +254,7 @@ void solo_shape(int n, int rows_per_item, int sms, int* grid, int* rb, int* nblk
 
 cudaError_t prepare_solo(int ld)
 {
-    const size_t smem = (size_t)ld * sizeof(float);
+    const size_t smem = 2 * (size_t)ld * sizeof(float);
     if (smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(solo_lane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -163,7 +266,7 @@ cudaError_t launch_solo(const SoloArgs& a, int ld, cudaStream_t s)
     SoloArgs args = a;
     void* params[] = {&args};
     return cudaLaunchCooperativeKernel((const void*)solo_lane_kernel, dim3((unsigned)a.grid), dim3(kThreads), params,
-                                       (size_t)ld * sizeof(float), s);
+                                       2 * (size_t)ld * sizeof(float), s);
 }
 
 }  // namespace ubqp

@@ -443,6 +443,8 @@ struct SoloArgs {
     int32_t* err;               // set when a bounded wait runs out
     int32_t* active_after;      // 1 when the lane is unfinished at the end of the launch
     unsigned long long wait_ns; // limit of one barrier wait
+    int32_t fast;               // Alg. 2 steps with one barrier (whole x_k in every CTA)
+    int32_t pad_;
     Params P;
 };
 void solo_shape(int n, int rows_per_item, int sms, int* grid, int* rb, int* nblk);
