@@ -149,7 +149,8 @@ def c4_time_to_objective(device: int, restarts: int = 256):
     mu = np.diag(np.diag(I.perturbation(Q, 2)))
     starts = I.random_starts(2500, restarts - 1, 2)
     Qd, Md, Sd = (torch.from_numpy(a).cuda() for a in (Q, mu, starts))
-    ub.solve(Qd, None, mu=Md, starts=Sd, restarts=restarts, precision=ub.BF16X2_TC, max_outer=1)   # warm
+    _, _, swarm = ub.solve(Qd, None, mu=Md, starts=Sd, restarts=restarts, precision=ub.BF16X2_TC,
+                           max_outer=1)   # warm-up; its launch-form tuning is cached for the timed call
     sampler = ClockSampler(device)
     sampler.start()
     _, f32, s32 = ub.solve(Qd, None, mu=Md)
@@ -161,7 +162,10 @@ def c4_time_to_objective(device: int, restarts: int = 256):
     return {"workload": C4_WORKLOAD, "fp32_single_start": {"objective": f32, "ms": s32["ms_device"],
                                                            "steps": s32["ticks"], "scheduler": s32["gemv_kernel"]},
             "batched": {"restarts": restarts, "best_objective_at_stop": float(ftc), "ms_to_target": t_tc,
-                        "steps": stc["ticks"], "tc_kernel": stc["tc_kernel"], "cluster_size": stc["cluster_size"]},
+                        "steps": stc["ticks"], "tc_kernel": stc["tc_kernel"], "cluster_size": stc["cluster_size"],
+                        "us_per_step": (1e3 * t_tc / stc["ticks"]) if stc["ticks"] else None,
+                        "contraction_probe_us": {("persistent" if c == 0 else f"split_k_{c}"): t
+                                                 for c, t in enumerate(swarm["cluster_probe_us"]) if t > 0}},
             "target": target, "speedup": (s32["ms_device"] / t_tc) if t_tc and t_tc > 0 else None,
             "clocks": clocks}
 
@@ -212,6 +216,8 @@ def run_c4(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16x2", "data": "synthetic",
             "config": {"workload": C4_WORKLOAD, "restarts": args.restarts, "cluster_size": stats[-1]["cluster_size"],
+                       "contraction_probe_us": {("persistent" if c == 0 else f"split_k_{c}"): t
+                                                for c, t in enumerate(stats[-1]["cluster_probe_us"]) if t > 0},
                        "fp32_single_start": {"objective": f32, "ms_device": s32["ms_device"]},
                        "batched_best_objective": float(ftc), "ms_to_fp32_objective": stats[-1]["ms_to_target"],
                        "speedup_to_fp32_objective": (s32["ms_device"] / stats[-1]["ms_to_target"]

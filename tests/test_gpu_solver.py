@@ -370,7 +370,7 @@ def test_penalty_update_every_k_inner_iterations_vs_oracle(ub, K):
     that p moves every K iterations.  Three C2-law instances (n = 250) on the default schedulers
     against the oracle with the same cap: exact objectives.  Subproblems cut short leave the
     run more sensitive to rounding (which local optimum it ends in), so the objective bar is
-    0.1 % of the oracle where its own objective holds still under four FP32-rounding-sized
+    0.1 % of the oracle where its own objective holds still under 16 FP32-rounding-sized
     changes of the stored entries (mu + 1e-7 Q E, E symmetric standard normal), else no worse
     than the worst of those oracle runs plus 0.1 %."""
     Qs, mus = [], []
@@ -382,10 +382,10 @@ def test_penalty_update_every_k_inner_iterations_vs_oracle(ub, K):
     po = O.opts(max_inner=K)
     for Q, mu, x, f in zip(Qs, mus, xs, obj):
         fs = [O.solve(Q, None, mu, o=po)[1]]
-        for j in range(4):
+        for j in range(16):
             E = np.random.default_rng(j).standard_normal(Q.shape)
             fs.append(O.solve(Q, None, mu + 1e-7 * Q * (E + E.T) / 2, o=po)[1])
-        print(f"max_inner={K}: gpu {f} oracle {fs}")
+        print(f"max_inner={K}: gpu {f} oracle {fs[0]} spread {min(fs)} .. {max(fs)}")
         assert f == O.objective(Q, None, x)
         if max(fs) - min(fs) <= 1e-3 * abs(fs[0]):
             assert f - fs[0] <= 1e-3 * abs(fs[0]), (K, f, fs)
