@@ -242,24 +242,6 @@ __device__ __forceinline__ void item_rows_sell(const LaneDev& L, int row0, int r
         const float* V = L.spv + b + lane;
         const uint16_t* C = L.spc + b + lane;
         int k = k0;
-        // 16 entries (values and columns) in flight per lane, then 8
-        for (; k + 16 <= k1; k += 16) {
-            float q[16];
-            int c[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                q[j] = __ldg(V + 32 * (k + j));
-                c[j] = __ldg(C + 32 * (k + j));
-            }
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                float t = __fmul_rn(q[4 * h], su[c[4 * h]]);
-                t = fmaf(q[4 * h + 1], su[c[4 * h + 1]], t);
-                t = fmaf(q[4 * h + 2], su[c[4 * h + 2]], t);
-                t = fmaf(q[4 * h + 3], su[c[4 * h + 3]], t);
-                csum_add(acc, t);
-            }
-        }
         for (; k + 8 <= k1; k += 8) {
             float q[8];
             int c[8];

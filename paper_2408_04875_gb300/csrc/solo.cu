@@ -76,7 +76,8 @@ __device__ __forceinline__ bool solo_grid_sync(const SoloArgs& A, unsigned& gen,
 // with x_k and x_{k-1} from shared memory, g_{k-1} from gold and g_k written to gnew
 __device__ __forceinline__ void solo_inner_finish(const LaneDev& L, int k, int blk, int row0, int rows,
                                                   const double* sv, const Params& P, const float* sx,
-                                                  const float* sxp, const float* gold, float* gnew)
+                                                  const float* sxp, const float* gold, float* gnew,
+                                                  const float* dmpv, const float* tsumv, Partial* out)
 {
     Acc a;
     a.zero();
@@ -85,9 +86,8 @@ __device__ __forceinline__ void solo_inner_finish(const LaneDev& L, int k, int b
         const int i = row0 + threadIdx.x;
         const float v = (float)sv[threadIdx.x];
         const float x = sx[i];
-        const float dmp = L.vec[V_DMP * ld + i];
-        const float bb = L.vec[V_BBAR * ld + i];
-        const float g = fmaf(dmp, 2.f * x - 1.f, fmaf(2.f, v, L.tsum[i]));
+        const float dmp = dmpv[i];
+        const float g = fmaf(dmp, 2.f * x - 1.f, fmaf(2.f, v, tsumv[i]));
         if (k >= 1) {
             const float sd = x - sxp[i];
             const float y = g - gold[i];
@@ -96,14 +96,14 @@ __device__ __forceinline__ void solo_inner_finish(const LaneDev& L, int k, int b
             csum_add(a.s[2], y * y);
         } else {
             a.m[1] = fmaxf(a.m[1], fabsf(dmp));
-            a.m[2] = fmaxf(a.m[2], fabsf(bb));
+            a.m[2] = fmaxf(a.m[2], fabsf(L.vec[V_BBAR * ld + i]));
             a.m[3] = fmaxf(a.m[3], L.oabs[i] + fabsf(dmp));
         }
         gnew[i] = g;
         const float viol = (x > 0.f && x < 1.f) ? fabsf(g) : (x <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
         a.m[0] = fmaxf(a.m[0], viol);
     }
-    block_reduce_write<kWarps>(a, PH_INNER, L.part + blk, false);
+    block_reduce_write<kWarps>(a, PH_INNER, out, false);
     if (P.bytes && threadIdx.x == 0) {
         unsigned long long by = (unsigned long long)rows * L.n * 4ull + (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
         if (L.spv)
@@ -150,6 +150,28 @@ __global__ void __launch_bounds__(kThreads, 1) solo_lane_kernel(SoloArgs A)
     bool fast = false;
     const bool pabb = L.method == 0;
     float* gbuf[2] = {L.vec + (size_t)V_G * L.ld, L.vec + (size_t)V_W * L.ld};
+    // One CTA (n <= 256): during Alg. 2 the g buffers, d - p and d + b' live in shared memory
+    // and the step's partial record stays there too, so a step reads only the rows of Q from
+    // global memory.  The g buffers are loaded at the start and stored at the end of a launch
+    // that stops inside a subproblem.
+    const bool one = gridDim.x == 1 && A.fast != 0;
+    __shared__ Partial s_part;
+    float* sdmp = sxp + L.ld;
+    float* stsum = sdmp + L.ld;
+    const float* dmpv = L.vec + (size_t)V_DMP * L.ld;
+    const float* tsumv = L.tsum;
+    if (one) {
+        float* sg = stsum + L.ld;
+        for (int c = threadIdx.x; c < L.ld; c += kThreads) {
+            sg[c] = gbuf[0][c];
+            sg[L.ld + c] = gbuf[1][c];
+        }
+        gbuf[0] = sg;
+        gbuf[1] = sg + L.ld;
+        dmpv = sdmp;
+        tsumv = stsum;
+        __syncthreads();
+    }
 
     for (int step = 0; step < A.budget; ++step) {
         const int ph = S.phase;
@@ -160,6 +182,11 @@ __global__ void __launch_bounds__(kThreads, 1) solo_lane_kernel(SoloArgs A)
             item_load_u(L, su);
             if (fast_step && k >= 1)
                 for (int c = threadIdx.x; c < L.ld; c += kThreads) sxp[c] = L.vec[(size_t)V_XPREV * L.ld + c];
+            if (fast_step && one)   // d - p and d + b' are fixed for the subproblem
+                for (int c = threadIdx.x; c < L.ld; c += kThreads) {
+                    sdmp[c] = L.vec[(size_t)V_DMP * L.ld + c];
+                    stsum[c] = L.tsum[c];
+                }
             __syncthreads();
         }
         // ---- phase A: this CTA's row block(s)
@@ -168,13 +195,21 @@ __global__ void __launch_bounds__(kThreads, 1) solo_lane_kernel(SoloArgs A)
             const int rows = min(A.rows_per_item, L.n - row0);
             item_rows_solver(L, ph, row0, rows, su, sv, lane, warp);
             __syncthreads();
-            if (fast_step) solo_inner_finish(L, k, blk, row0, rows, sv, P, su, sxp, gbuf[(k + 1) & 1], gbuf[k & 1]);
+            if (fast_step)
+                solo_inner_finish(L, k, blk, row0, rows, sv, P, su, sxp, gbuf[(k + 1) & 1], gbuf[k & 1], dmpv, tsumv,
+                                  one ? &s_part : L.part + blk);
             else item_finish(L, ph, k, blk, row0, rows, sv, P);
             __syncthreads();
         }
         if (!solo_grid_sync(A, gen, &s_ok)) break;
-        // ---- the update: the same reduction and decision in every CTA
-        reduce_partials(L.part, A.nblk, ph, R);
+        // ---- the update: the same reduction and decision in every CTA (one CTA in Alg. 2: its
+        // single partial record, which the reduction would return unchanged)
+        if (fast_step && one) {
+            if (threadIdx.x == 0) R = s_part;
+            __syncthreads();
+        } else {
+            reduce_partials(L.part, A.nblk, ph, R);
+        }
         if (threadIdx.x == 0) decide(L, S, R, P, D);
         __syncthreads();
         if (fast_step && (D.act & ~A_TRACE) == A_STEP_PABB && D.usrc == U_X) {
@@ -224,6 +259,11 @@ __global__ void __launch_bounds__(kThreads, 1) solo_lane_kernel(SoloArgs A)
             L.vec[(size_t)V_U * L.ld + i] = su[i];
             L.vec[(size_t)V_XPREV * L.ld + i] = sxp[i];
         }
+        if (one)   // and the g buffers
+            for (int c = threadIdx.x; c < L.ld; c += kThreads) {
+                L.vec[(size_t)V_G * L.ld + c] = gbuf[0][c];
+                L.vec[(size_t)V_W * L.ld + c] = gbuf[1][c];
+            }
         // padding of u beyond n stays zero (x is zero there)
         for (int i = L.n + (int)threadIdx.x + (int)blockIdx.x * kThreads; i < L.ld; i += kThreads * (int)gridDim.x)
             L.vec[(size_t)V_U * L.ld + i] = 0.f;
@@ -252,9 +292,11 @@ void solo_shape(int n, int rows_per_item, int sms, int* grid, int* rb, int* nblk
     *grid = std::min(*nblk, sms);
 }
 
+static size_t solo_smem(int ld, int grid) { return (grid == 1 ? 6 : 2) * (size_t)ld * sizeof(float); }
+
 cudaError_t prepare_solo(int ld)
 {
-    const size_t smem = 2 * (size_t)ld * sizeof(float);
+    const size_t smem = solo_smem(ld, 1);
     if (smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(solo_lane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
@@ -266,7 +308,7 @@ cudaError_t launch_solo(const SoloArgs& a, int ld, cudaStream_t s)
     SoloArgs args = a;
     void* params[] = {&args};
     return cudaLaunchCooperativeKernel((const void*)solo_lane_kernel, dim3((unsigned)a.grid), dim3(kThreads), params,
-                                       2 * (size_t)ld * sizeof(float), s);
+                                       solo_smem(ld, a.grid), s);
 }
 
 }  // namespace ubqp
