@@ -115,6 +115,7 @@ def main():
     ctx = mp.get_context("spawn")
     with ctx.Pool(args.workers) as pool:
         for res in pool.imap_unordered(run_case, todo):
+            d = load(args.out)   # re-read: cases merged by another run since the start stay
             d["cases"][key(res)] = res
             save(d, args.out)
             print(key(res), res["f"], res["cpu_s"], "s", flush=True)
