@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "inner PG iters/s (batch×n) and time-to-oracle-objective vs plain FP32 path"
 UNIT = "lane-var-updates/s"
-GEMV_KERNELS = {1: "phase_a_gemv_kernel", 2: "lane_loop_kernel"}
+GEMV_KERNELS = {1: "phase_a_gemv_kernel", 2: "lane_loop_kernel", 3: "solo_lane_kernel"}
 # DRAM bytes (read + write) per algorithmic byte of lane_loop_kernel, from the ncu capture of
 # one whole-solve launch of this workload (profiles/lane_loop_kernel_c2.md); the symmetric
 # storage is the default, the dense rows the alternative (sym_storage = 0)
@@ -721,7 +721,7 @@ def main():
     ap.add_argument("--c5-count", type=int, default=512, help="instances of the ragged batch")
     ap.add_argument("--c5-restarts", type=int, default=0, help="starts per instance (0 = restart tuner)")
     ap.add_argument("--restarts", type=int, default=256)
-    ap.add_argument("--gemv-kernel", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--gemv-kernel", type=int, default=0, choices=[0, 1, 2, 3],
                     help="scheduler of the FP32 lanes: 0 library's choice, 1 lock-step, 2 lane loop")
     ap.add_argument("--rows-per-item", type=int, default=0,
                     help="FP32 lanes: matrix rows per work item (0 = library default)")

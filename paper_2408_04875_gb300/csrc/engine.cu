@@ -411,11 +411,14 @@ class Solver {
         // 32 rows 13.7 s per step, 64 rows 13.9 s, 128 rows 15.5 s: the eight warps of a slice
         // keep more loads in flight than two)
         if (sparse_) rb = (o_.rows_per_item == 64 || o_.rows_per_item == 128 || o_.rows_per_item == 256) ? o_.rows_per_item : 32;
-        // one FP32 lane: the single-lane persistent kernel (a cooperative launch of one CTA per
-        // row block), unless another scheduler or the per-tick timeline is asked for
-        solo_ = !tc && !sym_ && lanes.size() == 1 && 2 * (size_t)max_ld * sizeof(float) <= 200 * 1024 &&
-                (o_.gemv_kernel == 3 || (o_.gemv_kernel == 0 && o_.profile_kernels < 2));
-        if (solo_ && sparse_) {
+        // FP32 lanes on the single-lane persistent kernel (a cooperative launch in which each lane
+        // runs on its own group of CTAs): one lane whenever its vectors fit in shared memory; several
+        // lanes on the sliced storage when every lane gets a group of CTAs that owns at most
+        // kSoloMaxSl slices each, all groups resident at once; or when the caller asks for it
+        const bool solo_fit = !tc && !sym_ && 2 * (size_t)max_ld * sizeof(float) <= 200 * 1024;
+        const bool solo_auto = o_.gemv_kernel == 0 && o_.profile_kernels < 2;
+        solo_ = solo_fit && (o_.gemv_kernel == 3 || (solo_auto && (lanes.size() == 1 || sparse_)));
+        if (solo_ && lanes.size() == 1 && sparse_) {
             // one CTA per 32-row slice (one CTA for up to 256 rows), unless the caller chose
             const int n0 = (int)insts[lanes[0].inst].n;
             if (o_.rows_per_item != 64 && o_.rows_per_item != 128 && o_.rows_per_item != 256 && o_.rows_per_item != 32)
@@ -426,8 +429,23 @@ class Solver {
             }
             solo_nblk_ = (n0 + rb - 1) / rb;
             solo_grid_ = std::min(solo_nblk_, num_sms_);
-        } else if (solo_) {
+        } else if (solo_ && lanes.size() == 1) {
             solo_shape((int)insts[lanes[0].inst].n, o_.rows_per_item, num_sms_, &solo_grid_, &rb, &solo_nblk_);
+        }
+        if (solo_ && lanes.size() > 1) {
+            std::vector<int> nb(lanes.size());
+            for (size_t l = 0; l < lanes.size(); ++l) nb[l] = (int)((insts[lanes[l].inst].n + rb - 1) / rb);
+            const bool ok = plan_solo_groups(nb, max_ld, o_.gemv_kernel == 3);
+            if (!ok && o_.gemv_kernel == 3) {
+                set_error("the lanes do not fit the single-lane kernel");
+                return UBQP_ENOTSUP;
+            }
+            solo_ = ok;
+        } else if (solo_) {
+            solo_glanes_.assign(1, 0);
+            solo_gfirst_ = {0, 1};
+            solo_gcta_ = {0, solo_grid_};
+            solo_one_ok_ = solo_grid_ == 1 && 6 * (size_t)max_ld * sizeof(float) <= 200 * 1024;
         }
         rows_per_item_ = rb;
 
@@ -497,7 +515,11 @@ class Solver {
         o_symctr_ = sym_ ? ar_.reserve(lanes.size() * sizeof(unsigned int)) : 0;
         o_symlanes_ = sym_ ? ar_.reserve(lanes.size() * sizeof(SymLane)) : 0;
         o_queue_ = ar_.reserve(2 * sizeof(int32_t));
-        o_solo_ = ar_.reserve(4 * sizeof(int32_t));
+        // single-lane kernel: err, active_after, then one barrier of kSoloBarStride words per group,
+        // then the group tables
+        const size_t nsg = solo_ ? solo_gcta_.size() - 1 : 1;
+        o_solo_ = ar_.reserve((4 + nsg * kSoloBarStride) * sizeof(int32_t));
+        o_sologrp_ = solo_ ? ar_.reserve((solo_glanes_.size() + solo_gfirst_.size() + solo_gcta_.size()) * sizeof(int32_t)) : 0;
         o_lanes_ = ar_.reserve(lanes.size() * sizeof(LaneDev));
         o_linit_ = ar_.reserve(lanes.size() * sizeof(LaneInit));
         o_items_ = ar_.reserve((size_t)std::max<int64_t>(nitems, 1) * sizeof(int2));
@@ -511,7 +533,7 @@ class Solver {
         for (InstDev& I : inst_) xbuf += round_up((size_t)I.n, 256);
         o_final_xbuf_ = ar_.reserve(xbuf);
         nitems_ = (int)nitems;
-        if (!tc && nitems > 0) {
+        if (!tc && nitems > 0 && !solo_) {
             // scheduler of the FP32 lanes: the persistent lane loop, unless the lock-step
             // tick kernel is asked for (or the per-tick timeline, which needs one launch per
             // tick); ring entries hold lane and block indices in 16 bits each
@@ -546,7 +568,15 @@ class Solver {
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_counters_), 0, lanes.size() * sizeof(unsigned int), stream_));
         if (sym_) UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_symctr_), 0, lanes.size() * sizeof(unsigned int), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_queue_), 0, 2 * sizeof(int32_t), stream_));
-        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_solo_), 0, 4 * sizeof(int32_t), stream_));
+        UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_solo_), 0, (4 + nsg * kSoloBarStride) * sizeof(int32_t), stream_));
+        if (solo_) {
+            std::vector<int32_t> tab(solo_glanes_);
+            tab.insert(tab.end(), solo_gfirst_.begin(), solo_gfirst_.end());
+            tab.insert(tab.end(), solo_gcta_.begin(), solo_gcta_.end());
+            solo_tab_host_ = tab;
+            UBQP_CK(cudaMemcpyAsync(ar_.at<int32_t>(o_sologrp_), solo_tab_host_.data(), tab.size() * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, stream_));
+        }
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_valid_), 0, insts.size() * 4 * sizeof(float), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_nnz_), 0, insts.size() * sizeof(unsigned long long), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_scal_), 0, insts.size() * 4 * sizeof(float), stream_));
@@ -1210,20 +1240,25 @@ class Solver {
         SoloArgs sa;
         memset(&sa, 0, sizeof(sa));
         sa.lane = ar_.at<LaneDev>(o_lanes_);
+        const int32_t* tab = ar_.at<int32_t>(o_sologrp_);
+        sa.ngroups = (int)solo_gcta_.size() - 1;
+        sa.glanes = tab;
+        sa.gfirst = tab + solo_glanes_.size();
+        sa.gcta = sa.gfirst + solo_gfirst_.size();
         sa.rows_per_item = rows_per_item_;
-        sa.nblk = solo_nblk_;
         sa.budget = probe_ticks_ > 0 ? probe_ticks_ : (o_.lane_budget > 0 ? o_.lane_budget : 1024);
-        sa.grid = solo_grid_;
+        sa.grid = solo_gcta_.back();
         int32_t* ctl = ar_.at<int32_t>(o_solo_);
-        sa.bar = reinterpret_cast<unsigned*>(ctl);
-        sa.err = ctl + 2;
-        sa.active_after = ctl + 3;
+        sa.err = ctl;
+        sa.active_after = ctl + 1;
+        sa.bar = reinterpret_cast<unsigned*>(ctl + 4);
         sa.wait_ns = o_.wait_limit_us > 0 ? 1000ull * (unsigned long long)o_.wait_limit_us : 5000000000ull;
         sa.fast = 1;
+        sa.one_ok = solo_one_ok_ ? 1 : 0;
         sa.P = make_params(o_, ar_.at<int64_t>(o_hist_));
         const bool prof = o_.profile_kernels != 0;
         if (prof) sa.P.bytes = ar_.at<unsigned long long>(o_bytes_);
-        UBQP_CK(prepare_solo(max_ld_));
+        UBQP_CK(prepare_solo(max_ld_, solo_one_ok_));
         UBQP_CK(cudaMallocHost(&h_active_, 2 * sizeof(int32_t)));
         if (prof) {
             evA_.resize(2);
@@ -1234,10 +1269,11 @@ class Solver {
                             (int64_t)(o_.max_outer + 1) * (int64_t)(o_.max_inner + o_.lobpcg_max_iter + 8);
         int64_t granted = 0;
         for (;;) {
+            UBQP_CK(cudaMemsetAsync(sa.active_after, 0, sizeof(int32_t), stream_));
             if (prof) UBQP_CK(cudaEventRecord(evA_[0], stream_));
             UBQP_CK(launch_solo(sa, max_ld_, stream_));
             if (prof) UBQP_CK(cudaEventRecord(evA_[1], stream_));
-            UBQP_CK(cudaMemcpyAsync(h_active_, ctl + 2, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream_));
+            UBQP_CK(cudaMemcpyAsync(h_active_, ctl, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream_));
             launches_ += 1;
             granted += sa.budget;
             UBQP_CK(cudaStreamSynchronize(stream_));
@@ -1257,7 +1293,7 @@ class Solver {
             if (rc) return rc;
             if (stop) break;
             if (h_active_[1] == 0) break;
-            if (granted > cap) {
+            if (granted > cap * solo_max_lanes_) {
                 set_error("step cap %lld exceeded", (long long)cap);
                 return UBQP_ETIMEOUT;
             }
@@ -1267,8 +1303,66 @@ class Solver {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0_, ev1_);
         ms_device_ = ms;
-        ticks_ = -1;   // filled from the lane's own step count
+        ticks_ = -1;   // filled from the lanes' own step counts
         return UBQP_OK;
+    }
+
+    // Groups of CTAs for several lanes on the single-lane kernel, largest lanes first.  With
+    // at most as many lanes as resident CTAs, every lane gets its own group of ceil(nblk / m)
+    // CTAs for the smallest m (blocks per CTA) at which all groups are resident together; the
+    // automatic choice takes it only for m <= kSoloMaxSl (all of a CTA's slices in one pass).
+    // Otherwise (asked for explicitly) one-CTA groups share the lanes, each lane going to the
+    // group with the fewest blocks so far.
+    bool plan_solo_groups(const std::vector<int>& nb, int max_ld, bool forced)
+    {
+        const size_t nl = nb.size();
+        solo_one_ok_ = 6 * (size_t)max_ld * sizeof(float) <= 48 * 1024;
+        if (prepare_solo(max_ld, solo_one_ok_) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        const int per = solo_ctas_per_sm(max_ld, solo_one_ok_);
+        if (per < 1) return false;
+        const int64_t capc = (int64_t)per * num_sms_;
+        std::vector<int> order(nl);
+        for (size_t l = 0; l < nl; ++l) order[l] = (int)l;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nb[a] > nb[b]; });
+        solo_glanes_.clear();
+        solo_gfirst_.assign(1, 0);
+        solo_gcta_.assign(1, 0);
+        solo_max_lanes_ = 1;
+        const int maxnb = *std::max_element(nb.begin(), nb.end());
+        if ((int64_t)nl <= capc) {
+            int m = 1;
+            for (; m <= maxnb; ++m) {
+                int64_t tot = 0;
+                for (int b : nb) tot += (b + m - 1) / m;
+                if (tot <= capc) break;
+            }
+            if (!forced && m > kSoloMaxSl) return false;
+            for (int l : order) {
+                solo_glanes_.push_back(l);
+                solo_gfirst_.push_back((int)solo_glanes_.size());
+                solo_gcta_.push_back(solo_gcta_.back() + (nb[l] + m - 1) / m);
+            }
+            return true;
+        }
+        if (!forced) return false;
+        const int G = (int)capc;
+        std::vector<std::vector<int>> gl(G);
+        std::vector<int64_t> load(G, 0);
+        for (int l : order) {
+            const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            gl[g].push_back(l);
+            load[g] += nb[l];
+        }
+        for (int g = 0; g < G; ++g) {
+            for (int l : gl[g]) solo_glanes_.push_back(l);
+            solo_gfirst_.push_back((int)solo_glanes_.size());
+            solo_gcta_.push_back(g + 1);
+            solo_max_lanes_ = std::max(solo_max_lanes_, (int)gl[g].size());
+        }
+        return true;
     }
 
     // FP32 lanes on the persistent lane loop: each launch (seed + loop, one graph) lets
@@ -1548,7 +1642,10 @@ class Solver {
     Arena sp_ar_;                // the sliced storage (allocated once its size is known)
     int64_t sliced_entries_ = 0;
     int solo_grid_ = 0, solo_nblk_ = 0;
-    size_t o_solo_ = 0;
+    size_t o_solo_ = 0, o_sologrp_ = 0;
+    std::vector<int32_t> solo_glanes_, solo_gfirst_, solo_gcta_, solo_tab_host_;
+    bool solo_one_ok_ = false;
+    int solo_max_lanes_ = 1;
     int loop_grid_ = 0, loop_budget_ = 0;
     uint64_t loop_cap_ = 0;
     int nitems_ = 0;

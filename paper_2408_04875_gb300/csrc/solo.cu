@@ -43,21 +43,22 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
     return v;
 }
 
-// sense by generation: bar[0] counts arrivals, bar[1] is the generation released so far
-__device__ __forceinline__ bool solo_grid_sync(const SoloArgs& A, unsigned& gen, int* s_ok)
+// sense by generation: bar[0] counts arrivals, bar[1] is the generation released so far; the
+// nc CTAs of one group take part
+__device__ __forceinline__ bool solo_grid_sync(const SoloArgs& A, unsigned* bar, int nc, unsigned& gen, int* s_ok)
 {
     __syncthreads();
-    if (gridDim.x == 1) return *s_ok != 0;
+    if (nc == 1) return *s_ok != 0;
     if (threadIdx.x == 0) {
         const unsigned target = gen + 1u;
         __threadfence();
-        if (atomicAdd(&A.bar[0], 1u) == gridDim.x - 1u) {
-            A.bar[0] = 0u;
+        if (atomicAdd(&bar[0], 1u) == (unsigned)nc - 1u) {
+            bar[0] = 0u;
             __threadfence();
-            atomicExch(&A.bar[1], target);
+            atomicExch(&bar[1], target);
         } else {
             const uint64_t t0 = solo_clock();
-            while (ld_acquire_u32(&A.bar[1]) != target) {
+            while (ld_acquire_u32(&bar[1]) != target) {
                 if (solo_clock() - t0 > A.wait_ns) {
                     atomicExch(A.err, 1);
                     *s_ok = 0;
@@ -72,8 +73,40 @@ __device__ __forceinline__ bool solo_grid_sync(const SoloArgs& A, unsigned& gen,
     return *s_ok != 0;
 }
 
-// Alg. 2 row epilogue of the single-barrier step: the arithmetic of row_epilogue (PH_INNER)
-// with x_k and x_{k-1} from shared memory, g_{k-1} from gold and g_k written to gnew
+// Alg. 2 row epilogue of the single-barrier step for row i (x_k and x_{k-1} from shared memory,
+// g_{k-1} from gold, g_k written to gnew): the arithmetic of row_epilogue (PH_INNER)
+__device__ __forceinline__ void solo_inner_row(const LaneDev& L, int k, int i, float v, const float* sx,
+                                               const float* sxp, const float* gold, float* gnew, const float* dmpv,
+                                               const float* tsumv, Acc& a)
+{
+    const float x = sx[i];
+    const float dmp = dmpv[i];
+    const float g = fmaf(dmp, 2.f * x - 1.f, fmaf(2.f, v, tsumv[i]));
+    if (k >= 1) {
+        const float sd = x - sxp[i];
+        const float y = g - gold[i];
+        csum_add(a.s[0], sd * sd);
+        csum_add(a.s[1], sd * y);
+        csum_add(a.s[2], y * y);
+    } else {
+        a.m[1] = fmaxf(a.m[1], fabsf(dmp));
+        a.m[2] = fmaxf(a.m[2], fabsf(L.vec[V_BBAR * L.ld + i]));
+        a.m[3] = fmaxf(a.m[3], L.oabs[i] + fabsf(dmp));
+    }
+    gnew[i] = g;
+    const float viol = (x > 0.f && x < 1.f) ? fabsf(g) : (x <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
+    a.m[0] = fmaxf(a.m[0], viol);
+}
+
+__device__ __forceinline__ unsigned long long solo_item_bytes(const LaneDev& L, int blk, int row0, int rows)
+{
+    if (L.spv)
+        return 6ull * (unsigned long long)(L.spo[(row0 + rows + 31) >> 5] - L.spo[row0 >> 5]) +
+               (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
+    return (unsigned long long)rows * L.n * 4ull + (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
+}
+
+// the row epilogue of one block and its partial record, by the whole CTA
 __device__ __forceinline__ void solo_inner_finish(const LaneDev& L, int k, int blk, int row0, int rows,
                                                   const double* sv, const Params& P, const float* sx,
                                                   const float* sxp, const float* gold, float* gnew,
@@ -81,197 +114,362 @@ __device__ __forceinline__ void solo_inner_finish(const LaneDev& L, int k, int b
 {
     Acc a;
     a.zero();
-    const int ld = L.ld;
-    if ((int)threadIdx.x < rows) {
-        const int i = row0 + threadIdx.x;
-        const float v = (float)sv[threadIdx.x];
-        const float x = sx[i];
-        const float dmp = dmpv[i];
-        const float g = fmaf(dmp, 2.f * x - 1.f, fmaf(2.f, v, tsumv[i]));
-        if (k >= 1) {
-            const float sd = x - sxp[i];
-            const float y = g - gold[i];
-            csum_add(a.s[0], sd * sd);
-            csum_add(a.s[1], sd * y);
-            csum_add(a.s[2], y * y);
-        } else {
-            a.m[1] = fmaxf(a.m[1], fabsf(dmp));
-            a.m[2] = fmaxf(a.m[2], fabsf(L.vec[V_BBAR * ld + i]));
-            a.m[3] = fmaxf(a.m[3], L.oabs[i] + fabsf(dmp));
-        }
-        gnew[i] = g;
-        const float viol = (x > 0.f && x < 1.f) ? fabsf(g) : (x <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
-        a.m[0] = fmaxf(a.m[0], viol);
-    }
+    if ((int)threadIdx.x < rows)
+        solo_inner_row(L, k, row0 + threadIdx.x, (float)sv[threadIdx.x], sx, sxp, gold, gnew, dmpv, tsumv, a);
     block_reduce_write<kWarps>(a, PH_INNER, out, false);
-    if (P.bytes && threadIdx.x == 0) {
-        unsigned long long by = (unsigned long long)rows * L.n * 4ull + (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
-        if (L.spv)
-            by = 6ull * (unsigned long long)(L.spo[(row0 + rows + 31) >> 5] - L.spo[row0 >> 5]) +
-                 (blk == 0 ? 4ull * L.n : 0ull) + 16ull * rows;
-        atomicAdd(P.bytes, by);
+    if (P.bytes && threadIdx.x == 0) atomicAdd(P.bytes, solo_item_bytes(L, blk, row0, rows));
+}
+
+// The same epilogue and record for a block of at most 32 rows, by one warp (lane r: row r).
+// block_reduce_write over the CTA would merge this warp's sums with seven warps' zero sums in
+// warp order; the merges below are those, so the record has the same bits.
+__device__ __forceinline__ void solo_inner_finish_warp(const LaneDev& L, int k, int blk, int row0, int rows,
+                                                       const double* sv, const Params& P, const float* sx,
+                                                       const float* sxp, const float* gold, float* gnew,
+                                                       const float* dmpv, const float* tsumv, Partial* out,
+                                                       int lane)
+{
+    Acc a;
+    a.zero();
+    if (lane < rows) solo_inner_row(L, k, row0 + lane, (float)sv[lane], sx, sxp, gold, gnew, dmpv, tsumv, a);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) a.s[t] = csum_shfl_reduce(a.s[t]);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) a.m[t] = max_shfl_reduce(a.m[t]);
+    if (lane == 0) {
+        Partial R;
+        const float2 z2 = make_float2(0.f, 0.f);
+        for (int t = 0; t < 12; ++t) R.s[t] = z2;
+        for (int t = 0; t < 6; ++t) R.m[t] = 0.f;
+        R.f = 0.0;
+        const int ns = phase_nsum(PH_INNER), nm = phase_nmax(PH_INNER);
+        for (int t = 0; t < ns; ++t) R.s[t] = csum_merge(R.s[t], a.s[t]);
+        for (int t = 0; t < nm; ++t) R.m[t] = fmaxf(R.m[t], a.m[t]);
+        R.f += 0.0;
+        for (int w = 1; w < kWarps; ++w) {
+            for (int t = 0; t < ns; ++t) R.s[t] = csum_merge(R.s[t], z2);
+            for (int t = 0; t < nm; ++t) R.m[t] = fmaxf(R.m[t], 0.f);
+            R.f += 0.0;
+        }
+        *out = R;
+        if (P.bytes) atomicAdd(P.bytes, solo_item_bytes(L, blk, row0, rows));
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) solo_lane_kernel(SoloArgs A)
+// Products of ns (<= kSoloMaxSl) blocks of one 32-row slice each (sliced storage, 32 rows per
+// item), for sv[32 b + r].  Warp w takes share w of every slice -- the shares of item_rows_sell
+// with eight warps per slice -- and the slices' loads are interleaved, four entries of each
+// slice at a time, so a CTA that owns several slices keeps all of them in flight.  Per share
+// the operations are those of item_rows_sell (four products summed with FMAs and added to the
+// compensated sum, two such groups per eight entries, the last (width mod 8) entries one by
+// one), and the shares are merged in the same order, so the products have the same bits.
+__device__ __forceinline__ void solo_rows_sliced(const LaneDev& L, const int* sl, int ns, const float* su, double* sv,
+                                                 float2 (*s_share)[kThreads], int lane, int warp)
+{
+    float2 acc[kSoloMaxSl];
+    const float* V[kSoloMaxSl];
+    const uint16_t* Cc[kSoloMaxSl];
+    int ng[kSoloMaxSl], kt[kSoloMaxSl], ke[kSoloMaxSl];
+    int maxg = 0;
+#pragma unroll
+    for (int b = 0; b < kSoloMaxSl; ++b) {
+        acc[b] = make_float2(0.f, 0.f);
+        ng[b] = 0;
+        kt[b] = ke[b] = 0;
+        V[b] = nullptr;
+        Cc[b] = nullptr;
+        if (b < ns) {
+            const int64_t base = L.spo[sl[b]];
+            const int width = (int)((L.spo[sl[b] + 1] - base) >> 5);
+            const int k0 = width * warp / kWarps, k1 = width * (warp + 1) / kWarps;
+            V[b] = L.spv + base + lane + 32 * (int64_t)k0;
+            Cc[b] = L.spc + base + lane + 32 * (int64_t)k0;
+            ng[b] = ((k1 - k0) >> 3) * 2;
+            kt[b] = 4 * ng[b];
+            ke[b] = k1 - k0;
+            maxg = max(maxg, ng[b]);
+        }
+    }
+#pragma unroll 2
+    for (int j = 0; j < maxg; ++j) {
+        float q[kSoloMaxSl][4];
+        int c[kSoloMaxSl][4];
+#pragma unroll
+        for (int b = 0; b < kSoloMaxSl; ++b)
+            if (j < ng[b]) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    q[b][e] = __ldg(V[b] + 32 * (4 * j + e));
+                    c[b][e] = __ldg(Cc[b] + 32 * (4 * j + e));
+                }
+            }
+#pragma unroll
+        for (int b = 0; b < kSoloMaxSl; ++b)
+            if (j < ng[b]) {
+                float t = __fmul_rn(q[b][0], su[c[b][0]]);
+                t = fmaf(q[b][1], su[c[b][1]], t);
+                t = fmaf(q[b][2], su[c[b][2]], t);
+                t = fmaf(q[b][3], su[c[b][3]], t);
+                csum_add(acc[b], t);
+            }
+    }
+#pragma unroll
+    for (int b = 0; b < kSoloMaxSl; ++b)
+        if (b < ns) {
+            for (int k = kt[b]; k < ke[b]; ++k) csum_add(acc[b], __fmul_rn(__ldg(V[b] + 32 * k), su[__ldg(Cc[b] + 32 * k)]));
+            s_share[b][lane * kWarps + warp] = acc[b];
+        }
+    __syncthreads();
+    if ((int)threadIdx.x < 32 * ns) {
+        const float2* sh = s_share[threadIdx.x >> 5] + (threadIdx.x & 31) * kWarps;
+        float2 a = sh[0];
+        for (int w = 1; w < kWarps; ++w) a = csum_merge(a, sh[w]);
+        sv[threadIdx.x] = (double)(a.x + a.y);
+    }
+}
+
+// the scalar decision and the general element-wise update, out of line: they run on the rare
+// steps that are not plain projected steps, and inlined they would take registers from the
+// products' loop
+static __device__ __noinline__ void solo_decide(const LaneDev& L, LaneState& S, const Partial& R, const Params& P,
+                                                Decision& D)
+{
+    decide(L, S, R, P, D);
+}
+static __device__ __noinline__ void solo_apply(const LaneDev& L, const Params& P, const Decision& D, int ia, int ib,
+                                               int qa, int qb)
+{
+    solo_apply(L, P, D, ia, ib, qa, qb);
+}
+
+__global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* su = reinterpret_cast<float*>(smem_raw);
     __shared__ double sv[kThreads];
     __shared__ LaneState S;
     __shared__ Partial R;
     __shared__ Decision D;
-    __shared__ int s_ok;
+    __shared__ int s_ok, s_g;
     __shared__ unsigned s_gen0;
+    __shared__ float2 s_share[kSoloMaxSl][kThreads];
+    __shared__ Partial s_part;
     // the descriptor never changes: one copy in shared memory (this file's plain loads go to
     // L2, so every field read from global memory would be an L2 round trip)
     __shared__ __align__(16) LaneDev sL;
     static_assert(sizeof(LaneDev) % 8 == 0, "descriptor copied in 8-byte pieces");
-    if (threadIdx.x < (int)(sizeof(LaneDev) / 8))
-        reinterpret_cast<int2*>(&sL)[threadIdx.x] = __ldg(reinterpret_cast<const int2*>(A.lane) + threadIdx.x);
-    __syncthreads();
-    const LaneDev& L = sL;
+
+    // ---- this CTA's group, its rank in the group and the group's barrier
     if (threadIdx.x == 0) {
-        S = *L.st;
+        int g = 0;
+        if (A.gcta) {
+            int lo = 0, hi = A.ngroups - 1;   // the last group whose first CTA is <= blockIdx.x
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (A.gcta[mid] <= (int)blockIdx.x) lo = mid;
+                else hi = mid - 1;
+            }
+            g = lo;
+        }
+        s_g = g;
         s_ok = 1;
-        s_gen0 = ld_acquire_u32(&A.bar[1]);
     }
+    __syncthreads();
+    const int g = s_g;
+    const int c0 = A.gcta ? A.gcta[g] : 0;
+    const int nc = A.gcta ? A.gcta[g + 1] - c0 : (int)gridDim.x;
+    const int rank = (int)blockIdx.x - c0;
+    unsigned* bar = A.bar + (size_t)g * kSoloBarStride;
+    if (threadIdx.x == 0) s_gen0 = ld_acquire_u32(&bar[1]);
     __syncthreads();
     unsigned gen = s_gen0;
     Params P = A.P;
-    if (blockIdx.x != 0) P.hist = nullptr;   // the subproblem histogram is counted once
-    const int ng = L.ld >> 2;
-    const int qa = (int)((int64_t)ng * blockIdx.x / gridDim.x), qb = (int)((int64_t)ng * (blockIdx.x + 1) / gridDim.x);
-    const int ia = min(4 * qa, L.n), ib = min(4 * qb, L.n);
+    if (rank != 0) P.hist = nullptr;   // the subproblem histogram is counted once per lane
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int li0 = A.glanes ? A.gfirst[g] : 0, li1 = A.glanes ? A.gfirst[g + 1] : 1;
+    int steps_left = A.budget;
 
-    // single-barrier Alg. 2 state: su = x_k and sxp = x_{k-1} (whole vectors) while fast is set
-    float* sxp = su + L.ld;
-    bool fast = false;
-    const bool pabb = L.method == 0;
-    float* gbuf[2] = {L.vec + (size_t)V_G * L.ld, L.vec + (size_t)V_W * L.ld};
-    // One CTA (n <= 256): during Alg. 2 the g buffers, d - p and d + b' live in shared memory
-    // and the step's partial record stays there too, so a step reads only the rows of Q from
-    // global memory.  The g buffers are loaded at the start and stored at the end of a launch
-    // that stops inside a subproblem.
-    const bool one = gridDim.x == 1 && A.fast != 0;
-    __shared__ Partial s_part;
-    float* sdmp = sxp + L.ld;
-    float* stsum = sdmp + L.ld;
-    const float* dmpv = L.vec + (size_t)V_DMP * L.ld;
-    const float* tsumv = L.tsum;
-    if (one) {
-        float* sg = stsum + L.ld;
-        for (int c = threadIdx.x; c < L.ld; c += kThreads) {
-            sg[c] = gbuf[0][c];
-            sg[L.ld + c] = gbuf[1][c];
-        }
-        gbuf[0] = sg;
-        gbuf[1] = sg + L.ld;
-        dmpv = sdmp;
-        tsumv = stsum;
+    for (int li = li0; li < li1 && steps_left > 0; ++li) {
+        const int lane_id = A.glanes ? A.glanes[li] : 0;
+        __syncthreads();   // shared state of the previous lane no longer in use
+        if (threadIdx.x < (int)(sizeof(LaneDev) / 8))
+            reinterpret_cast<int2*>(&sL)[threadIdx.x] =
+                __ldg(reinterpret_cast<const int2*>(A.lane + lane_id) + threadIdx.x);
         __syncthreads();
-    }
+        const LaneDev& L = sL;
+        if (threadIdx.x == 0) S = *L.st;
+        __syncthreads();
+        if (S.phase == PH_DONE) continue;
+        const int nblk = L.nblk;
+        const int ng = L.ld >> 2;
+        const int qa = (int)((int64_t)ng * rank / nc), qb = (int)((int64_t)ng * (rank + 1) / nc);
+        const int ia = min(4 * qa, L.n), ib = min(4 * qb, L.n);
 
-    for (int step = 0; step < A.budget; ++step) {
-        const int ph = S.phase;
-        if (ph == PH_DONE) break;
-        const int k = S.k;
-        const bool fast_step = A.fast && pabb && ph == PH_INNER;
-        if (!fast) {
-            item_load_u(L, su);
-            if (fast_step && k >= 1)
-                for (int c = threadIdx.x; c < L.ld; c += kThreads) sxp[c] = L.vec[(size_t)V_XPREV * L.ld + c];
-            if (fast_step && one)   // d - p and d + b' are fixed for the subproblem
-                for (int c = threadIdx.x; c < L.ld; c += kThreads) {
-                    sdmp[c] = L.vec[(size_t)V_DMP * L.ld + c];
-                    stsum[c] = L.tsum[c];
+        // single-barrier Alg. 2 state: su = x_k and sxp = x_{k-1} (whole vectors) while fast is set
+        float* su = reinterpret_cast<float*>(smem_raw);
+        float* sxp = su + L.ld;
+        bool fast = false;
+        const bool pabb = L.method == 0;
+        float* gbuf[2] = {L.vec + (size_t)V_G * L.ld, L.vec + (size_t)V_W * L.ld};
+        // One CTA for a lane of one block: during Alg. 2 the g buffers, d - p and d + b' live in
+        // shared memory and the step's partial record stays there too, so a step reads only the
+        // rows of Q from global memory.  The g buffers are loaded at the start and stored at the
+        // end of a launch that stops inside a subproblem.
+        const bool one = nc == 1 && nblk == 1 && A.fast && A.one_ok;
+        float* sdmp = sxp + L.ld;
+        float* stsum = sdmp + L.ld;
+        const float* dmpv = L.vec + (size_t)V_DMP * L.ld;
+        const float* tsumv = L.tsum;
+        if (one) {
+            float* sg = stsum + L.ld;
+            for (int c = threadIdx.x; c < L.ld; c += kThreads) {
+                sg[c] = gbuf[0][c];
+                sg[L.ld + c] = gbuf[1][c];
+            }
+            gbuf[0] = sg;
+            gbuf[1] = sg + L.ld;
+            dmpv = sdmp;
+            tsumv = stsum;
+            __syncthreads();
+        }
+        // this CTA's blocks (sliced storage, 32 rows per item: all of them in one pass)
+        const bool multi = L.spv && A.rows_per_item == 32 && (nblk + nc - 1) / nc <= kSoloMaxSl;
+        int my_sl[kSoloMaxSl];
+        int my_n = 0;
+#pragma unroll
+        for (int b = 0; b < kSoloMaxSl; ++b) {
+            const int blk = rank + b * nc;
+            my_sl[b] = blk;
+            if (blk < nblk) my_n = b + 1;
+        }
+
+        for (; steps_left > 0; --steps_left) {
+            const int ph = S.phase;
+            if (ph == PH_DONE) break;
+            const int k = S.k;
+            const bool fast_step = A.fast && pabb && ph == PH_INNER;
+            if (!fast) {
+                item_load_u(L, su);
+                if (fast_step && k >= 1)
+                    for (int c = threadIdx.x; c < L.ld; c += kThreads) sxp[c] = L.vec[(size_t)V_XPREV * L.ld + c];
+                if (fast_step && one)   // d - p and d + b' are fixed for the subproblem
+                    for (int c = threadIdx.x; c < L.ld; c += kThreads) {
+                        sdmp[c] = L.vec[(size_t)V_DMP * L.ld + c];
+                        stsum[c] = L.tsum[c];
+                    }
+                __syncthreads();
+            }
+            // ---- phase A: this CTA's row block(s)
+            if (fast_step && multi) {
+                if (my_n > 0) {
+                    // one slice: the lock-step kernel's own function (eight entries in flight per load
+                    // round); several: all of them in one pass
+                    if (my_n == 1) item_rows_sell(L, my_sl[0] * 32, min(32, L.n - my_sl[0] * 32), su, sv, lane, warp);
+                    else solo_rows_sliced(L, my_sl, my_n, su, sv, s_share, lane, warp);
+                    __syncthreads();
+                    if (warp < my_n) {
+                        const int blk = my_sl[warp], row0 = blk * 32;
+                        solo_inner_finish_warp(L, k, blk, row0, min(32, L.n - row0), sv + 32 * warp, P, su, sxp,
+                                               gbuf[(k + 1) & 1], gbuf[k & 1], dmpv, tsumv,
+                                               one ? &s_part : L.part + blk, lane);
+                    }
                 }
+            } else {
+                for (int blk = rank; blk < nblk; blk += nc) {
+                    const int row0 = blk * A.rows_per_item;
+                    const int rows = min(A.rows_per_item, L.n - row0);
+                    item_rows_solver(L, ph, row0, rows, su, sv, lane, warp);
+                    __syncthreads();
+                    if (fast_step)
+                        solo_inner_finish(L, k, blk, row0, rows, sv, P, su, sxp, gbuf[(k + 1) & 1], gbuf[k & 1], dmpv,
+                                          tsumv, one ? &s_part : L.part + blk);
+                    else item_finish(L, ph, k, blk, row0, rows, sv, P);
+                    __syncthreads();
+                }
+            }
+            if (!solo_grid_sync(A, bar, nc, gen, &s_ok)) break;
+            // ---- the update: the same reduction and decision in every CTA (one CTA in Alg. 2: its
+            // single partial record, which the reduction would return unchanged)
+            if (fast_step && one) {
+                if (threadIdx.x == 0) R = s_part;
+                __syncthreads();
+            } else {
+                reduce_partials(L.part, nblk, ph, R);
+            }
+            if (threadIdx.x == 0) solo_decide(L, S, R, P, D);
             __syncthreads();
-        }
-        // ---- phase A: this CTA's row block(s)
-        for (int blk = blockIdx.x; blk < A.nblk; blk += gridDim.x) {
-            const int row0 = blk * A.rows_per_item;
-            const int rows = min(A.rows_per_item, L.n - row0);
-            item_rows_solver(L, ph, row0, rows, su, sv, lane, warp);
-            __syncthreads();
-            if (fast_step)
-                solo_inner_finish(L, k, blk, row0, rows, sv, P, su, sxp, gbuf[(k + 1) & 1], gbuf[k & 1], dmpv, tsumv,
-                                  one ? &s_part : L.part + blk);
-            else item_finish(L, ph, k, blk, row0, rows, sv, P);
-            __syncthreads();
-        }
-        if (!solo_grid_sync(A, gen, &s_ok)) break;
-        // ---- the update: the same reduction and decision in every CTA (one CTA in Alg. 2: its
-        // single partial record, which the reduction would return unchanged)
-        if (fast_step && one) {
-            if (threadIdx.x == 0) R = s_part;
-            __syncthreads();
-        } else {
-            reduce_partials(L.part, A.nblk, ph, R);
-        }
-        if (threadIdx.x == 0) decide(L, S, R, P, D);
-        __syncthreads();
-        if (fast_step && (D.act & ~A_TRACE) == A_STEP_PABB && D.usrc == U_X) {
-            // x_{k+1} = P(x_k - alpha g_k) for every element, into the x_{k-1} buffer; the trace
-            // (x_k) is written for this CTA's slice
-            const float al = D.alpha;
-            const float* g = gbuf[k & 1];
-            if (D.act & A_TRACE)
-                for (int i = ia + (int)threadIdx.x; i < ib; i += kThreads) L.trace_x[(size_t)D.trace_k * L.n + i] = su[i];
-            __syncthreads();
-            for (int i = threadIdx.x; i < L.ld; i += kThreads) sxp[i] = fminf(fmaxf(fmaf(-al, g[i], su[i]), 0.f), 1.f);
-            __syncthreads();
-            float* t = su;
-            su = sxp;
-            sxp = t;
-            fast = true;
+            if (fast_step && (D.act & ~A_TRACE) == A_STEP_PABB && D.usrc == U_X) {
+                // x_{k+1} = P(x_k - alpha g_k) for every element, into the x_{k-1} buffer; the trace
+                // (x_k) is written for this CTA's slice
+                const float al = D.alpha;
+                const float* gk = gbuf[k & 1];
+                if (D.act & A_TRACE)
+                    for (int i = ia + (int)threadIdx.x; i < ib; i += kThreads)
+                        L.trace_x[(size_t)D.trace_k * L.n + i] = su[i];
+                __syncthreads();
+                for (int i = threadIdx.x; i < L.ld; i += kThreads) sxp[i] = fminf(fmaxf(fmaf(-al, gk[i], su[i]), 0.f), 1.f);
+                __syncthreads();
+                float* t = su;
+                su = sxp;
+                sxp = t;
+                fast = true;
+                if (threadIdx.x == 0) {
+                    S.updates += 1;
+                    if (rank == 0 && (D.act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
+                }
+                __syncthreads();
+                continue;
+            }
+            if (fast_step) {
+                // the subproblem ends (or the step is not a plain projected step): this CTA's slice
+                // of x_k, x_{k-1} and g_k back to the lane's vectors, then the general update
+                const float* gk = gbuf[k & 1];
+                for (int i = ia + (int)threadIdx.x; i < ib; i += kThreads) {
+                    L.vec[(size_t)V_X * L.ld + i] = su[i];
+                    L.vec[(size_t)V_XPREV * L.ld + i] = sxp[i];
+                    L.vec[(size_t)V_G * L.ld + i] = gk[i];
+                }
+                __syncthreads();
+                fast = false;
+                // the buffers may have traded places: x_k goes back to the start of shared memory
+                su = reinterpret_cast<float*>(smem_raw);
+                sxp = su + L.ld;
+            }
+            solo_apply(L, P, D, ia, ib, qa, qb);
             if (threadIdx.x == 0) {
                 S.updates += 1;
-                if (blockIdx.x == 0 && (D.act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
+                if (rank == 0 && (D.act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
             }
-            __syncthreads();
-            continue;
+            if (!solo_grid_sync(A, bar, nc, gen, &s_ok)) break;
         }
-        if (fast_step) {
-            // the subproblem ends (or the step is not a plain projected step): this CTA's slice of
-            // x_k, x_{k-1} and g_k back to the lane's vectors, then the general update
-            const float* g = gbuf[k & 1];
+        if (fast) {
+            // the launch ends inside a subproblem: x_k (also the next u) and x_{k-1} back to the lane
             for (int i = ia + (int)threadIdx.x; i < ib; i += kThreads) {
                 L.vec[(size_t)V_X * L.ld + i] = su[i];
+                L.vec[(size_t)V_U * L.ld + i] = su[i];
                 L.vec[(size_t)V_XPREV * L.ld + i] = sxp[i];
-                L.vec[(size_t)V_G * L.ld + i] = g[i];
             }
-            __syncthreads();
-            fast = false;
+            if (one)   // and the g buffers
+                for (int c = threadIdx.x; c < L.ld; c += kThreads) {
+                    L.vec[(size_t)V_G * L.ld + c] = gbuf[0][c];
+                    L.vec[(size_t)V_W * L.ld + c] = gbuf[1][c];
+                }
+            // padding of u beyond n stays zero (x is zero there)
+            for (int i = L.n + (int)threadIdx.x + rank * kThreads; i < L.ld; i += kThreads * nc)
+                L.vec[(size_t)V_U * L.ld + i] = 0.f;
         }
-        lane_apply(L, P, D, ia, ib, qa, qb, (int)threadIdx.x, (int)blockDim.x);
-        if (threadIdx.x == 0) {
-            S.updates += 1;
-            if (blockIdx.x == 0 && (D.act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
-        }
-        if (!solo_grid_sync(A, gen, &s_ok)) break;
+        __syncthreads();
+        if (rank == 0 && threadIdx.x == 0) *L.st = S;
+        if (!s_ok) break;
     }
-    if (fast) {
-        // the launch ends inside a subproblem: x_k (also the next u) and x_{k-1} back to the lane
-        for (int i = ia + (int)threadIdx.x; i < ib; i += kThreads) {
-            L.vec[(size_t)V_X * L.ld + i] = su[i];
-            L.vec[(size_t)V_U * L.ld + i] = su[i];
-            L.vec[(size_t)V_XPREV * L.ld + i] = sxp[i];
-        }
-        if (one)   // and the g buffers
-            for (int c = threadIdx.x; c < L.ld; c += kThreads) {
-                L.vec[(size_t)V_G * L.ld + c] = gbuf[0][c];
-                L.vec[(size_t)V_W * L.ld + c] = gbuf[1][c];
-            }
-        // padding of u beyond n stays zero (x is zero there)
-        for (int i = L.n + (int)threadIdx.x + (int)blockIdx.x * kThreads; i < L.ld; i += kThreads * (int)gridDim.x)
-            L.vec[(size_t)V_U * L.ld + i] = 0.f;
-    }
+    // ---- the group's lanes still unfinished (rank 0 wrote the state of every lane it ran)
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        *L.st = S;
-        *A.active_after = S.phase != PH_DONE ? 1 : 0;
+    if (rank == 0 && threadIdx.x == 0) {
+        int left = 0;
+        for (int li = li0; li < li1; ++li) {
+            const int lane_id = A.glanes ? A.glanes[li] : 0;
+            left += A.lane[lane_id].st->phase != PH_DONE ? 1 : 0;
+        }
+        if (left) atomicAdd(A.active_after, left);
     }
 }
 
@@ -292,13 +490,25 @@ void solo_shape(int n, int rows_per_item, int sms, int* grid, int* rb, int* nblk
     *grid = std::min(*nblk, sms);
 }
 
-static size_t solo_smem(int ld, int grid) { return (grid == 1 ? 6 : 2) * (size_t)ld * sizeof(float); }
+size_t solo_smem(int ld, bool one) { return (one ? 6 : 2) * (size_t)ld * sizeof(float); }
 
-cudaError_t prepare_solo(int ld)
+cudaError_t prepare_solo(int ld, bool one)
 {
-    const size_t smem = solo_smem(ld, 1);
+    const size_t smem = solo_smem(ld, one);
     if (smem <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(solo_lane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// CTAs of the kernel resident on one SM with the dynamic shared memory of lanes of ld
+int solo_ctas_per_sm(int ld, bool one)
+{
+    int per = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, solo_lane_kernel, kThreads, solo_smem(ld, one)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        per = 0;
+    }
+    return per;
 }
 
 // every CTA must be resident: a cooperative launch fails instead of starting a grid that
@@ -308,7 +518,7 @@ cudaError_t launch_solo(const SoloArgs& a, int ld, cudaStream_t s)
     SoloArgs args = a;
     void* params[] = {&args};
     return cudaLaunchCooperativeKernel((const void*)solo_lane_kernel, dim3((unsigned)a.grid), dim3(kThreads), params,
-                                       solo_smem(ld, a.grid), s);
+                                       solo_smem(ld, a.one_ok != 0), s);
 }
 
 }  // namespace ubqp

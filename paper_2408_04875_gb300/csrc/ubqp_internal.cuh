@@ -432,23 +432,31 @@ struct LoopArgs {
     Params P;
 };
 
-// one FP32 lane as one persistent cooperative launch (solo.cu)
+// FP32 lanes as one persistent cooperative launch (solo.cu): the CTAs form groups, and each
+// group runs its lanes one after another, every lane on all CTAs of its group
 struct SoloArgs {
-    const LaneDev* lane;
+    const LaneDev* lane;        // the lanes
+    const int32_t* glanes;      // lane indices, group after group (null: lane 0 alone)
+    const int32_t* gfirst;      // group g's lanes: glanes[gfirst[g] .. gfirst[g+1])
+    const int32_t* gcta;        // group g's CTAs: gcta[g] .. gcta[g+1]-1 (null: one group)
+    int32_t ngroups;
     int32_t rows_per_item;
-    int32_t nblk;
-    int32_t budget;             // steps this launch may take
+    int32_t budget;             // steps each group may take in this launch
     int32_t grid;
-    unsigned* bar;              // grid barrier: [0] arrivals, [1] generation released
+    unsigned* bar;              // per group (stride kSoloBarStride): [0] arrivals, [1] generation
     int32_t* err;               // set when a bounded wait runs out
-    int32_t* active_after;      // 1 when the lane is unfinished at the end of the launch
+    int32_t* active_after;      // lanes unfinished at the end of the launch (the caller zeroes it)
     unsigned long long wait_ns; // limit of one barrier wait
     int32_t fast;               // Alg. 2 steps with one barrier (whole x_k in every CTA)
-    int32_t pad_;
+    int32_t one_ok;             // shared memory holds the one-CTA state (6 vectors)
     Params P;
 };
+constexpr int kSoloBarStride = 32;   // unsigned per group barrier (128 bytes)
+constexpr int kSoloMaxSl = 6;        // 32-row slices a CTA computes in one pass
 void solo_shape(int n, int rows_per_item, int sms, int* grid, int* rb, int* nblk);
-cudaError_t prepare_solo(int ld);
+size_t solo_smem(int ld, bool one);
+cudaError_t prepare_solo(int ld, bool one);
+int solo_ctas_per_sm(int ld, bool one);
 cudaError_t launch_solo(const SoloArgs& a, int ld, cudaStream_t s);
 
 cudaError_t prepare_lane_loop(int max_ld);

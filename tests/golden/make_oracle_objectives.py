@@ -10,6 +10,10 @@ Cases:
   path uses; for each start r the oracle's objective of Alg. 3 run from that start alone
   (r = 0: x^0 of Eq. (gamma); r >= 1: row r-1 of instances.random_starts(n, R-1, seed)).
   n = 1000, seed 2, R = 32; and n = 2500, seed 2, start 0 only.
+- "c2d": the "c2" instances with the stored entries changed by about one FP32 rounding,
+  mu + 1e-7 Q (E + E^T)/2 with E standard normal from numpy's default_rng(draw): draws 1-16
+  at n = 500 and 1000, draws 1-7 at n = 2500.  How far these runs spread shows how much the
+  method's end point (which local optimum Alg. 3 reaches) depends on rounding.
 - "c5": four instances of the ragged-batch law (instances.c5_specs(4, seed=7, n_lo=100,
   n_hi=400): two integer-Q, two Max-Cut), diagonal-only perturbation drawn as for "c4"
   with the instance's own seed, R = 8 starts each (start 0 = x^0, then
@@ -19,7 +23,7 @@ An oracle solve takes about 1 s at n = 250, 11 s at n = 500, 3 min at n = 1000 a
 n = 2500 on one core, so the cases run in a process pool and the file is rewritten after
 each finished case (a later run computes only the cases still missing).  Run from the
 repository root:
-    python tests/golden/make_oracle_objectives.py [--workers K] [--only c2|c4|c5] [--out FILE]
+    python tests/golden/make_oracle_objectives.py [--workers K] [--only c2|c2d|c4|c5] [--out FILE]
     python tests/golden/make_oracle_objectives.py --merge FILE   # add FILE's cases to the golden file
 """
 import argparse
@@ -41,6 +45,8 @@ def case_list():
     for n, seeds in ((500, (0, 1, 2)), (1000, (0, 1, 2)), (2500, (0,))):
         for s in seeds:
             cases.append({"family": "c2", "n": n, "seed": s, "start": 0})
+            for d in range(1, (7 if n == 2500 else 16) + 1):
+                cases.append({"family": "c2d", "n": n, "seed": s, "start": 0, "draw": d})
     for r in range(C4_R):
         cases.append({"family": "c4", "n": 1000, "seed": 2, "start": r, "R": C4_R})
     cases.append({"family": "c4", "n": 2500, "seed": 2, "start": 0, "R": 256})
@@ -53,7 +59,8 @@ def case_list():
 
 
 def key(c):
-    return f"{c['family']}:n={c['n']}:seed={c['seed']}:start={c['start']}"
+    k = f"{c['family']}:n={c['n']}:seed={c['seed']}:start={c['start']}"
+    return k + f":draw={c['draw']}" if "draw" in c else k
 
 
 def run_case(c):
@@ -61,9 +68,12 @@ def run_case(c):
     import oracle as O
     from paper_2408_04875_gb300 import instances as I
     t0 = time.time()
-    if c["family"] == "c2":
+    if c["family"] in ("c2", "c2d"):
         Q, b = I.c2_instance(c["n"], c["seed"])
         mu = I.perturbation(Q, c["seed"])
+        if c["family"] == "c2d":
+            E = np.random.default_rng(c["draw"]).standard_normal(Q.shape)
+            mu = mu + 1e-7 * Q * (E + E.T) / 2
         xs = None
     else:
         if c["family"] == "c4":
@@ -100,6 +110,7 @@ def main():
     ap.add_argument("--only", default=None)
     ap.add_argument("--out", default=PATH)
     ap.add_argument("--merge", default=None)
+    ap.add_argument("--small-first", action="store_true", help="start the short solves first")
     args = ap.parse_args()
     if args.merge:
         d = load()
@@ -111,7 +122,7 @@ def main():
     O.build()
     d = load(args.out)
     todo = [c for c in case_list() if key(c) not in d["cases"] and (args.only is None or c["family"] == args.only)]
-    todo.sort(key=lambda c: -c["n"])   # the long solves start first
+    todo.sort(key=lambda c: c["n"] if args.small_first else -c["n"])   # by default the long solves first
     ctx = mp.get_context("spawn")
     with ctx.Pool(args.workers) as pool:
         for res in pool.imap_unordered(run_case, todo):

@@ -412,10 +412,11 @@ def test_ragged_batch_matches_single_solves(ub):
 @pytest.mark.parametrize("specs", [[(37, 1)], [(1000, 2)], [(2500, 3)], [(250, 4), (1000, 5), (61, 6)],
                                    [(300, 7), (2000, 8), (90, 9), (777, 10), (1500, 11)]])
 def test_schedulers_agree_bitwise(ub, specs, sparse):
-    """The lock-step scheduler (one launch per step of all lanes) and the persistent lane
-    loop (lanes advance independently inside one launch) run the same row kernels in the
-    same order of operations, so every solve is bit-identical: single lanes of 1, 63 and
-    157 row blocks and ragged batches of three and five sizes."""
+    """The lock-step scheduler (one launch per step of all lanes), the persistent lane loop
+    (lanes advance independently inside one launch) and, for batches, the single-lane kernel
+    with a group of CTAs per lane run the same row kernels in the same order of operations, so
+    every solve is bit-identical: single lanes of 1, 63 and 157 row blocks and ragged batches
+    of three and five sizes."""
     Qs = [I.random_ubqp(n, 0.1, s)[0] for n, s in specs]
     mus = [I.perturbation(Q, s) for Q, (n, s) in zip(Qs, specs)]
     kw = dict(max_outer=4, sym_storage=0, sparse_storage=sparse)   # dense rows, or sliced rows, in both
@@ -425,10 +426,16 @@ def test_schedulers_agree_bitwise(ub, specs, sparse):
     assert np.array_equal(f1, f2) and all(np.array_equal(a, b) for a, b in zip(x1, x2))
     for key in ("inner_iters", "outer_steps", "lobpcg_iters", "jacobi_iters", "var_updates"):
         assert s1[key] == s2[key], key
+    if len(specs) > 1:   # lane groups on the single-lane kernel (the same items as lock-step)
+        x3, f3, s3 = ub.solve_batched(Qs, None, mus, gemv_kernel=3, **kw)
+        assert s3["gemv_kernel"] == 3
+        assert np.array_equal(f1, f3) and all(np.array_equal(a, b) for a, b in zip(x1, x3))
+        for key in ("inner_iters", "outer_steps", "lobpcg_iters", "jacobi_iters", "var_updates"):
+            assert s1[key] == s3[key], key
     _, _, s0 = ub.solve_batched(Qs, None, mus, max_outer=4)
-    # the default: the single-lane kernel for one lane, the loop from 4 lanes, lock-step in
-    # between; at density 0.1 the sliced rows (their bytes are fewer than the symmetric tiles')
-    assert s0["gemv_kernel"] == (3 if len(specs) == 1 else (2 if len(specs) >= 4 else 1))
+    # the default at density 0.1: the sliced rows (their bytes are fewer than the symmetric
+    # tiles'), and on them the single-lane kernel with a group of CTAs per lane
+    assert s0["gemv_kernel"] == 3
     assert s0["storage"] == 2
 
 
@@ -443,11 +450,12 @@ def test_single_lane_kernel_agrees_with_lockstep_bitwise(ub, n, seed, budget):
     mu = I.perturbation(Q, seed)
     kw = dict(max_outer=6, rows_per_item=16, sparse_storage=2)
     if budget == 0 and n in (1000, 2500):   # the sliced rows too, with the same items in both
-        kw2 = dict(max_outer=6, rows_per_item=64, sparse_storage=1)
-        x1, f1, s1 = ub.solve(Q, None, mu=mu, gemv_kernel=1, **kw2)
-        x3, f3, s3 = ub.solve(Q, None, mu=mu, gemv_kernel=3, **kw2)
-        assert s1["storage"] == 2 and s3["storage"] == 2
-        assert f1 == f3 and np.array_equal(x1, x3) and s1["inner_iters"] == s3["inner_iters"]
+        for rb in (64, 32):   # 32: one slice per CTA, the warp-level epilogue
+            kw2 = dict(max_outer=6, rows_per_item=rb, sparse_storage=1)
+            x1, f1, s1 = ub.solve(Q, None, mu=mu, gemv_kernel=1, **kw2)
+            x3, f3, s3 = ub.solve(Q, None, mu=mu, gemv_kernel=3, **kw2)
+            assert s1["storage"] == 2 and s3["storage"] == 2
+            assert f1 == f3 and np.array_equal(x1, x3) and s1["inner_iters"] == s3["inner_iters"]
     x1, f1, s1 = ub.solve(Q, None, mu=mu, gemv_kernel=1, **kw)
     x3, f3, s3 = ub.solve(Q, None, mu=mu, gemv_kernel=3, lane_budget=budget, **kw)
     assert s1["gemv_kernel"] == 1 and s3["gemv_kernel"] == 3
@@ -456,6 +464,32 @@ def test_single_lane_kernel_agrees_with_lockstep_bitwise(ub, n, seed, budget):
         assert s1[key] == s3[key], key
     if budget:
         assert s3["kernel_launches"] > 100
+
+
+@pytest.mark.parametrize("case", ["mixed", "mixed_budget", "many"])
+def test_lane_groups_agree_with_lockstep_bitwise(ub, case):
+    """Several lanes on the single-lane kernel.  "mixed": every lane on its own group of CTAs
+    (sliced rows, 32-row items, a CTA computing up to six slices in one pass), also relaunched
+    every 7 steps; "many": more lanes than resident CTAs, so one-CTA groups run several lanes in
+    turn (lanes of one slice keep Alg. 2 in shared memory).  Same objectives, points and step
+    counts as the lock-step scheduler with the same items."""
+    if case.startswith("mixed"):
+        specs = [(2500, 11), (1000, 12), (500, 13), (250, 14), (37, 15), (1000, 16), (300, 17)]
+    else:
+        specs = [(20 + (i % 5) * 7, 100 + i) for i in range(400)]
+    Qs = [I.random_ubqp(n, 0.1, s)[0] for n, s in specs]
+    mus = [I.perturbation(Q, s) for Q, (n, s) in zip(Qs, specs)]
+    kw = dict(max_outer=4, rows_per_item=32, sparse_storage=1)
+    budget = {"mixed": 0, "mixed_budget": 7, "many": 5}[case]
+    x1, f1, s1 = ub.solve_batched(Qs, None, mus, gemv_kernel=1, **kw)
+    x3, f3, s3 = ub.solve_batched(Qs, None, mus, gemv_kernel=3, lane_budget=budget, **kw)
+    assert s1["gemv_kernel"] == 1 and s3["gemv_kernel"] == 3 and s3["storage"] == 2
+    assert np.array_equal(f1, f3) and all(np.array_equal(a, b) for a, b in zip(x1, x3))
+    for key in ("inner_iters", "inner_steps", "outer_steps", "lobpcg_iters", "jacobi_iters", "var_updates"):
+        assert s1[key] == s3[key], key
+    if case == "mixed":   # the automatic choice for FP32 lanes on the sliced storage
+        _, _, s0 = ub.solve_batched(Qs, None, mus, max_outer=1)
+        assert s0["gemv_kernel"] == 3 and s0["storage"] == 2
 
 
 def test_lane_loop_small_budget_relaunches(ub):
