@@ -486,7 +486,8 @@ class Solver {
             if (!tc) nitems += sym_ ? sym_slots(sym_host_[l]) : L.nblk;
             o_vec_[l] = ar_.reserve((size_t)NVEC * I.ld * 4);
             o_bx_[l] = ar_.reserve((size_t)I.ld);
-            o_part_[l] = ar_.reserve((size_t)L.nblk * sizeof(Partial));
+            // the single-lane kernel's one-barrier steps alternate between two sets of records
+            o_part_[l] = ar_.reserve((size_t)(solo_ ? 2 : 1) * L.nblk * sizeof(Partial));
             if (in.trace_len > 0) {
                 o_trace_x_[l] = ar_.reserve((size_t)in.trace_len * I.n * 4);
                 o_trace_a_[l] = ar_.reserve((size_t)in.trace_len * 4);

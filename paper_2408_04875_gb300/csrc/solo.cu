@@ -1,26 +1,30 @@
-// One FP32 lane (a single instance solved from a single start: the plain FP32 path) as one
-// persistent launch that runs many steps of Alg. 3 with Alg. 2 (or Alg. 1).
+// FP32 lanes (an instance solved from one start: the plain FP32 path), each as a persistent
+// run of many steps of Alg. 3 with Alg. 2 (or Alg. 1), in one cooperative launch.
 //
-// A step is the matrix-vector product of the lane's phase over all CTAs, then its update.
-// CTA c owns row block c of the lane (rows_per_item rows, as many blocks as CTAs) and a
+// The CTAs form groups; group g owns CTAs gcta[g] .. gcta[g+1]-1 and runs its lanes one after
+// another (one group and one lane for a single instance).  A step of a lane is the
+// matrix-vector product of the lane's phase over the group's CTAs, then its update.  CTA c of
+// the group owns row blocks c, c + C, ... (C CTAs, rows_per_item rows per block) and a
 // contiguous slice of the elements.  Per step:
-//   1. every CTA loads u, computes its block's rows and row epilogue with the same functions as
-//      the other schedulers (gemv_rows.cuh) and writes the block's partial record;
-//   2. grid barrier;
+//   1. every CTA loads u, computes its blocks' rows and row epilogues with the same functions
+//      as the other schedulers (gemv_rows.cuh) and writes one partial record per block;
+//   2. group barrier;
 //   3. every CTA reduces all partial records in the same order (reduce_partials) and takes the
 //      same decision (decide) on its own copy of the lane state, so all copies stay equal;
 //      then it applies the element-wise update (lane_apply) to its slice;
-//   4. grid barrier (u complete).
+//   4. group barrier (u complete).
 // Alg. 2 steps (PABB) take one barrier: every CTA holds the whole x_k and x_{k-1} in shared
 // memory, and after the barrier computes the whole x_{k+1} = P(x_k - alpha g_k) itself from g_k
 // (every CTA's rows are in global memory by then), instead of updating a slice and exchanging
-// it.  g alternates between two global buffers by the parity of k (V_G, V_W), so a CTA that
-// writes g_{k+1} never overwrites the g_k another CTA may still be reading.  When the
-// subproblem ends, or the launch's budget does, the CTAs write x_k, x_{k-1} and u back.
-// The arithmetic is that of the lock-step scheduler with the same rows per item, so both give
-// the same bits.  The launch is cooperative (every CTA resident), and each barrier wait is
-// bounded: when it runs out the CTA sets the error flag and leaves, and the others leave at
-// their own next wait.  With one CTA (n <= 256) the barriers are the CTA's own.
+// it.  g alternates between two global buffers by the parity of k (V_G, V_W), and so do the
+// blocks' partial records (the lane holds two sets), so a CTA that has passed the step's barrier
+// and computes step k+1 never overwrites g_k or a record of step k that another CTA of the
+// group may still be reading.  On the sliced storage with one slice per block, a CTA computes
+// all of its slices in one pass (their loads in flight together).  When the subproblem ends,
+// or the launch's budget does, the CTAs write x_k, x_{k-1} and u back.  The arithmetic is that
+// of the lock-step scheduler with the same rows per item, so both give the same bits.  Every
+// group barrier wait is bounded: when it runs out the CTA sets the error flag and leaves, and
+// the others leave at their own next wait.  A group of one CTA needs no barrier.
 //
 // Lane vectors and partial records written by one CTA are read by others within the launch,
 // so this file is compiled with plain loads cached in L2 only (-dlcm=cg); Q keeps its
@@ -370,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
                         const int blk = my_sl[warp], row0 = blk * 32;
                         solo_inner_finish_warp(L, k, blk, row0, min(32, L.n - row0), sv + 32 * warp, P, su, sxp,
                                                gbuf[(k + 1) & 1], gbuf[k & 1], dmpv, tsumv,
-                                               one ? &s_part : L.part + blk, lane);
+                                               one ? &s_part : L.part + (size_t)(k & 1) * nblk + blk, lane);
                     }
                 }
             } else {
@@ -381,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
                     __syncthreads();
                     if (fast_step)
                         solo_inner_finish(L, k, blk, row0, rows, sv, P, su, sxp, gbuf[(k + 1) & 1], gbuf[k & 1], dmpv,
-                                          tsumv, one ? &s_part : L.part + blk);
+                                          tsumv, one ? &s_part : L.part + (size_t)(k & 1) * nblk + blk);
                     else item_finish(L, ph, k, blk, row0, rows, sv, P);
                     __syncthreads();
                 }
@@ -393,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
                 if (threadIdx.x == 0) R = s_part;
                 __syncthreads();
             } else {
-                reduce_partials(L.part, nblk, ph, R);
+                reduce_partials(fast_step ? L.part + (size_t)(k & 1) * nblk : L.part, nblk, ph, R);
             }
             if (threadIdx.x == 0) solo_decide(L, S, R, P, D);
             __syncthreads();
