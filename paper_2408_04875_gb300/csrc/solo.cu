@@ -232,20 +232,6 @@ __device__ __forceinline__ void solo_rows_sliced(const LaneDev& L, const int* sl
     }
 }
 
-// the scalar decision and the general element-wise update, out of line: they run on the rare
-// steps that are not plain projected steps, and inlined they would take registers from the
-// products' loop
-static __device__ __noinline__ void solo_decide(const LaneDev& L, LaneState& S, const Partial& R, const Params& P,
-                                                Decision& D)
-{
-    decide(L, S, R, P, D);
-}
-static __device__ __noinline__ void solo_apply(const LaneDev& L, const Params& P, const Decision& D, int ia, int ib,
-                                               int qa, int qb)
-{
-    solo_apply(L, P, D, ia, ib, qa, qb);
-}
-
 __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -399,7 +385,10 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
             } else {
                 reduce_partials(fast_step ? L.part + (size_t)(k & 1) * nblk : L.part, nblk, ph, R);
             }
-            if (threadIdx.x == 0) solo_decide(L, S, R, P, D);
+            // (decide and lane_apply stay inlined: built out of line in this file, with its plain
+            // loads cached in L2 only, their reads of the shared-memory state through generic
+            // references returned wrong values on the GPU)
+            if (threadIdx.x == 0) decide(L, S, R, P, D);
             __syncthreads();
             if (fast_step && (D.act & ~A_TRACE) == A_STEP_PABB && D.usrc == U_X) {
                 // x_{k+1} = P(x_k - alpha g_k) for every element, into the x_{k-1} buffer; the trace
@@ -438,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
                 su = reinterpret_cast<float*>(smem_raw);
                 sxp = su + L.ld;
             }
-            solo_apply(L, P, D, ia, ib, qa, qb);
+            lane_apply(L, P, D, ia, ib, qa, qb, (int)threadIdx.x, (int)blockDim.x);
             if (threadIdx.x == 0) {
                 S.updates += 1;
                 if (rank == 0 && (D.act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
