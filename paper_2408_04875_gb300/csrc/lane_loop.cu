@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kThreads, 4) lane_loop_kernel(LoopArgs A)
 cudaError_t prepare_lane_loop(int max_ld)
 {
     const size_t smem = (size_t)max_ld * sizeof(float);
-    if (smem <= 48 * 1024) return cudaSuccess;
+    // always opted in: the static shared memory counts against the 48 KB default as well
     return cudaFuncSetAttribute(lane_loop_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 

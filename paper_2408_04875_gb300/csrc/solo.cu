@@ -488,7 +488,7 @@ size_t solo_smem(int ld, bool one) { return (one ? 6 : 2) * (size_t)ld * sizeof(
 cudaError_t prepare_solo(int ld, bool one)
 {
     const size_t smem = solo_smem(ld, one);
-    if (smem <= 48 * 1024) return cudaSuccess;
+    // always opted in: the static shared memory counts against the 48 KB default as well
     return cudaFuncSetAttribute(solo_lane_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 

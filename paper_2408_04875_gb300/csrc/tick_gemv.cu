@@ -160,7 +160,7 @@ cudaError_t launch_penalized_vjp(const void* x, const void* g, const void* go, i
 template <typename T>
 static cudaError_t set_smem(size_t smem)
 {
-    if (smem <= 48 * 1024) return cudaSuccess;
+    // always opted in: the static shared memory counts against the 48 KB default as well
     return cudaFuncSetAttribute(phase_a_gemv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
