@@ -126,8 +126,11 @@ typedef struct {
                              /* largest whose step time is at most twice that of one  */
                              /* start wins (needs x_starts == NULL)                    */
     int precision;           /* UBQP_FP32 (default), UBQP_BF16X2_TC, UBQP_BF16_TC      */
-    int lobpcg_max_iter;     /* cap of the lambda_min eigen-solver: 64                 */
-    double lobpcg_tol;       /* relative change of the Ritz value to stop: 1e-4        */
+    int lobpcg_max_iter;     /* cap of the lambda_min eigen-solver: 256                */
+    double lobpcg_tol;       /* relative change of the Ritz value to stop: 1e-7 (the   */
+                             /* Ritz value is an upper bound of lambda_min, so a loose */
+                             /* stop overstates alpha); tensor-core lanes stop at      */
+                             /* max(lobpcg_tol, 1e-5), their products' resolution      */
     int jacobi_max_iter;     /* sweeps for x^0: 60                                      */
     int max_ticks_per_sync;  /* ticks launched between host checks: 64                 */
     int profile_kernels;     /* 1: time every phase-A launch with CUDA events; 2: also  */

@@ -136,7 +136,9 @@ static Params make_params(const ubqp_opts& o, int64_t* hist)
     P.tau_z = (float)o.tau_z;
     P.eps_hp_rel = (float)o.eps_hp_rel;
     P.lambda_floor_rel = (float)o.lambda_floor_rel;
-    P.lob_tol = (float)o.lobpcg_tol;
+    // the Ritz value approaches lambda_min from above, so a loose stop overstates alpha of
+    // Eq. (eq:alpha1); tensor-core lanes stop at their BF16 x2 products' resolution at most
+    P.lob_tol = (float)(o.precision == UBQP_FP32 ? o.lobpcg_tol : std::max(o.lobpcg_tol, 1e-5));
     P.jac_tol = 2e-7f;
     P.hist = hist;
     P.bytes = nullptr;
@@ -433,9 +435,13 @@ class Solver {
             solo_shape((int)insts[lanes[0].inst].n, o_.rows_per_item, num_sms_, &solo_grid_, &rb, &solo_nblk_);
         }
         if (solo_ && lanes.size() > 1) {
-            std::vector<int> nb(lanes.size());
-            for (size_t l = 0; l < lanes.size(); ++l) nb[l] = (int)((insts[lanes[l].inst].n + rb - 1) / rb);
-            const bool ok = plan_solo_groups(nb, max_ld, o_.gemv_kernel == 3);
+            solo_nb_.assign(lanes.size(), 0);
+            std::vector<int> ids(lanes.size());
+            for (size_t l = 0; l < lanes.size(); ++l) {
+                solo_nb_[l] = (int)((insts[lanes[l].inst].n + rb - 1) / rb);
+                ids[l] = (int)l;
+            }
+            const bool ok = plan_solo_groups(ids, max_ld, o_.gemv_kernel == 3);
             if (!ok && o_.gemv_kernel == 3) {
                 set_error("the lanes do not fit the single-lane kernel");
                 return UBQP_ENOTSUP;
@@ -518,9 +524,12 @@ class Solver {
         o_queue_ = ar_.reserve(2 * sizeof(int32_t));
         // single-lane kernel: err, active_after, then one barrier of kSoloBarStride words per group,
         // then the group tables
-        const size_t nsg = solo_ ? solo_gcta_.size() - 1 : 1;
+        // (room for the largest plan: a group per lane, or one per resident CTA)
+        const size_t nsg = solo_ ? (size_t)std::max<int64_t>((int64_t)lanes.size(), solo_capc_) : 1;
         o_solo_ = ar_.reserve((4 + nsg * kSoloBarStride) * sizeof(int32_t));
-        o_sologrp_ = solo_ ? ar_.reserve((solo_glanes_.size() + solo_gfirst_.size() + solo_gcta_.size()) * sizeof(int32_t)) : 0;
+        solo_gmax_ = nsg;
+        solo_nl_ = (int)lanes.size();
+        o_sologrp_ = solo_ ? ar_.reserve((lanes.size() + 2 * (nsg + 1)) * sizeof(int32_t)) : 0;
         o_lanes_ = ar_.reserve(lanes.size() * sizeof(LaneDev));
         o_linit_ = ar_.reserve(lanes.size() * sizeof(LaneInit));
         o_items_ = ar_.reserve((size_t)std::max<int64_t>(nitems, 1) * sizeof(int2));
@@ -570,14 +579,7 @@ class Solver {
         if (sym_) UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_symctr_), 0, lanes.size() * sizeof(unsigned int), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_queue_), 0, 2 * sizeof(int32_t), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_solo_), 0, (4 + nsg * kSoloBarStride) * sizeof(int32_t), stream_));
-        if (solo_) {
-            std::vector<int32_t> tab(solo_glanes_);
-            tab.insert(tab.end(), solo_gfirst_.begin(), solo_gfirst_.end());
-            tab.insert(tab.end(), solo_gcta_.begin(), solo_gcta_.end());
-            solo_tab_host_ = tab;
-            UBQP_CK(cudaMemcpyAsync(ar_.at<int32_t>(o_sologrp_), solo_tab_host_.data(), tab.size() * sizeof(int32_t),
-                                    cudaMemcpyHostToDevice, stream_));
-        }
+        if (solo_) UBQP_CK(upload_solo_plan());
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_valid_), 0, insts.size() * 4 * sizeof(float), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_nnz_), 0, insts.size() * sizeof(unsigned long long), stream_));
         UBQP_CK(cudaMemsetAsync(ar_.at<char>(o_scal_), 0, insts.size() * 4 * sizeof(float), stream_));
@@ -1241,14 +1243,17 @@ class Solver {
         SoloArgs sa;
         memset(&sa, 0, sizeof(sa));
         sa.lane = ar_.at<LaneDev>(o_lanes_);
-        const int32_t* tab = ar_.at<int32_t>(o_sologrp_);
-        sa.ngroups = (int)solo_gcta_.size() - 1;
-        sa.glanes = tab;
-        sa.gfirst = tab + solo_glanes_.size();
-        sa.gcta = sa.gfirst + solo_gfirst_.size();
+        auto set_plan = [&]() {
+            const int32_t* tab = ar_.at<int32_t>(o_sologrp_);
+            sa.ngroups = (int)solo_gcta_.size() - 1;
+            sa.glanes = tab;
+            sa.gfirst = tab + solo_nl_;
+            sa.gcta = sa.gfirst + solo_gmax_ + 1;
+            sa.grid = solo_gcta_.back();
+        };
+        set_plan();
         sa.rows_per_item = rows_per_item_;
         sa.budget = probe_ticks_ > 0 ? probe_ticks_ : (o_.lane_budget > 0 ? o_.lane_budget : 1024);
-        sa.grid = solo_gcta_.back();
         int32_t* ctl = ar_.at<int32_t>(o_solo_);
         sa.err = ctl;
         sa.active_after = ctl + 1;
@@ -1269,6 +1274,7 @@ class Solver {
         const int64_t cap = (int64_t)(o_.jacobi_max_iter + 2) +
                             (int64_t)(o_.max_outer + 1) * (int64_t)(o_.max_inner + o_.lobpcg_max_iter + 8);
         int64_t granted = 0;
+        int active_prev = nlanes_;
         for (;;) {
             UBQP_CK(cudaMemsetAsync(sa.active_after, 0, sizeof(int32_t), stream_));
             if (prof) UBQP_CK(cudaEventRecord(evA_[0], stream_));
@@ -1298,6 +1304,21 @@ class Solver {
                 set_error("step cap %lld exceeded", (long long)cap);
                 return UBQP_ETIMEOUT;
             }
+            if (nlanes_ > 1 && h_active_[1] < active_prev) {
+                // lanes have finished: the CTAs are shared out again over the lanes still running
+                // (a lane's arithmetic does not depend on its group, only on its blocks)
+                active_prev = h_active_[1];
+                std::vector<LaneState> st(nlanes_);
+                UBQP_CK(cudaMemcpy(st.data(), ar_.at<LaneState>(o_states_), st.size() * sizeof(LaneState),
+                                   cudaMemcpyDeviceToHost));
+                std::vector<int> ids;
+                for (int l = 0; l < nlanes_; ++l)
+                    if (st[l].phase != PH_DONE) ids.push_back(l);
+                if (!ids.empty() && plan_solo_groups(ids, max_ld_, true)) {
+                    UBQP_CK(upload_solo_plan());
+                    set_plan();
+                }
+            }
         }
         UBQP_CK(cudaEventRecord(ev1_, stream_));
         UBQP_CK(cudaStreamSynchronize(stream_));
@@ -1308,62 +1329,82 @@ class Solver {
         return UBQP_OK;
     }
 
-    // Groups of CTAs for several lanes on the single-lane kernel, largest lanes first.  With
-    // at most as many lanes as resident CTAs, every lane gets its own group of ceil(nblk / m)
-    // CTAs for the smallest m (blocks per CTA) at which all groups are resident together; the
+    // Groups of CTAs for the given lanes on the single-lane kernel, largest lanes first.  With at
+    // most as many lanes as resident CTAs, every lane gets its own group of ceil(nblk / m) CTAs
+    // for the smallest m (blocks per CTA) at which all groups are resident together; the
     // automatic choice takes it only for m <= kSoloMaxSl (all of a CTA's slices in one pass).
     // Otherwise (asked for explicitly) one-CTA groups share the lanes, each lane going to the
     // group with the fewest blocks so far.
-    bool plan_solo_groups(const std::vector<int>& nb, int max_ld, bool forced)
+    bool plan_solo_groups(const std::vector<int>& ids, int max_ld, bool forced)
     {
-        const size_t nl = nb.size();
-        solo_one_ok_ = 6 * (size_t)max_ld * sizeof(float) <= 48 * 1024;
-        if (prepare_solo(max_ld, solo_one_ok_) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
+        const size_t nl = ids.size();
+        if (solo_capc_ == 0) {
+            solo_one_ok_ = 6 * (size_t)max_ld * sizeof(float) <= 48 * 1024;
+            if (prepare_solo(max_ld, solo_one_ok_) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            const int per = solo_ctas_per_sm(max_ld, solo_one_ok_);
+            if (per < 1) return false;
+            solo_capc_ = (int64_t)per * num_sms_;
         }
-        const int per = solo_ctas_per_sm(max_ld, solo_one_ok_);
-        if (per < 1) return false;
-        const int64_t capc = (int64_t)per * num_sms_;
-        std::vector<int> order(nl);
-        for (size_t l = 0; l < nl; ++l) order[l] = (int)l;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nb[a] > nb[b]; });
-        solo_glanes_.clear();
-        solo_gfirst_.assign(1, 0);
-        solo_gcta_.assign(1, 0);
-        solo_max_lanes_ = 1;
-        const int maxnb = *std::max_element(nb.begin(), nb.end());
+        const int64_t capc = solo_capc_;
+        std::vector<int> order(ids);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return solo_nb_[a] > solo_nb_[b]; });
+        std::vector<int32_t> gl, gf(1, 0), gc(1, 0);
+        int max_lanes = 1;
+        int maxnb = 0;
+        for (int l : ids) maxnb = std::max(maxnb, solo_nb_[l]);
         if ((int64_t)nl <= capc) {
             int m = 1;
             for (; m <= maxnb; ++m) {
                 int64_t tot = 0;
-                for (int b : nb) tot += (b + m - 1) / m;
+                for (int l : ids) tot += (solo_nb_[l] + m - 1) / m;
                 if (tot <= capc) break;
             }
             if (!forced && m > kSoloMaxSl) return false;
             for (int l : order) {
-                solo_glanes_.push_back(l);
-                solo_gfirst_.push_back((int)solo_glanes_.size());
-                solo_gcta_.push_back(solo_gcta_.back() + (nb[l] + m - 1) / m);
+                gl.push_back(l);
+                gf.push_back((int)gl.size());
+                gc.push_back(gc.back() + (solo_nb_[l] + m - 1) / m);
             }
-            return true;
+        } else {
+            if (!forced) return false;
+            const int G = (int)capc;
+            std::vector<std::vector<int>> lanes_of(G);
+            std::vector<int64_t> load(G, 0);
+            for (int l : order) {
+                const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                lanes_of[g].push_back(l);
+                load[g] += solo_nb_[l];
+            }
+            for (int g = 0; g < G; ++g) {
+                for (int l : lanes_of[g]) gl.push_back(l);
+                gf.push_back((int)gl.size());
+                gc.push_back(g + 1);
+                max_lanes = std::max(max_lanes, (int)lanes_of[g].size());
+            }
         }
-        if (!forced) return false;
-        const int G = (int)capc;
-        std::vector<std::vector<int>> gl(G);
-        std::vector<int64_t> load(G, 0);
-        for (int l : order) {
-            const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-            gl[g].push_back(l);
-            load[g] += nb[l];
-        }
-        for (int g = 0; g < G; ++g) {
-            for (int l : gl[g]) solo_glanes_.push_back(l);
-            solo_gfirst_.push_back((int)solo_glanes_.size());
-            solo_gcta_.push_back(g + 1);
-            solo_max_lanes_ = std::max(solo_max_lanes_, (int)gl[g].size());
-        }
+        solo_glanes_ = gl;
+        solo_gfirst_ = gf;
+        solo_gcta_ = gc;
+        solo_max_lanes_ = std::max(solo_max_lanes_, max_lanes);
         return true;
+    }
+
+    // the group tables to the device (glanes, then gfirst and gcta at fixed offsets) and the
+    // groups' barrier counters to zero (a new plan regroups the CTAs)
+    cudaError_t upload_solo_plan()
+    {
+        const size_t G1 = solo_gmax_ + 1;
+        solo_tab_host_.assign((size_t)solo_nl_ + 2 * G1, 0);
+        std::copy(solo_glanes_.begin(), solo_glanes_.end(), solo_tab_host_.begin());
+        std::copy(solo_gfirst_.begin(), solo_gfirst_.end(), solo_tab_host_.begin() + solo_nl_);
+        std::copy(solo_gcta_.begin(), solo_gcta_.end(), solo_tab_host_.begin() + solo_nl_ + G1);
+        cudaError_t e = cudaMemcpyAsync(ar_.at<int32_t>(o_sologrp_), solo_tab_host_.data(),
+                                        solo_tab_host_.size() * sizeof(int32_t), cudaMemcpyHostToDevice, stream_);
+        if (e != cudaSuccess) return e;
+        return cudaMemsetAsync(ar_.at<int32_t>(o_solo_) + 4, 0, solo_gmax_ * kSoloBarStride * sizeof(int32_t), stream_);
     }
 
     // FP32 lanes on the persistent lane loop: each launch (seed + loop, one graph) lets
@@ -1645,8 +1686,12 @@ class Solver {
     int solo_grid_ = 0, solo_nblk_ = 0;
     size_t o_solo_ = 0, o_sologrp_ = 0;
     std::vector<int32_t> solo_glanes_, solo_gfirst_, solo_gcta_, solo_tab_host_;
+    std::vector<int> solo_nb_;   // row blocks per lane
     bool solo_one_ok_ = false;
     int solo_max_lanes_ = 1;
+    int64_t solo_capc_ = 0;      // CTAs resident at once
+    size_t solo_gmax_ = 1;       // groups the tables and barriers have room for
+    int solo_nl_ = 0;            // lanes (the tables' first part)
     int loop_grid_ = 0, loop_budget_ = 0;
     uint64_t loop_cap_ = 0;
     int nitems_ = 0;
@@ -1714,8 +1759,8 @@ void ubqp_opts_default(ubqp_opts* o)
     o->seed = 0;
     o->restarts = 1;
     o->precision = UBQP_FP32;
-    o->lobpcg_max_iter = 64;
-    o->lobpcg_tol = 1e-4;
+    o->lobpcg_max_iter = 256;
+    o->lobpcg_tol = 1e-7;
     o->jacobi_max_iter = 60;
     o->max_ticks_per_sync = 64;
     o->profile_kernels = 0;

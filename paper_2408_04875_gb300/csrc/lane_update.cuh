@@ -371,15 +371,24 @@ static __device__ void reduce_partials(const Partial* part, int nblk, int ph, Pa
         sh_f[warp] = a.f;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int t = 0; t < 12; ++t) R.s[t] = make_float2(0.f, 0.f);
-        for (int t = 0; t < 6; ++t) R.m[t] = 0.f;
-        R.f = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            for (int t = 0; t < 12; ++t) R.s[t] = csum_merge(R.s[t], sh_s[w][t]);
-            for (int t = 0; t < 6; ++t) R.m[t] = fmaxf(R.m[t], sh_m[w][t]);
-            if (ph == PH_EVAL) R.f += sh_f[w];
-        }
+    // the warps' results merged in warp order, one quantity per thread (threads 0-11 the sums,
+    // 12-17 the maxima, 18 the FP64 sum): each quantity sees the same operations in the same
+    // order as one thread merging them all would
+    const int nw = (int)(blockDim.x >> 5);
+    const int q = threadIdx.x;
+    if (q < 12) {
+        float2 v = make_float2(0.f, 0.f);
+        for (int w = 0; w < nw; ++w) v = csum_merge(v, sh_s[w][q]);
+        R.s[q] = v;
+    } else if (q < 18) {
+        float v = 0.f;
+        for (int w = 0; w < nw; ++w) v = fmaxf(v, sh_m[w][q - 12]);
+        R.m[q - 12] = v;
+    } else if (q == 18) {
+        double v = 0.0;
+        if (ph == PH_EVAL)
+            for (int w = 0; w < nw; ++w) v += sh_f[w];
+        R.f = v;
     }
     __syncthreads();
 }

@@ -40,38 +40,36 @@ __device__ __forceinline__ uint64_t solo_clock()
     return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
 {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
-// sense by generation: bar[0] counts arrivals, bar[1] is the generation released so far; the
-// nc CTAs of one group take part
-__device__ __forceinline__ bool solo_grid_sync(const SoloArgs& A, unsigned* bar, int nc, unsigned& gen, int* s_ok)
+// Group barrier on a monotonic 64-bit arrival counter: barrier number gen + 1 of the group is
+// complete when the counter reaches nc * (gen + 1).  A CTA adds its arrival without waiting for
+// the result and polls the counter (bounded); nobody resets anything, so a barrier costs one
+// round trip after the last arrival.
+__device__ __forceinline__ bool solo_grid_sync(const SoloArgs& A, unsigned long long* bar, int nc,
+                                               unsigned long long& gen, int* s_ok)
 {
     __syncthreads();
     if (nc == 1) return *s_ok != 0;
     if (threadIdx.x == 0) {
-        const unsigned target = gen + 1u;
+        const unsigned long long target = (gen + 1ull) * (unsigned long long)nc;
         __threadfence();
-        if (atomicAdd(&bar[0], 1u) == (unsigned)nc - 1u) {
-            bar[0] = 0u;
-            __threadfence();
-            atomicExch(&bar[1], target);
-        } else {
-            const uint64_t t0 = solo_clock();
-            while (ld_acquire_u32(&bar[1]) != target) {
-                if (solo_clock() - t0 > A.wait_ns) {
-                    atomicExch(A.err, 1);
-                    *s_ok = 0;
-                    break;
-                }
+        asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(bar) : "memory");
+        const uint64_t t0 = solo_clock();
+        while (ld_acquire_u64(bar) < target) {
+            if (solo_clock() - t0 > A.wait_ns) {
+                atomicExch(A.err, 1);
+                *s_ok = 0;
+                break;
             }
         }
-        __threadfence();
-        gen = target;
+        gen += 1ull;
     }
     __syncthreads();
     return *s_ok != 0;
@@ -194,7 +192,7 @@ __device__ __forceinline__ void solo_rows_sliced(const LaneDev& L, const int* sl
             maxg = max(maxg, ng[b]);
         }
     }
-#pragma unroll 2
+#pragma unroll 1
     for (int j = 0; j < maxg; ++j) {
         float q[kSoloMaxSl][4];
         int c[kSoloMaxSl][4];
@@ -232,6 +230,36 @@ __device__ __forceinline__ void solo_rows_sliced(const LaneDev& L, const int* sl
     }
 }
 
+// x_{k+1} = P(x_k - alpha g_k) over the whole padded vector (ld a multiple of 4), g_k from global
+// memory: 16-byte pieces, the loads of up to four pieces per thread issued before any use, so
+// the update costs one L2 round trip for ld <= 4096
+__device__ __forceinline__ void solo_project(const float* __restrict__ g, const float* x, float* y, int ld, float al)
+{
+    const float4* g4 = reinterpret_cast<const float4*>(g);
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    float4* y4 = reinterpret_cast<float4*>(y);
+    const int nq = ld >> 2;
+    for (int q0 = threadIdx.x; q0 < nq; q0 += 4 * kThreads) {
+        float4 gv[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            if (q0 + h * kThreads < nq) gv[h] = g4[q0 + h * kThreads];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int q = q0 + h * kThreads;
+            if (q < nq) {
+                const float4 xv = x4[q];
+                float4 r;
+                r.x = fminf(fmaxf(fmaf(-al, gv[h].x, xv.x), 0.f), 1.f);
+                r.y = fminf(fmaxf(fmaf(-al, gv[h].y, xv.y), 0.f), 1.f);
+                r.z = fminf(fmaxf(fmaf(-al, gv[h].z, xv.z), 0.f), 1.f);
+                r.w = fminf(fmaxf(fmaf(-al, gv[h].w, xv.w), 0.f), 1.f);
+                y4[q] = r;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -240,7 +268,7 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
     __shared__ Partial R;
     __shared__ Decision D;
     __shared__ int s_ok, s_g;
-    __shared__ unsigned s_gen0;
+    __shared__ unsigned long long s_gen0;
     __shared__ float2 s_share[kSoloMaxSl][kThreads];
     __shared__ Partial s_part;
     // the descriptor never changes: one copy in shared memory (this file's plain loads go to
@@ -268,12 +296,21 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
     const int c0 = A.gcta ? A.gcta[g] : 0;
     const int nc = A.gcta ? A.gcta[g + 1] - c0 : (int)gridDim.x;
     const int rank = (int)blockIdx.x - c0;
-    unsigned* bar = A.bar + (size_t)g * kSoloBarStride;
-    if (threadIdx.x == 0) s_gen0 = ld_acquire_u32(&bar[1]);
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(A.bar + (size_t)g * kSoloBarStride);
+    // barriers the group completed in earlier launches (a CTA that is already waiting at this
+    // launch's first barrier has added less than nc)
+    if (threadIdx.x == 0) s_gen0 = ld_acquire_u64(bar) / (unsigned long long)nc;
     __syncthreads();
-    unsigned gen = s_gen0;
-    Params P = A.P;
-    if (rank != 0) P.hist = nullptr;   // the subproblem histogram is counted once per lane
+    unsigned long long gen = s_gen0;
+    // the parameters in shared memory (read rarely; as a register copy they crowd the products'
+    // loop); the subproblem histogram is counted once per lane, by the group's first CTA
+    __shared__ Params sP;
+    if (threadIdx.x == 0) {
+        sP = A.P;
+        if (rank != 0) sP.hist = nullptr;
+    }
+    __syncthreads();
+    const Params& P = sP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int li0 = A.glanes ? A.gfirst[g] : 0, li1 = A.glanes ? A.gfirst[g + 1] : 1;
     int steps_left = A.budget;
@@ -399,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
                     for (int i = ia + (int)threadIdx.x; i < ib; i += kThreads)
                         L.trace_x[(size_t)D.trace_k * L.n + i] = su[i];
                 __syncthreads();
-                for (int i = threadIdx.x; i < L.ld; i += kThreads) sxp[i] = fminf(fmaxf(fmaf(-al, gk[i], su[i]), 0.f), 1.f);
+                solo_project(gk, su, sxp, L.ld, al);
                 __syncthreads();
                 float* t = su;
                 su = sxp;

@@ -443,7 +443,7 @@ struct SoloArgs {
     int32_t rows_per_item;
     int32_t budget;             // steps each group may take in this launch
     int32_t grid;
-    unsigned* bar;              // per group (stride kSoloBarStride): [0] arrivals, [1] generation
+    unsigned* bar;              // per group (stride kSoloBarStride words): a 64-bit arrival counter
     int32_t* err;               // set when a bounded wait runs out
     int32_t* active_after;      // lanes unfinished at the end of the launch (the caller zeroes it)
     unsigned long long wait_ns; // limit of one barrier wait
@@ -452,7 +452,7 @@ struct SoloArgs {
     Params P;
 };
 constexpr int kSoloBarStride = 32;   // unsigned per group barrier (128 bytes)
-constexpr int kSoloMaxSl = 6;        // 32-row slices a CTA computes in one pass
+constexpr int kSoloMaxSl = 5;        // 32-row slices a CTA computes in one pass
 void solo_shape(int n, int rows_per_item, int sms, int* grid, int* rb, int* nblk);
 size_t solo_smem(int ld, bool one);
 cudaError_t prepare_solo(int ld, bool one);

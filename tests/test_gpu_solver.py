@@ -249,8 +249,9 @@ PENALTY_CASES = [(50, 0, 0), (50, 0, 1), (250, 1, 0), (250, 1, 5), (250, 0, 3), 
 def test_penalty_step_lambda_min(ub):
     """The device eigen-solver (LOBPCG, FP32) against the oracle's dense lambda_min of
     Z^-1/2 Qbar_II Z^-1/2 (Sec. 3.4, Lemma 3.1) and the step alpha of Eq. (eq:alpha1):
-    - above the floor, with the default stopping rule (relative change 1e-4): lambda and alpha
-      within 2e-3; with the rule tightened to 1e-7 (300 iterations): within 2e-4;
+    - above the floor, with the default stopping rule (relative change of the Ritz value 1e-7,
+      at most 256 iterations): lambda and alpha within 2e-4; with the rule loosened to 1e-4
+      (64 iterations): within 2e-3;
     - below the floor (the oracle's lambda <= F = 4 delta rho): the device also takes the
       floor, alpha = eta F to FP32 rounding (no earlier floor steps in the probe).
     Every case prints its branch; at least two take the floor."""
@@ -260,15 +261,15 @@ def test_penalty_step_lambda_min(ub):
         Qp, bp, p, x = _state_at_outer_step(Q, b, I.perturbation(Q, seed), S)
         a_ref, m_ref, lam_ref, fb = O.penalty_step(Qp, bp, p, x)
         got = ub.penalty_probe(Qp, bp, p, x)
-        tight = ub.penalty_probe(Qp, bp, p, x, lobpcg_tol=1e-7, lobpcg_max_iter=300)
+        loose = ub.penalty_probe(Qp, bp, p, x, lobpcg_tol=1e-4, lobpcg_max_iter=64)
         print(f"n={n} seed={seed} s={S}: |I|={m_ref} oracle lambda={lam_ref:.6e} alpha={a_ref:.6e} floor={fb} | "
               f"gpu lambda={got['lambda']:.6e} alpha={got['alpha']:.6e} iters={got['iters']} | "
-              f"tight lambda={tight['lambda']:.6e} iters={tight['iters']}")
+              f"loose lambda={loose['lambda']:.6e} iters={loose['iters']}")
         assert got["n_active"] == m_ref
         if not fb:
-            assert abs(got["lambda"] - lam_ref) <= 2e-3 * abs(lam_ref), (n, seed, S)
-            assert abs(got["alpha"] - a_ref) <= 2e-3 * abs(a_ref), (n, seed, S)
-            assert abs(tight["lambda"] - lam_ref) <= 2e-4 * abs(lam_ref), (n, seed, S)
+            assert abs(got["lambda"] - lam_ref) <= 2e-4 * abs(lam_ref), (n, seed, S)
+            assert abs(got["alpha"] - a_ref) <= 2e-4 * abs(a_ref), (n, seed, S)
+            assert abs(loose["lambda"] - lam_ref) <= 2e-3 * abs(lam_ref), (n, seed, S)
         else:
             floors += 1
             assert abs(got["alpha"] - a_ref) <= 1e-5 * a_ref, (n, seed, S, got["alpha"], a_ref)
@@ -469,7 +470,7 @@ def test_single_lane_kernel_agrees_with_lockstep_bitwise(ub, n, seed, budget):
 @pytest.mark.parametrize("case", ["mixed", "mixed_budget", "many"])
 def test_lane_groups_agree_with_lockstep_bitwise(ub, case):
     """Several lanes on the single-lane kernel.  "mixed": every lane on its own group of CTAs
-    (sliced rows, 32-row items, a CTA computing up to six slices in one pass), also relaunched
+    (sliced rows, 32-row items, a CTA computing up to five slices in one pass), also relaunched
     every 7 steps; "many": more lanes than resident CTAs, so one-CTA groups run several lanes in
     turn (lanes of one slice keep Alg. 2 in shared memory).  Same objectives, points and step
     counts as the lock-step scheduler with the same items."""
