@@ -75,18 +75,16 @@ __device__ __forceinline__ bool solo_grid_sync(const SoloArgs& A, unsigned long 
     return *s_ok != 0;
 }
 
-// Alg. 2 row epilogue of the single-barrier step for row i (x_k and x_{k-1} from shared memory,
-// g_{k-1} from gold, g_k written to gnew): the arithmetic of row_epilogue (PH_INNER)
-__device__ __forceinline__ void solo_inner_row(const LaneDev& L, int k, int i, float v, const float* sx,
-                                               const float* sxp, const float* gold, float* gnew, const float* dmpv,
-                                               const float* tsumv, Acc& a)
+// Alg. 2 row epilogue of the single-barrier step for row i: x_k, x_{k-1}, d - p, d + b' and
+// g_{k-1} of the row given, g_k written to gnew[i] and returned; the arithmetic of row_epilogue
+// (PH_INNER)
+__device__ __forceinline__ float solo_inner_row(const LaneDev& L, int k, int i, float v, float x, float xp, float dmp,
+                                                float tsum, float gold, float* gnew, Acc& a)
 {
-    const float x = sx[i];
-    const float dmp = dmpv[i];
-    const float g = fmaf(dmp, 2.f * x - 1.f, fmaf(2.f, v, tsumv[i]));
+    const float g = fmaf(dmp, 2.f * x - 1.f, fmaf(2.f, v, tsum));
     if (k >= 1) {
-        const float sd = x - sxp[i];
-        const float y = g - gold[i];
+        const float sd = x - xp;
+        const float y = g - gold;
         csum_add(a.s[0], sd * sd);
         csum_add(a.s[1], sd * y);
         csum_add(a.s[2], y * y);
@@ -98,6 +96,7 @@ __device__ __forceinline__ void solo_inner_row(const LaneDev& L, int k, int i, f
     gnew[i] = g;
     const float viol = (x > 0.f && x < 1.f) ? fabsf(g) : (x <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
     a.m[0] = fmaxf(a.m[0], viol);
+    return g;
 }
 
 __device__ __forceinline__ unsigned long long solo_item_bytes(const LaneDev& L, int blk, int row0, int rows)
@@ -116,8 +115,10 @@ __device__ __forceinline__ void solo_inner_finish(const LaneDev& L, int k, int b
 {
     Acc a;
     a.zero();
-    if ((int)threadIdx.x < rows)
-        solo_inner_row(L, k, row0 + threadIdx.x, (float)sv[threadIdx.x], sx, sxp, gold, gnew, dmpv, tsumv, a);
+    if ((int)threadIdx.x < rows) {
+        const int i = row0 + threadIdx.x;
+        solo_inner_row(L, k, i, (float)sv[threadIdx.x], sx[i], sxp[i], dmpv[i], tsumv[i], k >= 1 ? gold[i] : 0.f, gnew, a);
+    }
     block_reduce_write<kWarps>(a, PH_INNER, out, false);
     if (P.bytes && threadIdx.x == 0) atomicAdd(P.bytes, solo_item_bytes(L, blk, row0, rows));
 }
@@ -133,7 +134,10 @@ __device__ __forceinline__ void solo_inner_finish_warp(const LaneDev& L, int k, 
 {
     Acc a;
     a.zero();
-    if (lane < rows) solo_inner_row(L, k, row0 + lane, (float)sv[lane], sx, sxp, gold, gnew, dmpv, tsumv, a);
+    if (lane < rows) {
+        const int i = row0 + lane;
+        solo_inner_row(L, k, i, (float)sv[lane], sx[i], sxp[i], dmpv[i], tsumv[i], k >= 1 ? gold[i] : 0.f, gnew, a);
+    }
 #pragma unroll
     for (int t = 0; t < 3; ++t) a.s[t] = csum_shfl_reduce(a.s[t]);
 #pragma unroll
@@ -155,6 +159,62 @@ __device__ __forceinline__ void solo_inner_finish_warp(const LaneDev& L, int k, 
         }
         *out = R;
         if (P.bytes) atomicAdd(P.bytes, solo_item_bytes(L, blk, row0, rows));
+    }
+}
+
+// Products of one 32-row slice (sliced storage) for sv[r]: the shares, operations and merge of
+// item_rows_sell with eight warps per slice, the loads sixteen entries of the share at a time
+// (a CTA with a single slice waits for fewer load rounds)
+__device__ __forceinline__ void solo_rows_one(const LaneDev& L, int sl, int rows, const float* su, double* sv,
+                                              float2* s_share1, int lane, int warp)
+{
+    const int64_t base = L.spo[sl];
+    const int width = (int)((L.spo[sl + 1] - base) >> 5);
+    const int k0 = width * warp / kWarps, k1 = width * (warp + 1) / kWarps;
+    const float* V = L.spv + base + lane + 32 * (int64_t)k0;
+    const uint16_t* C = L.spc + base + lane + 32 * (int64_t)k0;
+    const int ng = ((k1 - k0) >> 3) * 2;   // groups of four summed as FMA groups
+    float2 acc = make_float2(0.f, 0.f);
+    int j = 0;
+    for (; j + 4 <= ng; j += 4) {
+        float q[16];
+        int c[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            q[e] = __ldg(V + 32 * (4 * j + e));
+            c[e] = __ldg(C + 32 * (4 * j + e));
+        }
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float t = __fmul_rn(q[4 * h], su[c[4 * h]]);
+            t = fmaf(q[4 * h + 1], su[c[4 * h + 1]], t);
+            t = fmaf(q[4 * h + 2], su[c[4 * h + 2]], t);
+            t = fmaf(q[4 * h + 3], su[c[4 * h + 3]], t);
+            csum_add(acc, t);
+        }
+    }
+    for (; j < ng; ++j) {
+        float q[4];
+        int c[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            q[e] = __ldg(V + 32 * (4 * j + e));
+            c[e] = __ldg(C + 32 * (4 * j + e));
+        }
+        float t = __fmul_rn(q[0], su[c[0]]);
+        t = fmaf(q[1], su[c[1]], t);
+        t = fmaf(q[2], su[c[2]], t);
+        t = fmaf(q[3], su[c[3]], t);
+        csum_add(acc, t);
+    }
+    for (int k = 4 * ng; k < k1 - k0; ++k) csum_add(acc, __fmul_rn(__ldg(V + 32 * k), su[__ldg(C + 32 * k)]));
+    s_share1[lane * kWarps + warp] = acc;
+    __syncthreads();
+    if ((int)threadIdx.x < rows) {
+        const float2* sh = s_share1 + threadIdx.x * kWarps;
+        float2 a = sh[0];
+        for (int w = 1; w < kWarps; ++w) a = csum_merge(a, sh[w]);
+        sv[threadIdx.x] = (double)(a.x + a.y);
     }
 }
 
@@ -390,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
                 if (my_n > 0) {
                     // one slice: the lock-step kernel's own function (eight entries in flight per load
                     // round); several: all of them in one pass
-                    if (my_n == 1) item_rows_sell(L, my_sl[0] * 32, min(32, L.n - my_sl[0] * 32), su, sv, lane, warp);
+                    if (my_n == 1) solo_rows_one(L, my_sl[0], min(32, L.n - my_sl[0] * 32), su, sv, s_share[0], lane, warp);
                     else solo_rows_sliced(L, my_sl, my_n, su, sv, s_share, lane, warp);
                     __syncthreads();
                     if (warp < my_n) {
@@ -431,12 +491,11 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
                 // x_{k+1} = P(x_k - alpha g_k) for every element, into the x_{k-1} buffer; the trace
                 // (x_k) is written for this CTA's slice
                 const float al = D.alpha;
-                const float* gk = gbuf[k & 1];
                 if (D.act & A_TRACE)
                     for (int i = ia + (int)threadIdx.x; i < ib; i += kThreads)
                         L.trace_x[(size_t)D.trace_k * L.n + i] = su[i];
                 __syncthreads();
-                solo_project(gk, su, sxp, L.ld, al);
+                solo_project(gbuf[k & 1], su, sxp, L.ld, al);
                 __syncthreads();
                 float* t = su;
                 su = sxp;
