@@ -20,7 +20,7 @@
 // blocks' partial records (the lane holds two sets), so a CTA that has passed the step's barrier
 // and computes step k+1 never overwrites g_k or a record of step k that another CTA of the
 // group may still be reading.  On the sliced storage with one slice per block, a CTA computes
-// all of its slices in one pass (their loads in flight together).  When the subproblem ends,
+// its slices one after another, each with sixteen entries per thread in flight.  When the subproblem ends,
 // or the launch's budget does, the CTAs write x_k, x_{k-1} and u back.  The arithmetic is that
 // of the lock-step scheduler with the same rows per item, so both give the same bits.  Every
 // group barrier wait is bounded: when it runs out the CTA sets the error flag and leaves, and
@@ -218,78 +218,6 @@ __device__ __forceinline__ void solo_rows_one(const LaneDev& L, int sl, int rows
     }
 }
 
-// Products of ns (<= kSoloMaxSl) blocks of one 32-row slice each (sliced storage, 32 rows per
-// item), for sv[32 b + r].  Warp w takes share w of every slice -- the shares of item_rows_sell
-// with eight warps per slice -- and the slices' loads are interleaved, four entries of each
-// slice at a time, so a CTA that owns several slices keeps all of them in flight.  Per share
-// the operations are those of item_rows_sell (four products summed with FMAs and added to the
-// compensated sum, two such groups per eight entries, the last (width mod 8) entries one by
-// one), and the shares are merged in the same order, so the products have the same bits.
-__device__ __forceinline__ void solo_rows_sliced(const LaneDev& L, const int* sl, int ns, const float* su, double* sv,
-                                                 float2 (*s_share)[kThreads], int lane, int warp)
-{
-    float2 acc[kSoloMaxSl];
-    const float* V[kSoloMaxSl];
-    const uint16_t* Cc[kSoloMaxSl];
-    int ng[kSoloMaxSl], kt[kSoloMaxSl], ke[kSoloMaxSl];
-    int maxg = 0;
-#pragma unroll
-    for (int b = 0; b < kSoloMaxSl; ++b) {
-        acc[b] = make_float2(0.f, 0.f);
-        ng[b] = 0;
-        kt[b] = ke[b] = 0;
-        V[b] = nullptr;
-        Cc[b] = nullptr;
-        if (b < ns) {
-            const int64_t base = L.spo[sl[b]];
-            const int width = (int)((L.spo[sl[b] + 1] - base) >> 5);
-            const int k0 = width * warp / kWarps, k1 = width * (warp + 1) / kWarps;
-            V[b] = L.spv + base + lane + 32 * (int64_t)k0;
-            Cc[b] = L.spc + base + lane + 32 * (int64_t)k0;
-            ng[b] = ((k1 - k0) >> 3) * 2;
-            kt[b] = 4 * ng[b];
-            ke[b] = k1 - k0;
-            maxg = max(maxg, ng[b]);
-        }
-    }
-#pragma unroll 1
-    for (int j = 0; j < maxg; ++j) {
-        float q[kSoloMaxSl][4];
-        int c[kSoloMaxSl][4];
-#pragma unroll
-        for (int b = 0; b < kSoloMaxSl; ++b)
-            if (j < ng[b]) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    q[b][e] = __ldg(V[b] + 32 * (4 * j + e));
-                    c[b][e] = __ldg(Cc[b] + 32 * (4 * j + e));
-                }
-            }
-#pragma unroll
-        for (int b = 0; b < kSoloMaxSl; ++b)
-            if (j < ng[b]) {
-                float t = __fmul_rn(q[b][0], su[c[b][0]]);
-                t = fmaf(q[b][1], su[c[b][1]], t);
-                t = fmaf(q[b][2], su[c[b][2]], t);
-                t = fmaf(q[b][3], su[c[b][3]], t);
-                csum_add(acc[b], t);
-            }
-    }
-#pragma unroll
-    for (int b = 0; b < kSoloMaxSl; ++b)
-        if (b < ns) {
-            for (int k = kt[b]; k < ke[b]; ++k) csum_add(acc[b], __fmul_rn(__ldg(V[b] + 32 * k), su[__ldg(Cc[b] + 32 * k)]));
-            s_share[b][lane * kWarps + warp] = acc[b];
-        }
-    __syncthreads();
-    if ((int)threadIdx.x < 32 * ns) {
-        const float2* sh = s_share[threadIdx.x >> 5] + (threadIdx.x & 31) * kWarps;
-        float2 a = sh[0];
-        for (int w = 1; w < kWarps; ++w) a = csum_merge(a, sh[w]);
-        sv[threadIdx.x] = (double)(a.x + a.y);
-    }
-}
-
 // x_{k+1} = P(x_k - alpha g_k) over the whole padded vector (ld a multiple of 4), g_k from global
 // memory: 16-byte pieces, the loads of up to four pieces per thread issued before any use, so
 // the update costs one L2 round trip for ld <= 4096
@@ -418,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
             tsumv = stsum;
             __syncthreads();
         }
-        // this CTA's blocks (sliced storage, 32 rows per item: all of them in one pass)
+        // this CTA's blocks (sliced storage, 32 rows per item: all of them before one barrier)
         const bool multi = L.spv && A.rows_per_item == 32 && (nblk + nc - 1) / nc <= kSoloMaxSl;
         int my_sl[kSoloMaxSl];
         int my_n = 0;
@@ -448,10 +376,10 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
             // ---- phase A: this CTA's row block(s)
             if (fast_step && multi) {
                 if (my_n > 0) {
-                    // one slice: the lock-step kernel's own function (eight entries in flight per load
-                    // round); several: all of them in one pass
-                    if (my_n == 1) solo_rows_one(L, my_sl[0], min(32, L.n - my_sl[0] * 32), su, sv, s_share[0], lane, warp);
-                    else solo_rows_sliced(L, my_sl, my_n, su, sv, s_share, lane, warp);
+                    // the CTA's slices one after another, each into its own share buffer (measured
+                    // faster than interleaving the slices' loads, which cost registers)
+                    for (int b = 0; b < my_n; ++b)
+                        solo_rows_one(L, my_sl[b], min(32, L.n - my_sl[b] * 32), su, sv + 32 * b, s_share[b], lane, warp);
                     __syncthreads();
                     if (warp < my_n) {
                         const int blk = my_sl[warp], row0 = blk * 32;

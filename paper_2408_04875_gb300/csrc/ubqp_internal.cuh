@@ -452,7 +452,7 @@ struct SoloArgs {
     Params P;
 };
 constexpr int kSoloBarStride = 32;   // unsigned per group barrier (128 bytes)
-constexpr int kSoloMaxSl = 5;        // 32-row slices a CTA computes in one pass
+constexpr int kSoloMaxSl = 5;        // most 32-row slices a CTA of the lane groups computes per step
 void solo_shape(int n, int rows_per_item, int sms, int* grid, int* rb, int* nblk);
 size_t solo_smem(int ld, bool one);
 cudaError_t prepare_solo(int ld, bool one);

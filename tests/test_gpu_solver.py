@@ -470,7 +470,7 @@ def test_single_lane_kernel_agrees_with_lockstep_bitwise(ub, n, seed, budget):
 @pytest.mark.parametrize("case", ["mixed", "mixed_budget", "many"])
 def test_lane_groups_agree_with_lockstep_bitwise(ub, case):
     """Several lanes on the single-lane kernel.  "mixed": every lane on its own group of CTAs
-    (sliced rows, 32-row items, a CTA computing up to five slices in one pass), also relaunched
+    (sliced rows, 32-row items, a CTA computing up to five slices per step), also relaunched
     every 7 steps; "many": more lanes than resident CTAs, so one-CTA groups run several lanes in
     turn (lanes of one slice keep Alg. 2 in shared memory).  Same objectives, points and step
     counts as the lock-step scheduler with the same items."""
