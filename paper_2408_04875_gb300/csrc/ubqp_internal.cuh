@@ -225,6 +225,7 @@ __device__ __forceinline__ int phase_nsum(int ph)
     default: return 0;
     }
 }
+constexpr int phase_nsum_inner = 3, phase_nmax_inner = 4;   // phase_nsum / phase_nmax of PH_INNER
 __device__ __forceinline__ int phase_nmax(int ph)
 {
     switch (ph) {
