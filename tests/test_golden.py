@@ -64,3 +64,34 @@ def test_stored_optima_match_a_fresh_enumeration():
         if c["n"] == 16 or (c["n"] == 20 and c["seed"] == 0):
             f, _ = enumerate_min(Q, b)
             assert f == c["f_star"], c
+
+
+OBJ = os.path.join(os.path.dirname(__file__), "golden", "oracle_objectives.json")
+
+
+def test_stored_oracle_objectives_are_attained_by_their_points():
+    """Every stored oracle objective (tests/golden/oracle_objectives.json: the sweep law, its
+    rounding draws, the restart and ragged-batch laws) is the exact objective of the stored
+    binary point on the stored instance, recomputed here with a plain product; every sweep
+    instance has its draws (16, or 7 at n = 2500)."""
+    cases = json.load(open(OBJ))["cases"]
+    inst = {}
+    for key, c in sorted(cases.items()):
+        x = np.array([int(v) for v in c["x"]], dtype=np.float64)
+        fam, n, seed = c["family"], c["n"], c["seed"]
+        if (fam, n, seed) not in inst:
+            if fam in ("c2", "c2d"):
+                inst[(fam, n, seed)] = I.c2_instance(n, seed)
+            elif fam == "c4":
+                inst[(fam, n, seed)] = I.c4_instance(n, seed)
+            else:
+                inst[(fam, n, seed)] = I.c5_instance((n, c["density"], c["kind"], seed))
+        Q, b = inst[(fam, n, seed)]
+        assert x.shape == (n,), key
+        f = float(x @ Q @ x + (0.0 if b is None else b @ x))
+        assert f == c["f"], (key, f, c["f"])
+    for key, c in cases.items():
+        if c["family"] == "c2":
+            pre = f"c2d:n={c['n']}:seed={c['seed']}:start=0:draw="
+            draws = [k for k in cases if k.startswith(pre)]
+            assert len(draws) == (7 if c["n"] == 2500 else 16), (key, len(draws))
