@@ -146,11 +146,17 @@ typedef struct {
     int gemv_kernel;         /* scheduler of the FP32 lanes: 1 lock-step (one launch   */
                              /* per step of all lanes), 2 persistent lane loop (lanes  */
                              /* advance independently inside one launch), 3 single-lane */
-                             /* persistent kernel (one lane only: many steps per        */
-                             /* cooperative launch, two grid barriers per step); 0 = 3  */
-                             /* for one lane, 2 for 4 or more lanes, else 1 (and 1 when */
-                             /* profile_kernels == 2)                                   */
-    int lane_budget;         /* lane loop: steps per lane between host checks; 0 = 1024 */
+                             /* persistent kernel (many steps per cooperative launch;  */
+                             /* each lane on its own group of CTAs with a bounded group */
+                             /* barrier, one per PABB step; with more lanes than       */
+                             /* resident CTAs, one-CTA groups run several lanes in      */
+                             /* turn); 0 = 3 for one lane and for lanes on the sliced   */
+                             /* storage whose groups fit with at most 5 slices per CTA, */
+                             /* else 2 for 4 or more lanes, else 1 (1 when              */
+                             /* profile_kernels == 2); UBQP_ENOTSUP when 3 is asked for */
+                             /* and a lane's two vectors exceed 200 KiB of shared memory */
+    int lane_budget;         /* lane loop and single-lane kernel: steps per lane (per   */
+                             /* group) between host checks; 0 = 1024                    */
     int rows_per_item;       /* FP32 lanes: matrix rows per work item, 8..256 (a multiple */
                              /* of 8); 0 = chosen from the batch size                  */
     int sym_storage;         /* FP32 lanes on the lane loop: 1 = store only the upper   */

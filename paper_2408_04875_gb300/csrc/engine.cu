@@ -419,6 +419,10 @@ class Solver {
         // kSoloMaxSl slices each, all groups resident at once; or when the caller asks for it
         const bool solo_fit = !tc && !sym_ && 2 * (size_t)max_ld * sizeof(float) <= 200 * 1024;
         const bool solo_auto = o_.gemv_kernel == 0 && o_.profile_kernels < 2;
+        if (!tc && o_.gemv_kernel == 3 && !solo_fit) {
+            set_error("the single-lane kernel keeps two vectors of ld floats in shared memory: ld <= 25600");
+            return UBQP_ENOTSUP;
+        }
         solo_ = solo_fit && (o_.gemv_kernel == 3 || (solo_auto && (lanes.size() == 1 || sparse_)));
         if (solo_ && lanes.size() == 1 && sparse_) {
             // one CTA per 32-row slice (one CTA for up to 256 rows), unless the caller chose

@@ -376,6 +376,19 @@ static __device__ void reduce_partials(const Partial* part, int nblk, int ph, Pa
 #pragma unroll
             for (int t = 0; t < 4; ++t) a.m[t] = fmaxf(a.m[t], wm[t]);
         }
+    } else if (ph == PH_LOB) {
+        // the eigen-solver step's twelve Gram sums, level by level likewise
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float2 w[12];
+#pragma unroll
+            for (int t = 0; t < 12; ++t) {
+                w[t].x = __shfl_xor_sync(0xffffffffu, a.s[t].x, o);
+                w[t].y = __shfl_xor_sync(0xffffffffu, a.s[t].y, o);
+            }
+#pragma unroll
+            for (int t = 0; t < 12; ++t) a.s[t] = csum_merge(a.s[t], w[t]);
+        }
     } else {
 #pragma unroll
         for (int t = 0; t < 12; ++t)

@@ -6,12 +6,12 @@ minutes at n = 1000 and hours at n = 2500, so the values are stored, not recompu
 Bars: the returned objective is the exact f(x) of the returned point (integer data, so FP64
 evaluates it exactly), and the GPU's best objective is not worse than the oracle's by more
 than 0.1 % (the method is a heuristic minimiser: a better objective always passes).
-- plain sweep law (C2): n = 500 and 1000 (3 seeds each) and n = 2500 (seed 0), FP32 path,
+- plain sweep law (C2): n = 250, 500 and 1000 (3 seeds each) and n = 2500 (seed 0), FP32 path,
   the two storages of Q'_off the benchmark runs (sliced rows on the lane groups, the default
   at density 0.1; symmetric tiles on the lane loop, the default for dense data); the dense
-  rows (asked for explicitly) exact and within 1 % at these sizes, and within 0.1 % at
-  n = 250 (test_gpu_solver.py).  Which local optimum Alg. 3 ends in depends on rounding:
-  the oracle's own objective moves by 0.3-0.9 % at these sizes when the stored entries change
+  rows (asked for explicitly) exact and within 1 % of the oracle.  Which local optimum Alg. 3
+  ends in depends on rounding:
+  the oracle's own objective moves by up to 0.9 % at these sizes when the stored entries change
   by about one FP32 rounding (the "c2d" draws of the golden file: mu + 1e-7 Q E).  So the bar
   is 0.1 % of the oracle where its objective holds still under those draws, else no worse
   than the worst of the draws plus 0.1 % (the rule of the capped-subproblem test);
@@ -57,7 +57,7 @@ def _within(f, f_orc):
     return f - f_orc <= 1e-3 * abs(f_orc)
 
 
-C2_CASES = [(500, 0), (500, 1), (500, 2), (1000, 0), (1000, 1), (1000, 2), (2500, 0)]
+C2_CASES = [(250, 0), (250, 1), (250, 2), (500, 0), (500, 1), (500, 2), (1000, 0), (1000, 1), (1000, 2), (2500, 0)]
 
 
 def _draws(gold, n, s):
@@ -117,7 +117,8 @@ def test_c4_law_restart_batch_vs_oracle_best_of_same_starts(ub, gold):
 def test_c4_full_configuration_vs_oracle(ub, gold):
     """The benchmark's batched-restart configuration (n = 2500, 256 starts, BF16 x2 terms on
     the tensor cores): its best objective is exact and within 0.1 % of (or better than) the
-    oracle's run from x^0, and of the FP32 path's single start."""
+    oracle's run from x^0, and of the FP32 path's single start.  The FP32 single start itself
+    against the oracle under the sweep's sensitivity rule (the "c4d" draws)."""
     n, seed, R = 2500, 2, 256
     Q, _ = I.c4_instance(n, seed)
     mu = np.diag(np.diag(I.perturbation(Q, seed)))
@@ -129,7 +130,13 @@ def test_c4_full_configuration_vs_oracle(ub, gold):
     assert st["lanes"] == R
     assert f == O.objective(Q, None, x)
     assert _within(f, f_orc) and _within(f, f32), (f, f_orc, f32)
-    assert _within(f32, f_orc), (f32, f_orc)
+    pre = f"c4d:n={n}:seed={seed}:start=0:draw="
+    fs = [f_orc] + [v["f"] for k, v in gold.items() if k.startswith(pre)]
+    assert len(fs) == 8, f"{pre}* missing from {GOLD}: run tests/golden/make_oracle_objectives.py --only c4d"
+    strict = max(fs) - min(fs) <= 1e-3 * abs(f_orc)
+    print(f"C4 FP32 single start {f32}: oracle {f_orc}, draws {min(fs)} .. {max(fs)}, "
+          f"bar {'0.1 % of the oracle' if strict else 'worst draw + 0.1 %'}")
+    assert _within(f32, f_orc) if strict else _within(f32, max(fs)), (f32, f_orc, max(fs))
 
 
 def test_c5_law_instances_vs_oracle_best_of_same_starts(ub, gold):

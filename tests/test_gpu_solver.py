@@ -538,22 +538,6 @@ def test_restarts_keep_best_and_are_exact(ub):
         assert f8 <= fr + 1e-3 * abs(fr)
 
 
-@pytest.mark.parametrize("sched", ["dense", "sym", "sliced_loop"])
-@pytest.mark.parametrize("n", [250])
-def test_c2_sizes_within_tenth_percent(ub, n, sched):
-    Qs, mus = [], []
-    for seed in range(3):
-        Q, _ = I.c2_instance(n, seed)
-        Qs.append(Q)
-        mus.append(I.perturbation(Q, seed))
-    xs, obj, st = ub.solve_batched(Qs, None, mus, **SCHEDULES[sched])
-    assert st["storage"] == {"dense": 0, "sym": 1, "sliced_loop": 2}[sched]
-    for Q, mu, x, f in zip(Qs, mus, xs, obj):
-        assert f == O.objective(Q, None, x)
-        _, f_orc, _ = O.solve(Q, None, mu)
-        assert f - f_orc <= 1e-3 * abs(f_orc), (f, f_orc)
-
-
 @pytest.mark.parametrize("sched", ["dense", "sym", "sliced"])
 def test_full_size_c2_instance_properties(ub, sched):
     """n = 2500 (largest single-instance size; 210 symmetric tiles): exact objective of the
