@@ -31,10 +31,11 @@ sys.path.insert(0, ROOT)
 METRIC = "inner PG iters/s (batch×n) and time-to-oracle-objective vs plain FP32 path"
 UNIT = "lane-var-updates/s"
 GEMV_KERNELS = {1: "phase_a_gemv_kernel", 2: "lane_loop_kernel", 3: "solo_lane_kernel"}
-# DRAM bytes (read + write) per algorithmic byte of lane_loop_kernel, from the ncu capture of
-# one whole-solve launch of this workload (profiles/lane_loop_kernel_c2.md); the symmetric
-# storage is the default, the dense rows the alternative (sym_storage = 0)
-LOOP_TRAFFIC_RATIO = {1: 15.70 / 16.90, 0: 28.12 / 28.60}
+# DRAM bytes (read + write) per algorithmic byte of the dominant kernel, keyed by (scheduler,
+# storage), from an ncu capture of every launch of this workload's timed solve
+# (dram__bytes_read.sum + dram__bytes_write.sum over the launches against the bench's own
+# algorithmic bytes; profiles/solo_lane_kernel_c2.md); other combinations report null
+TRAFFIC_RATIO = {(3, 2): 0.7919 / 37.774}
 SIZES = (250, 500, 1000, 2500)
 SEEDS_PER_SIZE = 10
 WORKLOAD = ("plain PSDP sweep: n in {250,500,1000,2500} x 10 seeded instances, density 0.1, "
@@ -673,8 +674,9 @@ def run_gpu(args):
                        "ticks_per_step": stats[-1]["ticks"], "best_objectives_first3": [float(v) for v in objs[:3]]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None,
-                         "traffic": (LOOP_TRAFFIC_RATIO[stats[-1]["sym_storage"]] * pa_bytes / max(pa_n, 1)
-                                     if stats[-1]["gemv_kernel"] == 2 and pa_n else None),
+                         "traffic": (TRAFFIC_RATIO[(stats[-1]["gemv_kernel"], stats[-1]["storage"])] * alg_bytes
+                                     / max(pa_n, 1) if (stats[-1]["gemv_kernel"], stats[-1]["storage"]) in TRAFFIC_RATIO
+                                     and pa_n else None),
                          "kernel": GEMV_KERNELS.get(stats[-1]["gemv_kernel"], "?"), "launches": pa_n,
                          "avg_launch_us": pa_ms * 1e3 / max(pa_n, 1),
                          "algorithmic_bytes_per_launch": alg_bytes / max(pa_n, 1),

@@ -356,48 +356,7 @@ static __device__ void reduce_partials(const Partial* part, int nblk, int ph, Pa
     __shared__ float sh_m[kBWarps][6];
     __shared__ double sh_f[kBWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (ph == PH_INNER) {
-        // the inner step's three sums and four maxima: the same butterflies as below, level by
-        // level for all seven quantities, so that they overlap
-        static_assert(phase_nsum_inner == 3 && phase_nmax_inner == 4, "inner-step partials");
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float2 w[3];
-            float wm[4];
-#pragma unroll
-            for (int t = 0; t < 3; ++t) {
-                w[t].x = __shfl_xor_sync(0xffffffffu, a.s[t].x, o);
-                w[t].y = __shfl_xor_sync(0xffffffffu, a.s[t].y, o);
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) wm[t] = __shfl_xor_sync(0xffffffffu, a.m[t], o);
-#pragma unroll
-            for (int t = 0; t < 3; ++t) a.s[t] = csum_merge(a.s[t], w[t]);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) a.m[t] = fmaxf(a.m[t], wm[t]);
-        }
-    } else if (ph == PH_LOB) {
-        // the eigen-solver step's twelve Gram sums, level by level likewise
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            float2 w[12];
-#pragma unroll
-            for (int t = 0; t < 12; ++t) {
-                w[t].x = __shfl_xor_sync(0xffffffffu, a.s[t].x, o);
-                w[t].y = __shfl_xor_sync(0xffffffffu, a.s[t].y, o);
-            }
-#pragma unroll
-            for (int t = 0; t < 12; ++t) a.s[t] = csum_merge(a.s[t], w[t]);
-        }
-    } else {
-#pragma unroll
-        for (int t = 0; t < 12; ++t)
-            if (t < ns) a.s[t] = csum_shfl_reduce(a.s[t]);
-#pragma unroll
-        for (int t = 0; t < 6; ++t)
-            if (t < nm) a.m[t] = max_shfl_reduce(a.m[t]);
-        if (ph == PH_EVAL) a.f = dsum_shfl_reduce(a.f);
-    }
+    acc_shfl_reduce(a, ph, ph == PH_EVAL);
     if (lane == 0) {
 #pragma unroll
         for (int t = 0; t < 12; ++t) sh_s[warp][t] = a.s[t];

@@ -173,14 +173,7 @@ __device__ __forceinline__ void tmem_ld16_sum(uint32_t taddr, int bn, bool two, 
 // warp-level reduction of one lane's accumulator into its partial record (lane 0 writes)
 __device__ __forceinline__ void warp_reduce_write(Acc& a, int ph, Partial* out, bool has_f)
 {
-    const int ns = phase_nsum(ph), nm = phase_nmax(ph);
-#pragma unroll
-    for (int t = 0; t < 12; ++t)
-        if (t < ns) a.s[t] = csum_shfl_reduce(a.s[t]);
-#pragma unroll
-    for (int t = 0; t < 6; ++t)
-        if (t < nm) a.m[t] = max_shfl_reduce(a.m[t]);
-    if (has_f) a.f = dsum_shfl_reduce(a.f);
+    acc_shfl_reduce(a, ph, has_f);
     if ((threadIdx.x & 31) == 0) {
         Partial P;
 #pragma unroll

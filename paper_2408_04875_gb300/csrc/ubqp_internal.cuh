@@ -330,6 +330,57 @@ __device__ __forceinline__ void row_epilogue(const LaneDev& L, int ph, int k, in
 // ---------------------------------------------------------------------------------
 // Block-wide reduction of Acc into one Partial (blockDim.x threads, <= 1024)
 
+// The warp's butterfly reduction of a phase's sums (compensated), maxima and FP64 sum: for
+// every quantity the shuffles xor 16, 8, 4, 2, 1 in that order.  The inner step (3 sums, 4
+// maxima) and the eigen-solver step (12 sums, six at a time) run their quantities level by
+// level so that the chains overlap; the result of each quantity is the same either way.
+__device__ __forceinline__ void acc_shfl_reduce(Acc& a, int ph, bool has_f)
+{
+    static_assert(phase_nsum_inner == 3 && phase_nmax_inner == 4, "inner-step partials");
+    if (ph == PH_INNER) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float2 w[3];
+            float wm[4];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                w[t].x = __shfl_xor_sync(0xffffffffu, a.s[t].x, o);
+                w[t].y = __shfl_xor_sync(0xffffffffu, a.s[t].y, o);
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) wm[t] = __shfl_xor_sync(0xffffffffu, a.m[t], o);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) a.s[t] = csum_merge(a.s[t], w[t]);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) a.m[t] = fmaxf(a.m[t], wm[t]);
+        }
+    } else if (ph == PH_LOB) {
+        // six sums at a time (registers)
+#pragma unroll
+        for (int h = 0; h < 12; h += 6)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                float2 w[6];
+#pragma unroll
+                for (int t = 0; t < 6; ++t) {
+                    w[t].x = __shfl_xor_sync(0xffffffffu, a.s[h + t].x, o);
+                    w[t].y = __shfl_xor_sync(0xffffffffu, a.s[h + t].y, o);
+                }
+#pragma unroll
+                for (int t = 0; t < 6; ++t) a.s[h + t] = csum_merge(a.s[h + t], w[t]);
+            }
+    } else {
+        const int ns = phase_nsum(ph), nm = phase_nmax(ph);
+#pragma unroll
+        for (int t = 0; t < 12; ++t)
+            if (t < ns) a.s[t] = csum_shfl_reduce(a.s[t]);
+#pragma unroll
+        for (int t = 0; t < 6; ++t)
+            if (t < nm) a.m[t] = max_shfl_reduce(a.m[t]);
+    }
+    if (has_f) a.f = dsum_shfl_reduce(a.f);
+}
+
 template <int NWARP>
 __device__ __forceinline__ void block_reduce_write(Acc& a, int ph, Partial* out, bool has_f)
 {
@@ -338,6 +389,8 @@ __device__ __forceinline__ void block_reduce_write(Acc& a, int ph, Partial* out,
     __shared__ double sh_f[NWARP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ns = phase_nsum(ph), nm = phase_nmax(ph);
+    // (the plain per-quantity butterflies: this function is inlined at many call sites, and the
+    // level-by-level variants there made the single-lane kernel measurably slower)
 #pragma unroll
     for (int t = 0; t < 12; ++t)
         if (t < ns) a.s[t] = csum_shfl_reduce(a.s[t]);
