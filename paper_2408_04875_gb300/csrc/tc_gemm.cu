@@ -452,11 +452,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
                 s_k[c - c0] = st->k;
             }
         __syncthreads();
-        float* peers[8];
+        float* peers[kTcMaxCluster];
         for (int q = 0; q < S; ++q) peers[q] = cluster.map_shared_rank(P, q);
-        // lanes c0 + warp, + 8, ...: the next lane's gradient operands load while this one finishes
+        // lanes c0 + warp, + 8, ...: the next lane's gradient operands and its cluster partials
+        // (every rank's value of its four rows, summed in rank order when its turn comes) load
+        // while this one finishes
         InnerOps cur, nxt;
         bool cur_ok = false;
+        float pcur[kTcMaxCluster][4], pnxt[kTcMaxCluster][4];
+        auto load_parts = [&](int c, float (&pv)[kTcMaxCluster][4]) {
+#pragma unroll
+            for (int q = 0; q < kTcMaxCluster; ++q)
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (q < S) pv[q][j] = peers[q][c * 128 + lane + 32 * j];
+        };
+        if (c0 + warp < c1) load_parts(c0 + warp, pcur);
         if (!A.raw && c0 + warp < c1 && s_ph[c0 + warp - c0] == PH_INNER) {
             tc_inner_load(A.lanes[I.lane0 + nt * BN + c0 + warp], I.n, mt, lane, cur);
             cur_ok = true;
@@ -465,6 +476,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
             const int r = nt * BN + c;  // restart index within the instance
             const int cn = c + kTcThreads / 32;
             bool nxt_ok = false;
+            if (cn < c1) load_parts(cn, pnxt);
             if (!A.raw && cn < c1 && s_ph[cn - c0] == PH_INNER) {
                 tc_inner_load(A.lanes[I.lane0 + nt * BN + cn], I.n, mt, lane, nxt);
                 nxt_ok = true;
@@ -472,9 +484,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
             float vv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int row = lane + 32 * j;
                 float acc = 0.f;
-                for (int q = 0; q < S; ++q) acc += peers[q][c * 128 + row];
+#pragma unroll
+                for (int q = 0; q < kTcMaxCluster; ++q)
+                    if (q < S) acc += pcur[q][j];
                 vv[j] = acc;
             }
             if (A.raw) {
@@ -492,6 +505,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
             }
             cur = nxt;
             cur_ok = nxt_ok;
+#pragma unroll
+            for (int q = 0; q < kTcMaxCluster; ++q)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) pcur[q][j] = pnxt[q][j];
         }
     }
     cluster.sync();  // peers' shared memory stays alive until every CTA has read it

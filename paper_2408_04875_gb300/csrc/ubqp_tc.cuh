@@ -10,6 +10,7 @@ namespace ubqp {
 constexpr int kTcMaxStages = 4;
 constexpr int kTcpMaxStages = 8;   // persistent kernel
 constexpr int kTcMaxBn = 128;   // lanes per N tile (UMMA N)
+constexpr int kTcMaxCluster = 8;   // CTAs per split-K cluster
 
 // One instance of the batched path: BF16 Q_off (ld x ld) and its lanes' packed inputs
 // (hi and lo terms, R rows of ld), with the TMA descriptors of all three.
