@@ -211,6 +211,58 @@ __device__ __forceinline__ void tc_inner_load(const LaneDev& L, int n, int mt, i
     }
 }
 
+// the fields of a lane's descriptor that its gradient epilogue uses
+struct LaneEpi {
+    float* vec;
+    const float* tsum;
+    const float* oabs;
+    Partial* part;
+};
+
+__device__ __forceinline__ void tc_inner_load_p(const LaneEpi& E, int ld, int n, int mt, int lane, InnerOps& o)
+{
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = min(mt * 128 + lane + 32 * j, n - 1);
+        o.x[j] = E.vec[V_X * ld + i];
+        o.dmp[j] = E.vec[V_DMP * ld + i];
+        o.ts[j] = E.tsum[i];
+        o.xp[j] = E.vec[V_XPREV * ld + i];
+        o.go[j] = E.vec[V_G * ld + i];
+        o.oa[j] = E.oabs[i];
+    }
+}
+
+// Alg. 2 gradient for four rows from operands loaded beforehand
+__device__ __forceinline__ void tc_inner_finish_p(const LaneEpi& E, int ld, int n, int mt, int k, const float (&vv)[4],
+                                                  int lane, const InnerOps& o)
+{
+    float* vec = E.vec;
+    Acc a;
+    a.zero();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = mt * 128 + lane + 32 * j;
+        if (i >= n) continue;
+        const float g = fmaf(o.dmp[j], 2.f * o.x[j] - 1.f, fmaf(2.f, vv[j], o.ts[j]));
+        if (k >= 1) {
+            const float sj = o.x[j] - o.xp[j], yj = g - o.go[j];
+            csum_add(a.s[0], sj * sj);
+            csum_add(a.s[1], sj * yj);
+            csum_add(a.s[2], yj * yj);
+        } else {
+            a.m[1] = fmaxf(a.m[1], fabsf(o.dmp[j]));
+            a.m[2] = fmaxf(a.m[2], fabsf(vec[V_BBAR * ld + i]));
+            a.m[3] = fmaxf(a.m[3], o.oa[j] + fabsf(o.dmp[j]));
+        }
+        vec[V_G * ld + i] = g;
+        const float viol = (o.x[j] > 0.f && o.x[j] < 1.f) ? fabsf(g)
+                           : (o.x[j] <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
+        a.m[0] = fmaxf(a.m[0], viol);
+    }
+    warp_reduce_write(a, PH_INNER, E.part + mt, false);
+}
+
 // Alg. 2 gradient for four rows from operands loaded beforehand
 __device__ __forceinline__ void tc_inner_finish(const LaneDev& L, int n, int mt, int k, const float (&vv)[4],
                                                 int lane, const InnerOps& o)
@@ -355,6 +407,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
     __syncthreads();
     tc_fence_after();
 
+    // this CTA's share of the tile's lanes for the epilogue; warps 2.. (idle while warps 0 and 1
+    // run the main loop) read their states and descriptor fields now (neither changes during
+    // the launch)
+    __shared__ int s_ph[kTcMaxBn], s_k[kTcMaxBn];
+    __shared__ LaneEpi s_epi[kTcMaxBn];
+    const int nreal = min(BN, I.R - nt * BN);
+    const int c0 = (int)((int64_t)nreal * rank / S), c1 = (int)((int64_t)nreal * (rank + 1) / S);
+    if (!s_skip && !A.raw && warp >= 2)
+        for (int c = c0 + (int)threadIdx.x - 64; c < c1; c += kTcThreads - 64) {
+            const LaneDev& Ld = A.lanes[I.lane0 + nt * BN + c];
+            const LaneState* st = Ld.st;
+            s_ph[c - c0] = st->phase;
+            s_k[c - c0] = st->k;
+            s_epi[c - c0] = LaneEpi{Ld.vec, Ld.tsum, Ld.oabs, Ld.part};
+        }
+
     if (!s_skip && nkb > 0) {
         const uint32_t tmem = tmem_base;
         if (warp == 0 && lane == 0) {
@@ -430,10 +498,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
     cluster.sync();
 
     // ---- sum the cluster's partial accumulators and run the epilogue for this CTA's lanes
-    __shared__ int s_ph[kTcMaxBn], s_k[kTcMaxBn];
     if (!s_skip) {
-        const int nreal = min(BN, I.R - nt * BN);
-        const int c0 = (int)((int64_t)nreal * rank / S), c1 = (int)((int64_t)nreal * (rank + 1) / S);
         if (A.flops && rank == 0 && threadIdx.x == 0)   // 2 n flops per (row, lane), single term
             atomicAdd(A.flops, 2ull * (unsigned long long)min(128, I.n - mt * 128) * (unsigned long long)I.n *
                                    (unsigned long long)nreal);
@@ -445,12 +510,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
             if (mt == 0) by += 2ull * (two ? 2ull : 1ull) * (unsigned long long)nreal * (unsigned long long)I.n;
             atomicAdd(A.P.bytes, by);
         }
-        if (!A.raw)
-            for (int c = c0 + (int)threadIdx.x; c < c1; c += kTcThreads) {
-                const LaneState* st = A.lanes[I.lane0 + nt * BN + c].st;
-                s_ph[c - c0] = st->phase;
-                s_k[c - c0] = st->k;
-            }
         __syncthreads();
         float* peers[kTcMaxCluster];
         for (int q = 0; q < S; ++q) peers[q] = cluster.map_shared_rank(P, q);
@@ -469,7 +528,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
         };
         if (c0 + warp < c1) load_parts(c0 + warp, pcur);
         if (!A.raw && c0 + warp < c1 && s_ph[c0 + warp - c0] == PH_INNER) {
-            tc_inner_load(A.lanes[I.lane0 + nt * BN + c0 + warp], I.n, mt, lane, cur);
+            tc_inner_load_p(s_epi[warp], I.ld, I.n, mt, lane, cur);
             cur_ok = true;
         }
         for (int c = c0 + warp; c < c1; c += kTcThreads / 32) {
@@ -478,7 +537,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
             bool nxt_ok = false;
             if (cn < c1) load_parts(cn, pnxt);
             if (!A.raw && cn < c1 && s_ph[cn - c0] == PH_INNER) {
-                tc_inner_load(A.lanes[I.lane0 + nt * BN + cn], I.n, mt, lane, nxt);
+                tc_inner_load_p(s_epi[cn - c0], I.ld, I.n, mt, lane, nxt);
                 nxt_ok = true;
             }
             float vv[4];
@@ -499,7 +558,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
             } else {
                 const int ph = s_ph[c - c0];
                 if (ph != PH_DONE) {
-                    tc_lane_epilogue(A, I, mt, r, ph, s_k[c - c0], vv, lane, cur_ok ? &cur : nullptr);
+                    if (ph == PH_INNER && cur_ok) tc_inner_finish_p(s_epi[c - c0], I.ld, I.n, mt, s_k[c - c0], vv, lane, cur);
+                    else tc_lane_epilogue(A, I, mt, r, ph, s_k[c - c0], vv, lane, nullptr);
                     if (A.fuse) tc_fused_count(A, A.lanes[I.lane0 + r], s_upd[warp]);
                 }
             }
