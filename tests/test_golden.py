@@ -71,9 +71,10 @@ OBJ = os.path.join(os.path.dirname(__file__), "golden", "oracle_objectives.json"
 
 def test_stored_oracle_objectives_are_attained_by_their_points():
     """Every stored oracle objective (tests/golden/oracle_objectives.json: the sweep law, its
-    rounding draws, the restart and ragged-batch laws) is the exact objective of the stored
-    binary point on the stored instance, recomputed here with a plain product; every sweep
-    instance has its draws (16, or 7 at n = 2500)."""
+    rounding draws, the restart and ragged-batch laws and the restart instance's draws) is the
+    exact objective of the stored binary point on the stored instance, recomputed here with a
+    plain product; every sweep instance has its draws (16, or 7 at n = 2500), and so does the
+    n = 2500 restart instance (7)."""
     cases = json.load(open(OBJ))["cases"]
     inst = {}
     for key, c in sorted(cases.items()):
@@ -82,7 +83,7 @@ def test_stored_oracle_objectives_are_attained_by_their_points():
         if (fam, n, seed) not in inst:
             if fam in ("c2", "c2d"):
                 inst[(fam, n, seed)] = I.c2_instance(n, seed)
-            elif fam == "c4":
+            elif fam in ("c4", "c4d"):
                 inst[(fam, n, seed)] = I.c4_instance(n, seed)
             else:
                 inst[(fam, n, seed)] = I.c5_instance((n, c["density"], c["kind"], seed))
@@ -95,3 +96,4 @@ def test_stored_oracle_objectives_are_attained_by_their_points():
             pre = f"c2d:n={c['n']}:seed={c['seed']}:start=0:draw="
             draws = [k for k in cases if k.startswith(pre)]
             assert len(draws) == (7 if c["n"] == 2500 else 16), (key, len(draws))
+    assert len([k for k in cases if k.startswith("c4d:n=2500:seed=2:start=0:draw=")]) == 7
