@@ -128,15 +128,14 @@ __device__ __forceinline__ void solo_inner_finish(const LaneDev& L, int k, int b
 // warp order; the merges below are those, so the record has the same bits.
 __device__ __forceinline__ void solo_inner_finish_warp(const LaneDev& L, int k, int blk, int row0, int rows,
                                                        const double* sv, const Params& P, const float* sx,
-                                                       const float* sxp, const float* gold, float* gnew,
-                                                       const float* dmpv, const float* tsumv, Partial* out,
-                                                       int lane)
+                                                       const float* sxp, float* gnew, float dmp, float tsum,
+                                                       float gold, Partial* out, int lane)
 {
     Acc a;
     a.zero();
     if (lane < rows) {
         const int i = row0 + lane;
-        solo_inner_row(L, k, i, (float)sv[lane], sx[i], sxp[i], dmpv[i], tsumv[i], k >= 1 ? gold[i] : 0.f, gnew, a);
+        solo_inner_row(L, k, i, (float)sv[lane], sx[i], sxp[i], dmp, tsum, gold, gnew, a);
     }
 #pragma unroll
     for (int t = 0; t < 3; ++t) a.s[t] = csum_shfl_reduce(a.s[t]);
@@ -376,6 +375,15 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
             // ---- phase A: this CTA's row block(s)
             if (fast_step && multi) {
                 if (my_n > 0) {
+                    // the epilogue's per-row operands of warp w's block (d - p, d + b', g_{k-1}),
+                    // loaded before the products so that their round trip overlaps them
+                    float e_dmp = 0.f, e_ts = 0.f, e_g = 0.f;
+                    if (warp < my_n) {
+                        const int i = min(my_sl[warp] * 32 + lane, L.n - 1);
+                        e_dmp = dmpv[i];
+                        e_ts = tsumv[i];
+                        if (k >= 1) e_g = gbuf[(k + 1) & 1][i];
+                    }
                     // the CTA's slices one after another, each into its own share buffer (measured
                     // faster than interleaving the slices' loads, which cost registers)
                     for (int b = 0; b < my_n; ++b)
@@ -384,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 2) solo_lane_kernel(SoloArgs A)
                     if (warp < my_n) {
                         const int blk = my_sl[warp], row0 = blk * 32;
                         solo_inner_finish_warp(L, k, blk, row0, min(32, L.n - row0), sv + 32 * warp, P, su, sxp,
-                                               gbuf[(k + 1) & 1], gbuf[k & 1], dmpv, tsumv,
+                                               gbuf[k & 1], e_dmp, e_ts, e_g,
                                                one ? &s_part : L.part + (size_t)(k & 1) * nblk + blk, lane);
                     }
                 }

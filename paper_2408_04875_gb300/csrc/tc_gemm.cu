@@ -2,12 +2,12 @@
 // one contraction  D = Q_off * U^T  (Q_off in BF16, U = the lanes' inputs as BF16 hi + lo
 // rows, FP32 accumulation in TMEM), for the batched-restart and ragged paths.
 //
-// Tiling.  One CTA owns a 128-row M tile of one instance, an N tile of up to 256 lanes and
+// Tiling.  One CTA owns a 128-row M tile of one instance, an N tile of up to 128 lanes and
 // a slice of the K dimension; the S CTAs of a thread-block cluster share the M/N tile and
 // split K.  A (128 x 64) and B (N x 64) k-blocks arrive by TMA in 128-byte-swizzled tiles
-// into a shared-memory ring; one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32,
-// M = 128, K = 16 per instruction, the lo term as a second MMA into the same accumulator)
-// and tcgen05.commit frees ring slots.  The accumulators are then read with tcgen05.ld,
+// into a shared-memory ring, the lanes' hi rows and lo rows back to back; one thread issues
+// tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, K = 16 per instruction, N = twice the
+// tile's lanes, so one MMA covers both terms) and tcgen05.commit frees ring slots.  The accumulators are then read with tcgen05.ld,
 // parked in shared memory and summed across the cluster through distributed shared memory;
 // every CTA finishes a subset of the lanes with the per-row epilogue of the lane's phase.
 //
