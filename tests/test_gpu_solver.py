@@ -467,21 +467,24 @@ def test_single_lane_kernel_agrees_with_lockstep_bitwise(ub, n, seed, budget):
         assert s3["kernel_launches"] > 100
 
 
-@pytest.mark.parametrize("case", ["mixed", "mixed_budget", "many"])
+@pytest.mark.parametrize("case", ["mixed", "mixed_budget", "many", "large"])
 def test_lane_groups_agree_with_lockstep_bitwise(ub, case):
     """Several lanes on the single-lane kernel.  "mixed": every lane on its own group of CTAs
     (sliced rows, 32-row items, a CTA computing up to five slices per step), also relaunched
     every 7 steps; "many": more lanes than resident CTAs, so one-CTA groups run several lanes in
-    turn (lanes of one slice keep Alg. 2 in shared memory).  Same objectives, points and step
-    counts as the lock-step scheduler with the same items."""
+    turn (lanes of one slice keep Alg. 2 in shared memory); "large": n = 6000 next to smaller
+    lanes.  Same objectives, points and step counts as the lock-step scheduler with the same
+    items."""
     if case.startswith("mixed"):
         specs = [(2500, 11), (1000, 12), (500, 13), (250, 14), (37, 15), (1000, 16), (300, 17)]
+    elif case == "large":   # two vectors of 6016 floats per CTA in shared memory
+        specs = [(6000, 21), (1500, 22), (300, 23)]
     else:
         specs = [(20 + (i % 5) * 7, 100 + i) for i in range(400)]
     Qs = [I.random_ubqp(n, 0.1, s)[0] for n, s in specs]
     mus = [I.perturbation(Q, s) for Q, (n, s) in zip(Qs, specs)]
-    kw = dict(max_outer=4, rows_per_item=32, sparse_storage=1)
-    budget = {"mixed": 0, "mixed_budget": 7, "many": 5}[case]
+    kw = dict(max_outer=3 if case == "large" else 4, rows_per_item=32, sparse_storage=1)
+    budget = {"mixed": 0, "mixed_budget": 7, "many": 5, "large": 0}[case]
     x1, f1, s1 = ub.solve_batched(Qs, None, mus, gemv_kernel=1, **kw)
     x3, f3, s3 = ub.solve_batched(Qs, None, mus, gemv_kernel=3, lane_budget=budget, **kw)
     assert s1["gemv_kernel"] == 1 and s3["gemv_kernel"] == 3 and s3["storage"] == 2
