@@ -469,7 +469,7 @@ def run_c5(args):
             bh.append(b)
     gen_s = time.perf_counter() - t0
     max_outer = args.max_outer if args.max_outer is not None else 1000
-    kw = dict(precision=ub.BF16X2_TC, max_outer=max_outer)
+    kw = dict(precision=ub.BF16X2_TC, max_outer=max_outer, tc_cluster=args.tc_cluster)
     # first call: restart tuner + a full warm-up step
     _, _, st0 = ub.solve_batched(Qd, bd, None, restarts=args.c5_restarts, **kw)
     R = st0["restarts"]
@@ -719,7 +719,9 @@ def main():
     ap.add_argument("--no-c4", action="store_true",
                     help="skip the batched-restart time-to-objective comparison of the default line")
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "ppa", "sync", "single", "tcraw"])
-    ap.add_argument("--tc-cluster", type=int, default=0, help="tcraw: CTAs splitting K (0 = rule, -1 = persistent)")
+    ap.add_argument("--tc-cluster", type=int, default=0,
+                    help="CTAs splitting K: tcraw (0 = rule, -1 = persistent kernel); c5 (0 = measured "
+                         "tuner, 1 = no split: the persistent kernel when the tiles fill the GPU)")
     ap.add_argument("--c5-count", type=int, default=512, help="instances of the ragged batch")
     ap.add_argument("--c5-restarts", type=int, default=0, help="starts per instance (0 = restart tuner)")
     ap.add_argument("--restarts", type=int, default=256)
