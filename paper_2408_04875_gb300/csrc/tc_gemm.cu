@@ -34,8 +34,22 @@ namespace {
 
 constexpr int kTcThreads = 256;       // 8 warps: TMA producer, MMA issuer, then all 8 drain TMEM / run the epilogue
 constexpr uint64_t kWaitNs = 2000000000ull;
+// split-K kernel epilogue: each warp stages the operand rows of its next kEpiDepth lanes in
+// shared memory (slots of kEpiSlot floats = 7 vectors x 128 rows, after the accumulators)
+constexpr int kEpiDepth = 3;
+constexpr int kEpiSlot = 7 * 128;
+constexpr size_t kEpiSlotBytes = (size_t)(kTcThreads / 32) * kEpiDepth * kEpiSlot * 4;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// 16-byte asynchronous copy global -> shared (L2 only); groups complete in commit order
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ uint64_t globaltimer()
 {
@@ -188,30 +202,106 @@ __device__ __forceinline__ void warp_reduce_write(Acc& a, int ph, Partial* out, 
 }  // namespace
 
 // Per-row epilogue of one lane of an M tile (rows mt*128 + lane + 32 j, j < 4, values vv
-// from the contraction) and its partial record L.part[mt], by one warp.  The gradient step
-// (the common case) is split into loading its operands and finishing, so that the lane
-// loops can load the next lane's operands while they finish the current one.
-struct InnerOps {
-    float x[4], dmp[4], ts[4], xp[4], go[4], oa[4];
+// from the contraction) and its partial record part[mt], by one warp.  The gradient step and
+// the eigen-solver steps (the steps that dominate a solve) are split into loading their
+// operands and finishing, so that the lane loops can load the next lane's operands while they
+// finish the current one; the arithmetic and its order are those of row_epilogue.
+//   gradient step (Alg. 2, g^k): x, d - p, tsum, x_prev, g_{k-1}, |Q'_off| row sum;
+//   eigen-solver steps (Lemma 3.1, LOBPCG on Z^-1/2 Qbar_II Z^-1/2): D, w, d - p and, for an
+//   iteration, the basis vectors x, Ax, p, Ap.
+struct EpiOps {
+    float v[7][4];
 };
 
-__device__ __forceinline__ void tc_inner_load(const LaneDev& L, int n, int mt, int lane, InnerOps& o)
+__device__ __forceinline__ bool epi_ops_phase(int ph) { return ph == PH_INNER || ph == PH_LOB || ph == PH_LOB_INIT; }
+
+__device__ __forceinline__ void tc_epi_load(const float* vec, const float* tsum, const float* oabs, int ph, int ld, int n,
+                                            int mt, int lane, EpiOps& o)
 {
-    const float* vec = L.vec;
-    const int ld = L.ld;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int i = min(mt * 128 + lane + 32 * j, n - 1);
-        o.x[j] = vec[V_X * ld + i];
-        o.dmp[j] = vec[V_DMP * ld + i];
-        o.ts[j] = L.tsum[i];
-        o.xp[j] = vec[V_XPREV * ld + i];
-        o.go[j] = vec[V_G * ld + i];
-        o.oa[j] = L.oabs[i];
+        if (ph == PH_INNER) {
+            o.v[0][j] = vec[V_X * ld + i];
+            o.v[1][j] = vec[V_DMP * ld + i];
+            o.v[2][j] = tsum[i];
+            o.v[3][j] = vec[V_XPREV * ld + i];
+            o.v[4][j] = vec[V_G * ld + i];
+            o.v[5][j] = oabs[i];
+        } else {
+            o.v[0][j] = vec[V_D * ld + i];
+            o.v[1][j] = vec[(ph == PH_LOB_INIT ? V_LX : V_LW) * ld + i];
+            o.v[2][j] = vec[V_DMP * ld + i];
+            if (ph == PH_LOB) {
+                o.v[3][j] = vec[V_LX * ld + i];
+                o.v[4][j] = vec[V_LAX * ld + i];
+                o.v[5][j] = vec[V_LP * ld + i];
+                o.v[6][j] = vec[V_LAP * ld + i];
+            }
+        }
     }
 }
 
-// the fields of a lane's descriptor that its gradient epilogue uses
+__device__ __forceinline__ void tc_epi_finish(float* vec, Partial* part, int ph, int ld, int n, int mt, int k,
+                                              const float (&vv)[4], int lane, const EpiOps& o)
+{
+    Acc a;
+    a.zero();
+    if (ph == PH_INNER) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = mt * 128 + lane + 32 * j;
+            if (i >= n) continue;
+            const float x = o.v[0][j], dmp = o.v[1][j];
+            const float g = fmaf(dmp, 2.f * x - 1.f, fmaf(2.f, vv[j], o.v[2][j]));
+            if (k >= 1) {
+                const float sj = x - o.v[3][j], yj = g - o.v[4][j];
+                csum_add(a.s[0], sj * sj);
+                csum_add(a.s[1], sj * yj);
+                csum_add(a.s[2], yj * yj);
+            } else {
+                a.m[1] = fmaxf(a.m[1], fabsf(dmp));
+                a.m[2] = fmaxf(a.m[2], fabsf(vec[V_BBAR * ld + i]));
+                a.m[3] = fmaxf(a.m[3], o.v[5][j] + fabsf(dmp));
+            }
+            vec[V_G * ld + i] = g;
+            const float viol = (x > 0.f && x < 1.f) ? fabsf(g) : (x <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
+            a.m[0] = fmaxf(a.m[0], viol);
+        }
+        warp_reduce_write(a, PH_INNER, part + mt, false);
+        return;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = mt * 128 + lane + 32 * j;
+        if (i >= n) continue;
+        const float Dz = o.v[0][j], w = o.v[1][j];
+        float aw = 0.f;
+        if (Dz != 0.f) aw = Dz * fmaf(o.v[2][j], Dz * w, vv[j]);
+        vec[V_W * ld + i] = aw;
+        if (ph == PH_LOB_INIT) {
+            csum_add(a.s[0], w * aw);
+            csum_add(a.s[1], w * w);
+        } else {
+            const float x = o.v[3][j], ax = o.v[4][j], p = o.v[5][j], ap = o.v[6][j];
+            csum_add(a.s[0], x * ax);
+            csum_add(a.s[1], x * aw);
+            csum_add(a.s[2], x * ap);
+            csum_add(a.s[3], w * aw);
+            csum_add(a.s[4], w * ap);
+            csum_add(a.s[5], p * ap);
+            csum_add(a.s[6], x * x);
+            csum_add(a.s[7], x * w);
+            csum_add(a.s[8], x * p);
+            csum_add(a.s[9], w * w);
+            csum_add(a.s[10], w * p);
+            csum_add(a.s[11], p * p);
+        }
+    }
+    warp_reduce_write(a, ph, part + mt, false);
+}
+
+// the fields of a lane's descriptor that the prefetched epilogues use
 struct LaneEpi {
     float* vec;
     const float* tsum;
@@ -219,93 +309,59 @@ struct LaneEpi {
     Partial* part;
 };
 
-__device__ __forceinline__ void tc_inner_load_p(const LaneEpi& E, int ld, int n, int mt, int lane, InnerOps& o)
+// One warp copies a lane's operand rows ms .. ms + 127 (512 bytes per vector) into a slot:
+// gradient step x, d - p, x_prev, g_{k-1}; eigen-solver steps D, w, d - p (and x, Ax, p, Ap).
+__device__ __forceinline__ void tc_epi_copy(const float* vec, int ph, int ld, int ms, float* slot, int lane)
 {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = min(mt * 128 + lane + 32 * j, n - 1);
-        o.x[j] = E.vec[V_X * ld + i];
-        o.dmp[j] = E.vec[V_DMP * ld + i];
-        o.ts[j] = E.tsum[i];
-        o.xp[j] = E.vec[V_XPREV * ld + i];
-        o.go[j] = E.vec[V_G * ld + i];
-        o.oa[j] = E.oabs[i];
+    int vs[7];
+    int nv;
+    if (ph == PH_INNER) {
+        vs[0] = V_X; vs[1] = V_DMP; vs[2] = V_XPREV; vs[3] = V_G;
+        nv = 4;
+    } else {
+        vs[0] = V_D; vs[1] = ph == PH_LOB_INIT ? V_LX : V_LW; vs[2] = V_DMP;
+        vs[3] = V_LX; vs[4] = V_LAX; vs[5] = V_LP; vs[6] = V_LAP;
+        nv = ph == PH_LOB_INIT ? 3 : 7;
     }
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+        if (a < nv) cp_async16(slot + a * 128 + 4 * lane, vec + (size_t)vs[a] * ld + ms + 4 * lane);
 }
 
-// Alg. 2 gradient for four rows from operands loaded beforehand
-__device__ __forceinline__ void tc_inner_finish_p(const LaneEpi& E, int ld, int n, int mt, int k, const float (&vv)[4],
-                                                  int lane, const InnerOps& o)
+// the operands of rows lane + 32 j from a slot (and the instance's tsum and |Q'_off| row sums
+// of the tile, `inst`), in the order tc_epi_load gives them
+__device__ __forceinline__ void tc_epi_from_slot(const float* slot, const float (*inst)[128], int ph, int lane,
+                                                 EpiOps& o)
 {
-    float* vec = E.vec;
-    Acc a;
-    a.zero();
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int i = mt * 128 + lane + 32 * j;
-        if (i >= n) continue;
-        const float g = fmaf(o.dmp[j], 2.f * o.x[j] - 1.f, fmaf(2.f, vv[j], o.ts[j]));
-        if (k >= 1) {
-            const float sj = o.x[j] - o.xp[j], yj = g - o.go[j];
-            csum_add(a.s[0], sj * sj);
-            csum_add(a.s[1], sj * yj);
-            csum_add(a.s[2], yj * yj);
+        const int r = lane + 32 * j;
+        if (ph == PH_INNER) {
+            o.v[0][j] = slot[r];
+            o.v[1][j] = slot[128 + r];
+            o.v[2][j] = inst[0][r];
+            o.v[3][j] = slot[256 + r];
+            o.v[4][j] = slot[384 + r];
+            o.v[5][j] = inst[1][r];
         } else {
-            a.m[1] = fmaxf(a.m[1], fabsf(o.dmp[j]));
-            a.m[2] = fmaxf(a.m[2], fabsf(vec[V_BBAR * ld + i]));
-            a.m[3] = fmaxf(a.m[3], o.oa[j] + fabsf(o.dmp[j]));
-        }
-        vec[V_G * ld + i] = g;
-        const float viol = (o.x[j] > 0.f && o.x[j] < 1.f) ? fabsf(g)
-                           : (o.x[j] <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
-        a.m[0] = fmaxf(a.m[0], viol);
-    }
-    warp_reduce_write(a, PH_INNER, E.part + mt, false);
-}
-
-// Alg. 2 gradient for four rows from operands loaded beforehand
-__device__ __forceinline__ void tc_inner_finish(const LaneDev& L, int n, int mt, int k, const float (&vv)[4],
-                                                int lane, const InnerOps& o)
-{
-    float* vec = L.vec;
-    const int ld = L.ld;
-    Acc a;
-    a.zero();
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = mt * 128 + lane + 32 * j;
-        if (i >= n) continue;
-        const float g = fmaf(o.dmp[j], 2.f * o.x[j] - 1.f, fmaf(2.f, vv[j], o.ts[j]));
-        if (k >= 1) {
-            const float sj = o.x[j] - o.xp[j], yj = g - o.go[j];
-            csum_add(a.s[0], sj * sj);
-            csum_add(a.s[1], sj * yj);
-            csum_add(a.s[2], yj * yj);
-        } else {
-            a.m[1] = fmaxf(a.m[1], fabsf(o.dmp[j]));
-            a.m[2] = fmaxf(a.m[2], fabsf(vec[V_BBAR * ld + i]));
-            a.m[3] = fmaxf(a.m[3], o.oa[j] + fabsf(o.dmp[j]));
+            for (int a = 0; a < 7; ++a) o.v[a][j] = slot[a * 128 + r];
         }
-        vec[V_G * ld + i] = g;
-        const float viol = (o.x[j] > 0.f && o.x[j] < 1.f) ? fabsf(g)
-                           : (o.x[j] <= 0.f ? fmaxf(-g, 0.f) : fmaxf(g, 0.f));
-        a.m[0] = fmaxf(a.m[0], viol);
     }
-    warp_reduce_write(a, PH_INNER, L.part + mt, false);
 }
 
-// any phase; `pre` holds the gradient operands when the caller already loaded them
+// any phase; `pre` holds the operands when the caller already loaded them (epi_ops_phase)
 __device__ __forceinline__ void tc_lane_epilogue(const TcArgs& A, const TcInst& I, int mt, int r, int ph, int k,
-                                                 const float (&vv)[4], int lane, const InnerOps* pre)
+                                                 const float (&vv)[4], int lane, const EpiOps* pre)
 {
     const LaneDev& L = A.lanes[I.lane0 + r];
-    if (ph == PH_INNER) {
+    if (epi_ops_phase(ph)) {
         if (pre) {
-            tc_inner_finish(L, I.n, mt, k, vv, lane, *pre);
+            tc_epi_finish(L.vec, L.part, ph, I.ld, I.n, mt, k, vv, lane, *pre);
         } else {
-            InnerOps o;
-            tc_inner_load(L, I.n, mt, lane, o);
-            tc_inner_finish(L, I.n, mt, k, vv, lane, o);
+            EpiOps o;
+            tc_epi_load(L.vec, L.tsum, L.oabs, ph, I.ld, I.n, mt, lane, o);
+            tc_epi_finish(L.vec, L.part, ph, I.ld, I.n, mt, k, vv, lane, o);
         }
         return;
     }
@@ -412,6 +468,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
     // the launch)
     __shared__ int s_ph[kTcMaxBn], s_k[kTcMaxBn];
     __shared__ LaneEpi s_epi[kTcMaxBn];
+    __shared__ __align__(16) float s_rows[2][128];   // tsum and |Q'_off| row sums of the tile's rows
     const int nreal = min(BN, I.R - nt * BN);
     const int c0 = (int)((int64_t)nreal * rank / S), c1 = (int)((int64_t)nreal * (rank + 1) / S);
     if (!s_skip && !A.raw && warp >= 2)
@@ -474,6 +531,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
     if (threadIdx.x == 0) s_ok = (!s_skip && nkb > 0) ? (!s_fail && mbar_wait(&accum_bar, 0u)) : 1;
     __syncthreads();
     float* P = reinterpret_cast<float*>(ring);
+    // operand slots after the accumulators (the ring is free now); warp w's lanes are
+    // c0 + w + 8 t, lane t in slot t mod kEpiDepth, one copy group per lane
+    float* slots = P + 128 * A.max_bn + (size_t)warp * kEpiDepth * kEpiSlot;
+    auto epi_issue = [&](int t) {
+        const int c = c0 + warp + (kTcThreads / 32) * t;
+        if (!A.raw && c < c1 && epi_ops_phase(s_ph[c - c0]))
+            tc_epi_copy(s_epi[c - c0].vec, s_ph[c - c0], I.ld, mt * 128, slots + (t % kEpiDepth) * kEpiSlot, lane);
+        cp_async_commit();
+    };
+    if (!s_skip) {
+        if (!A.raw && threadIdx.x < 64) {
+            // the instance's vectors, through any of the CTA's lanes
+            if (c0 < c1) {
+                const float* src = threadIdx.x < 32 ? s_epi[0].tsum : s_epi[0].oabs;
+                cp_async16(&s_rows[threadIdx.x >> 5][4 * lane], src + mt * 128 + 4 * lane);
+            }
+            cp_async_commit();
+        }
+#pragma unroll
+        for (int t = 0; t < kEpiDepth; ++t) epi_issue(t);
+    }
     if (!s_skip) {
         const bool have = nkb > 0 && s_ok;
         if (nkb > 0) tc_fence_after();
@@ -510,14 +588,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
             if (mt == 0) by += 2ull * (two ? 2ull : 1ull) * (unsigned long long)nreal * (unsigned long long)I.n;
             atomicAdd(A.P.bytes, by);
         }
+        if (!A.raw && threadIdx.x < 64) cp_async_wait<kEpiDepth>();   // the tile's tsum and row sums
         __syncthreads();
         float* peers[kTcMaxCluster];
         for (int q = 0; q < S; ++q) peers[q] = cluster.map_shared_rank(P, q);
-        // lanes c0 + warp, + 8, ...: the next lane's gradient operands and its cluster partials
-        // (every rank's value of its four rows, summed in rank order when its turn comes) load
-        // while this one finishes
-        InnerOps cur, nxt;
-        bool cur_ok = false;
+        // lanes c0 + warp, + 8, ...: the operands come from the warp's slots; the next lane's
+        // cluster partials (every rank's value of its four rows, summed in rank order when its
+        // turn comes) load while this one finishes
         float pcur[kTcMaxCluster][4], pnxt[kTcMaxCluster][4];
         auto load_parts = [&](int c, float (&pv)[kTcMaxCluster][4]) {
 #pragma unroll
@@ -527,19 +604,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
                     if (q < S) pv[q][j] = peers[q][c * 128 + lane + 32 * j];
         };
         if (c0 + warp < c1) load_parts(c0 + warp, pcur);
-        if (!A.raw && c0 + warp < c1 && s_ph[c0 + warp - c0] == PH_INNER) {
-            tc_inner_load_p(s_epi[warp], I.ld, I.n, mt, lane, cur);
-            cur_ok = true;
-        }
-        for (int c = c0 + warp; c < c1; c += kTcThreads / 32) {
+        for (int c = c0 + warp, t = 0; c < c1; c += kTcThreads / 32, ++t) {
             const int r = nt * BN + c;  // restart index within the instance
             const int cn = c + kTcThreads / 32;
-            bool nxt_ok = false;
             if (cn < c1) load_parts(cn, pnxt);
-            if (!A.raw && cn < c1 && s_ph[cn - c0] == PH_INNER) {
-                tc_inner_load_p(s_epi[cn - c0], I.ld, I.n, mt, lane, nxt);
-                nxt_ok = true;
-            }
+            const int ph = A.raw ? PH_DONE : s_ph[c - c0];
+            const bool staged = epi_ops_phase(ph);
+            EpiOps cur;
+            cp_async_wait<kEpiDepth - 1>();   // lane t's group
+            __syncwarp();
+            if (staged) tc_epi_from_slot(slots + (t % kEpiDepth) * kEpiSlot, s_rows, ph, lane, cur);
+            __syncwarp();                     // the slot is read: it takes lane t + kEpiDepth
+            epi_issue(t + kEpiDepth);
             float vv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -555,22 +631,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tc_kernel(TcArgs A)
                     const int i = mt * 128 + lane + 32 * j;
                     if (i < I.n) A.raw[(size_t)r * I.ld + i] = vv[j];
                 }
-            } else {
-                const int ph = s_ph[c - c0];
-                if (ph != PH_DONE) {
-                    if (ph == PH_INNER && cur_ok) tc_inner_finish_p(s_epi[c - c0], I.ld, I.n, mt, s_k[c - c0], vv, lane, cur);
-                    else tc_lane_epilogue(A, I, mt, r, ph, s_k[c - c0], vv, lane, nullptr);
-                    if (A.fuse) tc_fused_count(A, A.lanes[I.lane0 + r], s_upd[warp]);
-                }
+            } else if (ph != PH_DONE) {
+                if (staged) tc_epi_finish(s_epi[c - c0].vec, s_epi[c - c0].part, ph, I.ld, I.n, mt, s_k[c - c0], vv, lane, cur);
+                else tc_lane_epilogue(A, I, mt, r, ph, s_k[c - c0], vv, lane, nullptr);
+                if (A.fuse) tc_fused_count(A, A.lanes[I.lane0 + r], s_upd[warp]);
             }
-            cur = nxt;
-            cur_ok = nxt_ok;
 #pragma unroll
             for (int q = 0; q < kTcMaxCluster; ++q)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) pcur[q][j] = pnxt[q][j];
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");   // no copy into this CTA's slots outstanding
     cluster.sync();  // peers' shared memory stays alive until every CTA has read it
 
     if (!s_skip) {
@@ -792,16 +864,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tcp_kernel(TcArgs A, in
                         atomicAdd(A.P.bytes, by);
                     }
                 }
-                // lanes warp - 2, + 6, ...: the next lane's gradient operands load while this one finishes
-                InnerOps cur, nxt;
+                // lanes warp - 2, + 6, ...: the next lane's operands load while this one finishes
+                EpiOps cur, nxt;
                 int cur_ph = PH_DONE, cur_k = 0;
-                auto lane_at = [&](int c, InnerOps& o, int& ph, int& k) {
+                auto lane_at = [&](int c, EpiOps& o, int& ph, int& k) {
                     ph = PH_DONE;
                     if (A.raw || c >= nreal) return;
-                    const LaneState* st = A.lanes[I.lane0 + T.nt * I.bn + c].st;
+                    const LaneDev& L = A.lanes[I.lane0 + T.nt * I.bn + c];
+                    const LaneState* st = L.st;
                     ph = st->phase;
                     k = st->k;
-                    if (ph == PH_INNER) tc_inner_load(A.lanes[I.lane0 + T.nt * I.bn + c], I.n, T.mt, lane, o);
+                    if (epi_ops_phase(ph)) tc_epi_load(L.vec, L.tsum, L.oabs, ph, I.ld, I.n, T.mt, lane, o);
                 };
                 lane_at(warp - 2, cur, cur_ph, cur_k);
                 for (int c = warp - 2; c < nreal; c += 6) {
@@ -818,7 +891,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) phase_a_tcp_kernel(TcArgs A, in
                             if (i < I.n) A.raw[(size_t)r * I.ld + i] = vv[q];
                         }
                     } else if (cur_ph != PH_DONE) {
-                        tc_lane_epilogue(A, I, T.mt, r, cur_ph, cur_k, vv, lane, cur_ph == PH_INNER ? &cur : nullptr);
+                        tc_lane_epilogue(A, I, T.mt, r, cur_ph, cur_k, vv, lane, epi_ops_phase(cur_ph) ? &cur : nullptr);
                         if (A.fuse) tc_fused_count(A, A.lanes[I.lane0 + r], s_upd[warp]);
                     }
                     cur = nxt;
@@ -856,7 +929,8 @@ static int pow2_at_least(int v)
 size_t tc_smem_bytes(int bn, bool two, int stages)
 {
     const size_t stage = 128 * 128 + (size_t)bn * 128 * (two ? 2 : 1);
-    const size_t ring = std::max(stage * stages, (size_t)bn * 128 * 4);  // reused for the accumulators
+    // reused for the accumulators and the epilogue's operand slots
+    const size_t ring = std::max(stage * stages, (size_t)bn * 128 * 4 + kEpiSlotBytes);
     return ring + 1024;  // alignment slack
 }
 
