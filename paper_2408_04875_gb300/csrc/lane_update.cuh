@@ -57,34 +57,49 @@ __device__ __forceinline__ float start_component(int i)
 
 // smallest eigenpair of a symmetric k x k matrix (k <= 3) by cyclic Jacobi rotations.
 // FP32 throughout: FP64 runs at a small fraction of the FP32 rate on this part, and the
-// preconditioned basis keeps the 3 x 3 Gram matrices well scaled.
-static __device__ void small_sym_eig_min(int k, float M[3][3], float& lam, float v[3])
+// preconditioned basis keeps the 3 x 3 Gram matrices well scaled.  Every loop runs over the
+// full 3 x 3 with the entries outside k x k masked, so that all indices are compile-time
+// constants and the matrices stay in registers (the operations and their order are those
+// of the k x k loops).
+__device__ __forceinline__ void small_sym_eig_min(int k, float (&M)[3][3], float& lam, float (&v)[3])
 {
     float V[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
     for (int sweep = 0; sweep < 8; ++sweep) {
         float off = 0.f, dia = 0.f;
-        for (int p = 0; p < k; ++p) {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            if (p >= k) break;
             dia += M[p][p] * M[p][p];
-            for (int q = p + 1; q < k; ++q) off += M[p][q] * M[p][q];
+#pragma unroll
+            for (int q = p + 1; q < 3; ++q)
+                if (q < k) off += M[p][q] * M[p][q];
         }
         if (off <= 1e-14f * dia) break;
-        for (int p = 0; p < k; ++p)
-            for (int q = p + 1; q < k; ++q) {
-                if (M[p][q] == 0.f) continue;
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = p + 1; q < 3; ++q) {
+                if (q >= k || M[p][q] == 0.f) continue;
                 float theta = (M[q][q] - M[p][p]) / (2.f * M[p][q]);
                 float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
                 float c = rsqrtf(t * t + 1.f), sn = t * c;
-                for (int r = 0; r < k; ++r) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    if (r >= k) break;
                     float mrp = M[r][p], mrq = M[r][q];
                     M[r][p] = c * mrp - sn * mrq;
                     M[r][q] = sn * mrp + c * mrq;
                 }
-                for (int r = 0; r < k; ++r) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    if (r >= k) break;
                     float mpr = M[p][r], mqr = M[q][r];
                     M[p][r] = c * mpr - sn * mqr;
                     M[q][r] = sn * mpr + c * mqr;
                 }
-                for (int r = 0; r < k; ++r) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    if (r >= k) break;
                     float vrp = V[r][p], vrq = V[r][q];
                     V[r][p] = c * vrp - sn * vrq;
                     V[r][q] = sn * vrp + c * vrq;
@@ -92,15 +107,19 @@ static __device__ void small_sym_eig_min(int k, float M[3][3], float& lam, float
             }
     }
     int j = 0;
-    for (int t = 1; t < k; ++t)
-        if (M[t][t] < M[j][j]) j = t;
-    lam = M[j][j];
-    for (int r = 0; r < 3; ++r) v[r] = r < k ? V[r][j] : 0.f;
+    lam = M[0][0];
+    if (k > 1 && M[1][1] < lam) { j = 1; lam = M[1][1]; }
+    if (k > 2 && M[2][2] < lam) { j = 2; lam = M[2][2]; }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) v[r] = r < k ? (j == 0 ? V[r][0] : (j == 1 ? V[r][1] : V[r][2])) : 0.f;
 }
 
 // Rayleigh-Ritz on span{x, w, p} (p only when has_p), FP32.  Returns false on breakdown.
 // Gram entries: ga = (xAx, xAw, xAp, wAw, wAp, pAp), gb = (xx, xw, xp, ww, wp, pp).
-static __device__ bool rayleigh_ritz(const float ga[6], const float gb[6], bool has_p, float& lam, float c[3])
+// Loops as in small_sym_eig_min: full 3 x 3, masked to k x k.  Not inlined: its registers are
+// needed only for the eigen-solver's decision, not in the kernels' hot loops.
+static __device__ __noinline__ bool rayleigh_ritz(const float (&ga)[6], const float (&gb)[6], bool has_p, float& lam,
+                                              float (&c)[3])
 {
     const float A[3][3] = {{ga[0], ga[1], ga[2]}, {ga[1], ga[3], ga[4]}, {ga[2], ga[4], ga[5]}};
     const float B[3][3] = {{gb[0], gb[1], gb[2]}, {gb[1], gb[3], gb[4]}, {gb[2], gb[4], gb[5]}};
@@ -110,13 +129,17 @@ static __device__ bool rayleigh_ritz(const float ga[6], const float gb[6], bool 
         if (k < 2) return false;
         float sc[3] = {0.f, 0.f, 0.f};
         bool bad = false;
-        for (int t = 0; t < k; ++t) {
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t >= k) break;
             if (!(B[t][t] > 0.f)) { bad = true; break; }
             sc[t] = rsqrtf(B[t][t]);
         }
         if (bad) { k -= 1; continue; }
         float As[3][3], Bs[3][3];
+#pragma unroll
         for (int r = 0; r < 3; ++r)
+#pragma unroll
             for (int q = 0; q < 3; ++q) {
                 As[r][q] = (r < k && q < k) ? A[r][q] * sc[r] * sc[q] : 0.f;
                 Bs[r][q] = (r < k && q < k) ? B[r][q] * sc[r] * sc[q] : 0.f;
@@ -124,41 +147,66 @@ static __device__ bool rayleigh_ritz(const float ga[6], const float gb[6], bool 
         // Cholesky Bs = L L^T; a pivot below 1e-3 (unit diagonal) means a nearly dependent
         // basis in FP32: drop the last direction and retry
         float Lc[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        for (int j = 0; j < k && !bad; ++j) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j >= k || bad) break;
             float sd = Bs[j][j];
+#pragma unroll
             for (int t = 0; t < j; ++t) sd -= Lc[j][t] * Lc[j][t];
             if (!(sd > 1e-3f)) { bad = true; break; }
             Lc[j][j] = sqrtf(sd);
-            for (int i = j + 1; i < k; ++i) {
+#pragma unroll
+            for (int i = j + 1; i < 3; ++i) {
+                if (i >= k) break;
                 float u = Bs[i][j];
+#pragma unroll
                 for (int t = 0; t < j; ++t) u -= Lc[i][t] * Lc[j][t];
                 Lc[i][j] = u / Lc[j][j];
             }
         }
         if (bad) { k -= 1; continue; }
         float Li[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        for (int j = 0; j < k; ++j) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j >= k) break;
             Li[j][j] = 1.f / Lc[j][j];
-            for (int i = j + 1; i < k; ++i) {
+#pragma unroll
+            for (int i = j + 1; i < 3; ++i) {
+                if (i >= k) break;
                 float u = 0.f;
+#pragma unroll
                 for (int t = j; t < i; ++t) u -= Lc[i][t] * Li[t][j];
                 Li[i][j] = u / Lc[i][i];
             }
         }
         float M[3][3];
+#pragma unroll
         for (int r = 0; r < 3; ++r)
+#pragma unroll
             for (int q = 0; q < 3; ++q) {
                 float u = 0.f;
                 if (r < k && q < k)
-                    for (int a = 0; a < k; ++a)
-                        for (int b = 0; b < k; ++b) u += Li[r][a] * As[a][b] * Li[q][b];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        if (a >= k) break;
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            if (b >= k) break;
+                            u += Li[r][a] * As[a][b] * Li[q][b];
+                        }
+                    }
                 M[r][q] = u;
             }
         float v[3];
         small_sym_eig_min(k, M, lam, v);
+#pragma unroll
         for (int r = 0; r < 3; ++r) {  // c = sc * L^-T v
             float u = 0.f;
-            for (int a = r; a < k; ++a) u += Li[a][r] * v[a];
+#pragma unroll
+            for (int a = r; a < 3; ++a) {
+                if (a >= k) break;
+                u += Li[a][r] * v[a];
+            }
             c[r] = r < k ? u * sc[r] : 0.f;
         }
         return isfinite(lam);
@@ -337,13 +385,14 @@ static __device__ void decide(const LaneDev& L, LaneState& S, const Partial& R, 
 // The reduction of a lane's phase-A partials (all threads of the CTA; the result is in R when
 // the call returns).  Thread t merges partials t, t + blockDim.x, ... in order, then the warps
 // and the CTA's warps in order: the result depends only on the partials and the CTA size.
-static __device__ void reduce_partials(const Partial* part, int nblk, int ph, Partial& R)
+// `first`: this thread's first partial (part[threadIdx.x]), when the caller loaded it already.
+static __device__ void reduce_partials(const Partial* part, int nblk, int ph, Partial& R,
+                                       const Partial* first = nullptr)
 {
     Acc a;
     a.zero();
     const int ns = phase_nsum(ph), nm = phase_nmax(ph);
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-        const Partial& p = part[b];
+    auto merge = [&](const Partial& p) {
 #pragma unroll
         for (int t = 0; t < 12; ++t)
             if (t < ns) a.s[t] = csum_merge(a.s[t], p.s[t]);
@@ -351,7 +400,13 @@ static __device__ void reduce_partials(const Partial* part, int nblk, int ph, Pa
         for (int t = 0; t < 6; ++t)
             if (t < nm) a.m[t] = fmaxf(a.m[t], p.m[t]);
         a.f += p.f;
+    };
+    int b0 = threadIdx.x;
+    if (first && b0 < nblk) {
+        merge(*first);
+        b0 += blockDim.x;
     }
+    for (int b = b0; b < nblk; b += blockDim.x) merge(part[b]);
     __shared__ float2 sh_s[kBWarps][12];
     __shared__ float sh_m[kBWarps][6];
     __shared__ double sh_f[kBWarps];
@@ -387,6 +442,30 @@ static __device__ void reduce_partials(const Partial* part, int nblk, int ph, Pa
     __syncthreads();
 }
 
+// One 16-byte group q of the projected step: x_prev <- x, x <- P(x - alpha g), u <- x.
+__device__ __forceinline__ void pabb_group(const LaneDev& L, float* vec, int ld, float al, int q, float4 x, float4 g)
+{
+    reinterpret_cast<float4*>(vec + (size_t)V_XPREV * ld)[q] = x;
+    float4 y;
+    y.x = fminf(fmaxf(fmaf(-al, g.x, x.x), 0.f), 1.f);
+    y.y = fminf(fmaxf(fmaf(-al, g.y, x.y), 0.f), 1.f);
+    y.z = fminf(fmaxf(fmaf(-al, g.z, x.z), 0.f), 1.f);
+    y.w = fminf(fmaxf(fmaf(-al, g.w, x.w), 0.f), 1.f);
+    reinterpret_cast<float4*>(vec + (size_t)V_X * ld)[q] = y;
+    if (L.mode == MODE_TC) {
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(y.x, y.y), h23 = __floats2bfloat162_rn(y.z, y.w);
+        reinterpret_cast<__nv_bfloat162*>(L.u_hi)[2 * q] = h01;
+        reinterpret_cast<__nv_bfloat162*>(L.u_hi)[2 * q + 1] = h23;
+        if (L.u_lo) {
+            const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+            reinterpret_cast<__nv_bfloat162*>(L.u_lo)[2 * q] = __floats2bfloat162_rn(y.x - f01.x, y.y - f01.y);
+            reinterpret_cast<__nv_bfloat162*>(L.u_lo)[2 * q + 1] = __floats2bfloat162_rn(y.z - f23.x, y.w - f23.y);
+        }
+    } else {
+        reinterpret_cast<float4*>(vec + (size_t)V_U * ld)[q] = y;
+    }
+}
+
 // The element-wise part of a lane's update for the decision D, over elements [ia, ib) (and,
 // for the plain projected step, 16-byte groups [qa, qb) of the padded length).  Every element
 // is computed on its own, so a lane's result does not depend on how the range is split.
@@ -401,10 +480,8 @@ static __device__ void lane_apply(const LaneDev& L, const Params& P, const Decis
         // the common tick: x_prev <- x, x <- P(x - alpha g), u <- x over the padded length in
         // 16-byte pieces (padding stays zero: x = g = 0 there)
         const float al = D.alpha;
-        float4* X4 = reinterpret_cast<float4*>(vec + (size_t)V_X * ld);
-        float4* XP4 = reinterpret_cast<float4*>(vec + (size_t)V_XPREV * ld);
+        const float4* X4 = reinterpret_cast<const float4*>(vec + (size_t)V_X * ld);
         const float4* G4 = reinterpret_cast<const float4*>(vec + (size_t)V_G * ld);
-        float4* U4 = reinterpret_cast<float4*>(vec + (size_t)V_U * ld);
         // two groups per thread per pass, both loaded before either is stored
         for (int q0 = qa + tid; q0 < qb; q0 += 2 * nt) {
             float4 xs[2], gs[2];
@@ -418,29 +495,9 @@ static __device__ void lane_apply(const LaneDev& L, const Params& P, const Decis
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-            const int q = q0 + h * nt;
-            if (q >= qb) break;
-            const float4 x = xs[h], g = gs[h];
-            XP4[q] = x;
-            float4 y;
-            y.x = fminf(fmaxf(fmaf(-al, g.x, x.x), 0.f), 1.f);
-            y.y = fminf(fmaxf(fmaf(-al, g.y, x.y), 0.f), 1.f);
-            y.z = fminf(fmaxf(fmaf(-al, g.z, x.z), 0.f), 1.f);
-            y.w = fminf(fmaxf(fmaf(-al, g.w, x.w), 0.f), 1.f);
-            X4[q] = y;
-            if (L.mode == MODE_TC) {
-                const __nv_bfloat162 h01 = __floats2bfloat162_rn(y.x, y.y), h23 = __floats2bfloat162_rn(y.z, y.w);
-                reinterpret_cast<__nv_bfloat162*>(L.u_hi)[2 * q] = h01;
-                reinterpret_cast<__nv_bfloat162*>(L.u_hi)[2 * q + 1] = h23;
-                if (L.u_lo) {
-                    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-                    reinterpret_cast<__nv_bfloat162*>(L.u_lo)[2 * q] = __floats2bfloat162_rn(y.x - f01.x, y.y - f01.y);
-                    reinterpret_cast<__nv_bfloat162*>(L.u_lo)[2 * q + 1] =
-                        __floats2bfloat162_rn(y.z - f23.x, y.w - f23.y);
-                }
-            } else {
-                U4[q] = y;
-            }
+                const int q = q0 + h * nt;
+                if (q >= qb) break;
+                pabb_group(L, vec, ld, al, q, xs[h], gs[h]);
             }
         }
     }
@@ -524,10 +581,65 @@ static __device__ void lane_apply(const LaneDev& L, const Params& P, const Decis
     }
 }
 
+// The element-wise part of a LOBPCG iteration that does not end the eigen-solve (act =
+// A_LOB_UPDATE | A_RESID, next input u = D w): lane_apply's arithmetic for these flags, with
+// the loads of U elements per thread issued before any of their stores.
+template <int U>
+__device__ __forceinline__ void lob_iteration_apply(const LaneDev& L, const Decision& D, int tid, int nt)
+{
+    const int n = L.n, ld = L.ld;
+    float* vec = L.vec;
+    for (int i0 = tid; i0 < n; i0 += U * nt) {
+        float lx[U], lw[U], lp[U], lax[U], aw[U], lap[U], tt[U], dz[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * nt;
+            if (i < n) {
+                lx[u] = vec[V_LX * ld + i];
+                lw[u] = vec[V_LW * ld + i];
+                lp[u] = vec[V_LP * ld + i];
+                lax[u] = vec[V_LAX * ld + i];
+                aw[u] = vec[V_W * ld + i];
+                lap[u] = vec[V_LAP * ld + i];
+                tt[u] = vec[V_T * ld + i];
+                dz[u] = vec[V_D * ld + i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * nt;
+            if (i >= n) break;
+            const float np = fmaf(D.cw, lw[u], D.cp * lp[u]);
+            const float nap = fmaf(D.cw, aw[u], D.cp * lap[u]);
+            const float x1 = fmaf(D.cx, lx[u], np);
+            const float ax1 = fmaf(D.cx, lax[u], nap);
+            vec[V_LX * ld + i] = x1;
+            vec[V_LAX * ld + i] = ax1;
+            vec[V_LP * ld + i] = np;
+            vec[V_LAP * ld + i] = nap;
+            const float r = ax1 - D.lam * x1;
+            const float w1 = tt[u] * r;
+            vec[V_LW * ld + i] = w1;
+            const float uu = dz[u] * w1;
+            if (L.mode == MODE_TC) {
+                __nv_bfloat16 hi = __float2bfloat16_rn(uu);
+                L.u_hi[i] = hi;
+                if (L.u_lo) L.u_lo[i] = __float2bfloat16_rn(uu - __bfloat162float(hi));
+            } else {
+                vec[V_U * ld + i] = uu;
+            }
+        }
+    }
+}
+
 // The update of one lane by one CTA of 32..kBThreads threads (a multiple of 32).  Called by
 // the stand-alone update kernel and by the CTA that completes a GEMV lane's step.  With at
 // most blockDim.x partials every thread merges at most one, so the reduction order (and the
-// result) does not depend on the CTA size.
+// result) does not depend on the CTA size.  kStaged (the stand-alone kernel, which has the
+// registers for it): the thread's first partial and its 16-byte groups of x and g for a
+// projected step load together with the lane state, before the phase is known, and LOBPCG
+// iterations take lob_iteration_apply; the arithmetic is the same.
+template <bool kStaged = false>
 static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& P, int32_t* active_count)
 {
     __shared__ LaneState S;
@@ -536,6 +648,23 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
     __shared__ int32_t phase0;
 
     if (L.mode == MODE_GRAD) return;
+    const int tid = (int)threadIdx.x, nt = (int)blockDim.x, nq = L.ld >> 2;
+    constexpr int kPre = 3;   // groups of x and g per thread loaded ahead
+    Partial p0;
+    float4 xs[kPre], gs[kPre];
+    if (kStaged) {
+        if (tid < L.nblk) p0 = L.part[tid];
+        const float4* X4 = reinterpret_cast<const float4*>(L.vec + (size_t)V_X * L.ld);
+        const float4* G4 = reinterpret_cast<const float4*>(L.vec + (size_t)V_G * L.ld);
+#pragma unroll
+        for (int h = 0; h < kPre; ++h) {
+            const int q = tid + h * nt;
+            if (q < nq) {
+                xs[h] = X4[q];
+                gs[h] = G4[q];
+            }
+        }
+    }
     if (threadIdx.x == 0) {
         S = *L.st;
         phase0 = S.phase;
@@ -545,11 +674,22 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
     if (ph == PH_DONE) return;
 
     // ---- reduce the partials of this lane and take its decision
-    reduce_partials(L.part, L.nblk, ph, R);
+    reduce_partials(L.part, L.nblk, ph, R, kStaged ? &p0 : nullptr);
     if (threadIdx.x == 0) decide(L, S, R, P, D);
     __syncthreads();
     // ---- element-wise update
-    lane_apply(L, P, D, 0, L.n, 0, L.ld >> 2, (int)threadIdx.x, (int)blockDim.x);
+    if (kStaged && D.act == A_STEP_PABB && D.usrc == U_X) {
+#pragma unroll
+        for (int h = 0; h < kPre; ++h) {
+            const int q = tid + h * nt;
+            if (q < nq) pabb_group(L, L.vec, L.ld, D.alpha, q, xs[h], gs[h]);
+        }
+        if (kPre * nt < nq) lane_apply(L, P, D, 0, L.n, kPre * nt, nq, tid, nt);
+    } else if (kStaged && D.act == (A_LOB_UPDATE | A_RESID) && D.usrc == U_DLW) {
+        lob_iteration_apply<4>(L, D, tid, nt);
+    } else {
+        lane_apply(L, P, D, 0, L.n, 0, nq, tid, nt);
+    }
     const int act = D.act;
     if (threadIdx.x == 0) {
         if ((act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;

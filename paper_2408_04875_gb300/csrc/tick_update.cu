@@ -6,7 +6,7 @@ namespace ubqp {
 
 __global__ void __launch_bounds__(kBThreads) phase_b_kernel(TickArgs A, int32_t* active_count)
 {
-    lane_update(A.lanes[blockIdx.x], A.P, active_count);
+    lane_update<true>(A.lanes[blockIdx.x], A.P, active_count);
 }
 
 // CTA size: each update is a chain of dependent steps (partials, decision, element-wise
