@@ -34,8 +34,8 @@ GEMV_KERNELS = {1: "phase_a_gemv_kernel", 2: "lane_loop_kernel", 3: "solo_lane_k
 # DRAM bytes (read + write) per algorithmic byte of the dominant kernel, keyed by (scheduler,
 # storage), from an ncu capture of every launch of this workload's timed solve
 # (dram__bytes_read.sum + dram__bytes_write.sum over the launches against the bench's own
-# algorithmic bytes; profiles/solo_lane_kernel_c2.md); other combinations report null
-TRAFFIC_RATIO = {(3, 2): 0.7919 / 37.774}
+# algorithmic bytes; the C2 launch list under profiles/); other combinations report null
+TRAFFIC_RATIO = {(3, 2): 0.7935 / 37.774}
 SIZES = (250, 500, 1000, 2500)
 SEEDS_PER_SIZE = 10
 WORKLOAD = ("plain PSDP sweep: n in {250,500,1000,2500} x 10 seeded instances, density 0.1, "
