@@ -442,8 +442,11 @@ static __device__ void reduce_partials(const Partial* part, int nblk, int ph, Pa
     __syncthreads();
 }
 
-// One 16-byte group q of the projected step: x_prev <- x, x <- P(x - alpha g), u <- x.
-__device__ __forceinline__ void pabb_group(const LaneDev& L, float* vec, int ld, float al, int q, float4 x, float4 g)
+// One 16-byte group q of the projected step: x_prev <- x, x <- P(x - alpha g), u <- x (the
+// lane's mode and BF16 input pointers passed in: read from the descriptor after the stores
+// here, they would be loaded again, since the compiler cannot rule out that vec aliases it).
+__device__ __forceinline__ void pabb_group(int mode, __nv_bfloat16* u_hi, __nv_bfloat16* u_lo, float* vec, int ld,
+                                           float al, int q, float4 x, float4 g)
 {
     reinterpret_cast<float4*>(vec + (size_t)V_XPREV * ld)[q] = x;
     float4 y;
@@ -452,14 +455,14 @@ __device__ __forceinline__ void pabb_group(const LaneDev& L, float* vec, int ld,
     y.z = fminf(fmaxf(fmaf(-al, g.z, x.z), 0.f), 1.f);
     y.w = fminf(fmaxf(fmaf(-al, g.w, x.w), 0.f), 1.f);
     reinterpret_cast<float4*>(vec + (size_t)V_X * ld)[q] = y;
-    if (L.mode == MODE_TC) {
+    if (mode == MODE_TC) {
         const __nv_bfloat162 h01 = __floats2bfloat162_rn(y.x, y.y), h23 = __floats2bfloat162_rn(y.z, y.w);
-        reinterpret_cast<__nv_bfloat162*>(L.u_hi)[2 * q] = h01;
-        reinterpret_cast<__nv_bfloat162*>(L.u_hi)[2 * q + 1] = h23;
-        if (L.u_lo) {
+        reinterpret_cast<__nv_bfloat162*>(u_hi)[2 * q] = h01;
+        reinterpret_cast<__nv_bfloat162*>(u_hi)[2 * q + 1] = h23;
+        if (u_lo) {
             const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-            reinterpret_cast<__nv_bfloat162*>(L.u_lo)[2 * q] = __floats2bfloat162_rn(y.x - f01.x, y.y - f01.y);
-            reinterpret_cast<__nv_bfloat162*>(L.u_lo)[2 * q + 1] = __floats2bfloat162_rn(y.z - f23.x, y.w - f23.y);
+            reinterpret_cast<__nv_bfloat162*>(u_lo)[2 * q] = __floats2bfloat162_rn(y.x - f01.x, y.y - f01.y);
+            reinterpret_cast<__nv_bfloat162*>(u_lo)[2 * q + 1] = __floats2bfloat162_rn(y.z - f23.x, y.w - f23.y);
         }
     } else {
         reinterpret_cast<float4*>(vec + (size_t)V_U * ld)[q] = y;
@@ -497,7 +500,7 @@ static __device__ void lane_apply(const LaneDev& L, const Params& P, const Decis
             for (int h = 0; h < 2; ++h) {
                 const int q = q0 + h * nt;
                 if (q >= qb) break;
-                pabb_group(L, vec, ld, al, q, xs[h], gs[h]);
+                pabb_group(L.mode, L.u_hi, L.u_lo, vec, ld, al, q, xs[h], gs[h]);
             }
         }
     }
@@ -587,8 +590,13 @@ static __device__ void lane_apply(const LaneDev& L, const Params& P, const Decis
 template <int U>
 __device__ __forceinline__ void lob_iteration_apply(const LaneDev& L, const Decision& D, int tid, int nt)
 {
-    const int n = L.n, ld = L.ld;
+    // descriptor fields and decision scalars in registers (stores through vec would make the
+    // compiler load them again)
+    const int n = L.n, ld = L.ld, mode = L.mode;
     float* vec = L.vec;
+    __nv_bfloat16* const u_hi = L.u_hi;
+    __nv_bfloat16* const u_lo = L.u_lo;
+    const float cw = D.cw, cp = D.cp, cx = D.cx, lam = D.lam;
     for (int i0 = tid; i0 < n; i0 += U * nt) {
         float lx[U], lw[U], lp[U], lax[U], aw[U], lap[U], tt[U], dz[U];
 #pragma unroll
@@ -609,22 +617,22 @@ __device__ __forceinline__ void lob_iteration_apply(const LaneDev& L, const Deci
         for (int u = 0; u < U; ++u) {
             const int i = i0 + u * nt;
             if (i >= n) break;
-            const float np = fmaf(D.cw, lw[u], D.cp * lp[u]);
-            const float nap = fmaf(D.cw, aw[u], D.cp * lap[u]);
-            const float x1 = fmaf(D.cx, lx[u], np);
-            const float ax1 = fmaf(D.cx, lax[u], nap);
+            const float np = fmaf(cw, lw[u], cp * lp[u]);
+            const float nap = fmaf(cw, aw[u], cp * lap[u]);
+            const float x1 = fmaf(cx, lx[u], np);
+            const float ax1 = fmaf(cx, lax[u], nap);
             vec[V_LX * ld + i] = x1;
             vec[V_LAX * ld + i] = ax1;
             vec[V_LP * ld + i] = np;
             vec[V_LAP * ld + i] = nap;
-            const float r = ax1 - D.lam * x1;
+            const float r = ax1 - lam * x1;
             const float w1 = tt[u] * r;
             vec[V_LW * ld + i] = w1;
             const float uu = dz[u] * w1;
-            if (L.mode == MODE_TC) {
+            if (mode == MODE_TC) {
                 __nv_bfloat16 hi = __float2bfloat16_rn(uu);
-                L.u_hi[i] = hi;
-                if (L.u_lo) L.u_lo[i] = __float2bfloat16_rn(uu - __bfloat162float(hi));
+                u_hi[i] = hi;
+                if (u_lo) u_lo[i] = __float2bfloat16_rn(uu - __bfloat162float(hi));
             } else {
                 vec[V_U * ld + i] = uu;
             }
@@ -647,15 +655,22 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
     __shared__ Decision D;
     __shared__ int32_t phase0;
 
-    if (L.mode == MODE_GRAD) return;
-    const int tid = (int)threadIdx.x, nt = (int)blockDim.x, nq = L.ld >> 2;
+    // descriptor fields read once, before any store (the compiler cannot rule out that the
+    // stores through vec alias the descriptor and would load them again after each)
+    const int mode = L.mode, ld = L.ld;
+    if (mode == MODE_GRAD) return;
+    float* const vec = L.vec;
+    __nv_bfloat16* const u_hi = L.u_hi;
+    __nv_bfloat16* const u_lo = L.u_lo;
+    LaneState* const st = L.st;
+    const int tid = (int)threadIdx.x, nt = (int)blockDim.x, nq = ld >> 2;
     constexpr int kPre = 3;   // groups of x and g per thread loaded ahead
     Partial p0;
     float4 xs[kPre], gs[kPre];
     if (kStaged) {
         if (tid < L.nblk) p0 = L.part[tid];
-        const float4* X4 = reinterpret_cast<const float4*>(L.vec + (size_t)V_X * L.ld);
-        const float4* G4 = reinterpret_cast<const float4*>(L.vec + (size_t)V_G * L.ld);
+        const float4* X4 = reinterpret_cast<const float4*>(vec + (size_t)V_X * ld);
+        const float4* G4 = reinterpret_cast<const float4*>(vec + (size_t)V_G * ld);
 #pragma unroll
         for (int h = 0; h < kPre; ++h) {
             const int q = tid + h * nt;
@@ -666,7 +681,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
         }
     }
     if (threadIdx.x == 0) {
-        S = *L.st;
+        S = *st;
         phase0 = S.phase;
     }
     __syncthreads();
@@ -679,10 +694,11 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
     __syncthreads();
     // ---- element-wise update
     if (kStaged && D.act == A_STEP_PABB && D.usrc == U_X) {
+        const float al = D.alpha;
 #pragma unroll
         for (int h = 0; h < kPre; ++h) {
             const int q = tid + h * nt;
-            if (q < nq) pabb_group(L, L.vec, L.ld, D.alpha, q, xs[h], gs[h]);
+            if (q < nq) pabb_group(mode, u_hi, u_lo, vec, ld, al, q, xs[h], gs[h]);
         }
         if (kPre * nt < nq) lane_apply(L, P, D, 0, L.n, kPre * nt, nq, tid, nt);
     } else if (kStaged && D.act == (A_LOB_UPDATE | A_RESID) && D.usrc == U_DLW) {
@@ -695,7 +711,7 @@ static __device__ __noinline__ void lane_update(const LaneDev& L, const Params& 
         if ((act & A_TRACE) && L.trace_alpha) L.trace_alpha[D.trace_k] = D.alpha;
         S.updates += 1;
         if (S.phase == PH_DONE && L.nt_active) atomicSub(L.nt_active, 1);   // phase0 != PH_DONE here
-        *L.st = S;
+        *st = S;
         if (S.phase != PH_DONE && active_count) atomicAdd(active_count, 1);
     }
 }
