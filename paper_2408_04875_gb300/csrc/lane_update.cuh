@@ -55,13 +55,24 @@ __device__ __forceinline__ float start_component(int i)
     return ((float)(h >> 8) + 0.5f) * (2.0f / 16777216.0f) - 1.0f;
 }
 
+// 1/sqrt(v): the hardware reciprocal square root on the device; the host form (the two
+// functions below also compile for the host, where the tests pin them) divides by sqrtf
+__host__ __device__ __forceinline__ float rr_rsqrt(float v)
+{
+#ifdef __CUDA_ARCH__
+    return rsqrtf(v);
+#else
+    return 1.0f / sqrtf(v);
+#endif
+}
+
 // smallest eigenpair of a symmetric k x k matrix (k <= 3) by cyclic Jacobi rotations.
 // FP32 throughout: FP64 runs at a small fraction of the FP32 rate on this part, and the
 // preconditioned basis keeps the 3 x 3 Gram matrices well scaled.  Every loop runs over the
 // full 3 x 3 with the entries outside k x k masked, so that all indices are compile-time
 // constants and the matrices stay in registers (the operations and their order are those
 // of the k x k loops).
-__device__ __forceinline__ void small_sym_eig_min(int k, float (&M)[3][3], float& lam, float (&v)[3])
+__host__ __device__ __forceinline__ void small_sym_eig_min(int k, float (&M)[3][3], float& lam, float (&v)[3])
 {
     float V[3][3] = {{1.f, 0.f, 0.f}, {0.f, 1.f, 0.f}, {0.f, 0.f, 1.f}};
     for (int sweep = 0; sweep < 8; ++sweep) {
@@ -82,7 +93,7 @@ __device__ __forceinline__ void small_sym_eig_min(int k, float (&M)[3][3], float
                 if (q >= k || M[p][q] == 0.f) continue;
                 float theta = (M[q][q] - M[p][p]) / (2.f * M[p][q]);
                 float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-                float c = rsqrtf(t * t + 1.f), sn = t * c;
+                float c = rr_rsqrt(t * t + 1.f), sn = t * c;
 #pragma unroll
                 for (int r = 0; r < 3; ++r) {
                     if (r >= k) break;
@@ -118,7 +129,7 @@ __device__ __forceinline__ void small_sym_eig_min(int k, float (&M)[3][3], float
 // Gram entries: ga = (xAx, xAw, xAp, wAw, wAp, pAp), gb = (xx, xw, xp, ww, wp, pp).
 // Loops as in small_sym_eig_min: full 3 x 3, masked to k x k.  Not inlined: its registers are
 // needed only for the eigen-solver's decision, not in the kernels' hot loops.
-static __device__ __noinline__ bool rayleigh_ritz(const float (&ga)[6], const float (&gb)[6], bool has_p, float& lam,
+static __host__ __device__ __noinline__ bool rayleigh_ritz(const float (&ga)[6], const float (&gb)[6], bool has_p, float& lam,
                                               float (&c)[3])
 {
     const float A[3][3] = {{ga[0], ga[1], ga[2]}, {ga[1], ga[3], ga[4]}, {ga[2], ga[4], ga[5]}};
@@ -133,7 +144,7 @@ static __device__ __noinline__ bool rayleigh_ritz(const float (&ga)[6], const fl
         for (int t = 0; t < 3; ++t) {
             if (t >= k) break;
             if (!(B[t][t] > 0.f)) { bad = true; break; }
-            sc[t] = rsqrtf(B[t][t]);
+            sc[t] = rr_rsqrt(B[t][t]);
         }
         if (bad) { k -= 1; continue; }
         float As[3][3], Bs[3][3];
