@@ -7,9 +7,11 @@
 // split K.  A (128 x 64) and B (N x 64) k-blocks arrive by TMA in 128-byte-swizzled tiles
 // into a shared-memory ring, the lanes' hi rows and lo rows back to back; one thread issues
 // tcgen05.mma (kind::f16, BF16 x BF16 -> FP32, M = 128, K = 16 per instruction, N = twice the
-// tile's lanes, so one MMA covers both terms) and tcgen05.commit frees ring slots.  The accumulators are then read with tcgen05.ld,
-// parked in shared memory and summed across the cluster through distributed shared memory;
-// every CTA finishes a subset of the lanes with the per-row epilogue of the lane's phase.
+// tile's lanes, so one MMA covers both terms) and tcgen05.commit frees ring slots.  The
+// accumulators are then read with tcgen05.ld, parked in shared memory and summed across the
+// cluster through distributed shared memory; every CTA finishes a subset of the lanes with the
+// per-row epilogue of the lane's phase, whose operand rows each warp has meanwhile copied
+// (cp.async, a few lanes ahead) into slots of the freed ring after the accumulators.
 //
 // Every mbarrier wait is bounded (2 s of globaltimer); on expiry the CTA records an error,
 // stops issuing work, still passes every cluster barrier and frees its TMEM.
