@@ -12,7 +12,9 @@ build spells that contraction out; the function's correction loops must make bot
 Tensor-core layout.  ``qbf_index`` places the BF16 matrix in 128 x 64 tiles; it must be a
 bijection onto [0, ld^2) in which tile (M tile, k-block) is one contiguous run of 8192
 elements at position M tile * (ld / 64) + k-block, so that one TMA box of the
-(ld^2 / 64) x 64 view is one contiguous 16 KB copy.
+(ld^2 / 64) x 64 view is one contiguous 16 KB copy.  The split-K kernel's shared memory
+(``tc_smem_bytes``, ``tc_pick_stages`` and the epilogue-slot constants, compiled from the
+source) must hold its TMA ring and, after the main loop, the accumulators and the slots.
 """
 import pathlib
 import re
@@ -106,3 +108,64 @@ def test_qbf_index_is_a_tiled_bijection(ld):
             base = (M * (ld // 64) + K) * 8192
             # rows of 64 entries, one after the other, from the tile's base
             assert np.array_equal(tile, base + np.arange(8192, dtype=np.uint64).reshape(128, 64))
+
+
+TC_HARNESS = r"""
+#include <algorithm>
+#include <cstddef>
+#include <cstdio>
+%s
+int main()
+{
+    for (int two = 0; two < 2; ++two)
+        for (int bn = 16; bn <= 128; bn += 16) {
+            const int stages = tc_pick_stages(bn, two != 0);
+            const size_t total = tc_smem_bytes(bn, two != 0, stages);
+            const size_t stage = 128 * 128 + (size_t)bn * 128 * (two ? 2 : 1);
+            std::printf("%%d %%d %%d %%zu %%zu %%zu %%d %%d\n", two, bn, stages, total, stage, kEpiSlotBytes,
+                        kEpiSlot, kEpiDepth);
+        }
+    return 0;
+}
+"""
+
+
+def _tc_source_parts() -> str:
+    tc = (SRC.parent / "tc_gemm.cu").read_text()
+    hdr = (SRC.parent / "ubqp_tc.cuh").read_text()
+    parts = []
+    for text, pat in ((hdr, r"constexpr int kTcMaxStages = .*?;"),
+                      (tc, r"constexpr int kTcThreads = .*?;"),
+                      (tc, r"constexpr int kEpiDepth = .*?;"),
+                      (tc, r"constexpr int kEpiSlot = .*?;"),
+                      (tc, r"constexpr size_t kEpiSlotBytes = .*?;"),
+                      (tc, r"size_t tc_smem_bytes\(int bn, bool two, int stages\)\n\{.*?\n\}\n"),
+                      (tc, r"int tc_pick_stages\(int bn, bool two\)\n\{.*?\n\}\n")):
+        m = re.search(pat, text, re.S)
+        assert m, pat
+        parts.append(m.group(0))
+    return "\n".join(parts)
+
+
+def test_tc_shared_memory_holds_the_ring_and_the_epilogue_slots(tmp_path):
+    """The split-K kernel's dynamic shared memory (tc_smem_bytes for the stage count
+    tc_pick_stages gives) must hold, after the 1 KB alignment slack, the TMA ring of `stages`
+    k-blocks and, once the ring is free, the accumulators (128 x bn FP32) followed by every
+    warp's epilogue slots; the slots' offsets are 16-byte aligned (cp.async), and the total
+    leaves room for the kernel's static shared memory (9 KB) under the 227 KB per CTA.  Every
+    tile width the engine forms (multiples of 16 up to 128), one and two BF16 terms."""
+    src = tmp_path / "tc_smem.cpp"
+    src.write_text(TC_HARNESS % _tc_source_parts())
+    exe = tmp_path / "tc_smem"
+    subprocess.run(["g++", "-std=c++17", "-O1", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True, timeout=60).stdout.split("\n")
+    rows = [list(map(int, ln.split())) for ln in out if ln.strip()]
+    assert len(rows) == 16
+    for two, bn, stages, total, stage, slot_bytes, slot, depth in rows:
+        ring = total - 1024
+        assert 2 <= stages <= 4
+        assert ring >= stages * stage, (two, bn)
+        assert ring >= 128 * bn * 4 + slot_bytes, (two, bn)
+        assert (128 * bn * 4) % 16 == 0 and (slot * 4) % 16 == 0 and (depth * slot * 4) % 16 == 0
+        assert slot >= 7 * 128                      # seven operand vectors of 128 rows
+        assert total + 9 * 1024 <= 227 * 1024, (two, bn, total)
